@@ -1,0 +1,250 @@
+"""Seeded synthetic inputs for the dislocation-dynamics burst.
+
+This module only *draws inputs*: node positions of closed glide loops, their
+Burgers vectors and glide normals, pinned flags, applied stress tensors and
+volumes.  It holds none of the method's arithmetic (no stress field, force,
+mobility or averaging), so both the CUDA path and the CPU oracle may take
+their inputs from here.
+
+The paper builds its microstructures from boundary-to-boundary segment pairs
+(Sec. 3.2.1) with MoDELib; those microstructures are not published.  The
+workloads here are ensembles of circular glide loops on the 12 FCC
+{111}<110> slip systems:
+
+* node k of a loop sits at c + R (cos phi_k e1 + sin phi_k e2), with
+  e1 = b_hat, e2 = n x b_hat, phi_k = 2 pi k / n_nodes + phi_0;
+* the line sense is drawn as +-1 (a -1 reverses the node order);
+* all lengths are SI metres, stresses Pa, volumes m^3.
+
+Every generator takes an explicit integer seed and uses numpy's PCG64 stream,
+so a (seed, arguments) pair fixes the workload bit for bit on any host.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# Material (the loop-ensemble workloads: isotropic FCC, mu = 48 GPa,
+# nu = 0.34, |b| = 0.2556 nm, core width a = |b|, drag B = 1e-4 Pa s).
+# --------------------------------------------------------------------------
+MU = 48.0e9
+NU = 0.34
+BURGERS = 2.556e-10
+CORE_A = BURGERS
+DRAG_B = 1.0e-4
+MICRON = 1.0e-6
+
+
+@dataclasses.dataclass(frozen=True)
+class Material:
+    mu: float = MU
+    nu: float = NU
+    b: float = BURGERS
+    a: float = CORE_A
+    B: float = DRAG_B
+
+    def as_tuple(self):
+        return (self.mu, self.nu, self.b, self.a, self.B)
+
+
+def fcc_slip_systems():
+    """The 12 FCC {111}<110> slip systems as unit vectors.
+
+    Returns (b_hat[12,3], n_hat[12,3]); every b_hat lies in its plane
+    (b_hat . n_hat = 0).  Order: plane (111), (-111), (1-11), (11-1), and in
+    each plane the three <110> directions perpendicular to its normal.
+    """
+    normals = np.array([[1, 1, 1], [-1, 1, 1], [1, -1, 1], [1, 1, -1]], dtype=np.float64)
+    cands = np.array([[0, 1, -1], [1, 0, -1], [1, -1, 0],
+                      [0, 1, 1], [1, 0, 1], [1, 1, 0]], dtype=np.float64)
+    bs, ns = [], []
+    for n in normals:
+        for c in cands:
+            if c @ n == 0.0:
+                bs.append(c / math.sqrt(2.0))
+                ns.append(n / math.sqrt(3.0))
+    b = np.array(bs)
+    n = np.array(ns)
+    assert b.shape == (12, 3)
+    return b, n
+
+
+@dataclasses.dataclass
+class Network:
+    """One realisation: closed loops of straight segments (SI units).
+
+    Loop k owns nodes [loop_off[k], loop_off[k+1]); segment i runs from node i
+    to the next node of its loop (wrapping at the loop end).
+    """
+    xyz: np.ndarray        # [n_nodes, 3] float64, m
+    loop_off: np.ndarray   # [n_loops + 1] int64
+    burgers: np.ndarray    # [n_loops, 3] float64, m
+    normal: np.ndarray     # [n_loops, 3] float64, unit
+    pinned: np.ndarray     # [n_nodes] uint8
+    volume: float          # m^3
+    sig_app: np.ndarray    # [6] Pa, Voigt order xx, yy, zz, yz, xz, xy
+
+    @property
+    def n_nodes(self):
+        return int(self.xyz.shape[0])
+
+    @property
+    def n_loops(self):
+        return int(self.loop_off.shape[0] - 1)
+
+    def copy(self):
+        return Network(self.xyz.copy(), self.loop_off.copy(), self.burgers.copy(),
+                       self.normal.copy(), self.pinned.copy(), float(self.volume),
+                       self.sig_app.copy())
+
+
+def uniaxial_stress(value_pa, axis=2):
+    """Voigt stress vector of a uniaxial stress along a cube axis."""
+    s = np.zeros(6)
+    s[axis] = value_pa
+    return s
+
+
+def circular_loops(rng, n_loops, box_edge, r_min=0.05 * MICRON, r_max=0.2 * MICRON,
+                   nodes_per_loop=32, b_mag=BURGERS, systems=None):
+    """Draw n_loops circular glide loops (each a regular nodes_per_loop-gon).
+
+    Radius ~ U(r_min, r_max), centre ~ U[0, box_edge)^3, slip system ~ U{12}
+    (or drawn from `systems`), phase phi_0 ~ U[0, 2 pi), line sense ~ +-1.
+    Returns (xyz, loop_off, burgers, normal).
+    """
+    bh, nh = fcc_slip_systems()
+    if systems is None:
+        systems = np.arange(12)
+    sys_idx = rng.choice(np.asarray(systems), size=n_loops)
+    radius = rng.uniform(r_min, r_max, size=n_loops)
+    centre = rng.uniform(0.0, box_edge, size=(n_loops, 3))
+    phi0 = rng.uniform(0.0, 2.0 * math.pi, size=n_loops)
+    sense = rng.choice(np.array([-1.0, 1.0]), size=n_loops)
+
+    e1 = bh[sys_idx]
+    nrm = nh[sys_idx]
+    e2 = np.cross(nrm, e1)
+    k = np.arange(nodes_per_loop, dtype=np.float64)
+    phi = phi0[:, None] + sense[:, None] * (2.0 * math.pi / nodes_per_loop) * k[None, :]
+    xyz = (centre[:, None, :]
+           + radius[:, None, None] * (np.cos(phi)[:, :, None] * e1[:, None, :]
+                                      + np.sin(phi)[:, :, None] * e2[:, None, :]))
+    xyz = xyz.reshape(-1, 3)
+    loop_off = np.arange(n_loops + 1, dtype=np.int64) * nodes_per_loop
+    burgers = b_mag * e1
+    return np.ascontiguousarray(xyz), loop_off, np.ascontiguousarray(burgers), np.ascontiguousarray(nrm)
+
+
+def loop_ensemble(seed, n_loops, box_edge, sig_app, nodes_per_loop=32,
+                  r_min=0.05 * MICRON, r_max=0.2 * MICRON):
+    """A single realisation of n_loops free glide loops in a cube of edge box_edge."""
+    rng = np.random.default_rng(seed)
+    xyz, off, bv, nv = circular_loops(rng, n_loops, box_edge, r_min, r_max, nodes_per_loop)
+    return Network(xyz, off, bv, nv, np.zeros(xyz.shape[0], np.uint8),
+                   box_edge ** 3, np.asarray(sig_app, dtype=np.float64).copy())
+
+
+# --------------------------------------------------------------------------
+# The named workloads.
+# --------------------------------------------------------------------------
+SMALL_LOOPS = dict(n_loops=16, box_edge=1.0 * MICRON, steps=100, dt=1e-11, seed=1001)
+LARGE_LOOPS = dict(n_loops=1024, box_edge=5.0 * MICRON, steps=1000, dt=1e-11, seed=1002)
+
+
+def small_loop_network(seed=SMALL_LOOPS["seed"]):
+    """16 loops x 32 segments (512) in a 1 um cube, 50 MPa uniaxial along [001]."""
+    return loop_ensemble(seed, SMALL_LOOPS["n_loops"], SMALL_LOOPS["box_edge"],
+                         uniaxial_stress(50e6))
+
+
+def large_loop_network(seed=LARGE_LOOPS["seed"]):
+    """1024 loops x 32 segments (32768) in a 5 um cube, 50 MPa uniaxial along [001]."""
+    return loop_ensemble(seed, LARGE_LOOPS["n_loops"], LARGE_LOOPS["box_edge"],
+                         uniaxial_stress(50e6))
+
+
+@dataclasses.dataclass
+class Batch:
+    """R realisations concatenated (SI units).
+
+    Realisation r owns nodes [node_off[r], node_off[r+1]) and loops
+    [loop_base[r], loop_base[r+1]); loop_off indexes the concatenated nodes.
+    """
+    xyz: np.ndarray
+    loop_off: np.ndarray     # [total_loops + 1], global node indices
+    loop_base: np.ndarray    # [R + 1]
+    node_off: np.ndarray     # [R + 1]
+    burgers: np.ndarray
+    normal: np.ndarray
+    pinned: np.ndarray
+    sig6: np.ndarray         # [R, 6]
+    volume: np.ndarray       # [R]
+
+    @property
+    def R(self):
+        return int(self.node_off.shape[0] - 1)
+
+    def realisation(self, r):
+        n0, n1 = int(self.node_off[r]), int(self.node_off[r + 1])
+        l0, l1 = int(self.loop_base[r]), int(self.loop_base[r + 1])
+        return Network(self.xyz[n0:n1].copy(), self.loop_off[l0:l1 + 1] - n0,
+                       self.burgers[l0:l1].copy(), self.normal[l0:l1].copy(),
+                       self.pinned[n0:n1].copy(), float(self.volume[r]),
+                       self.sig6[r].copy())
+
+
+def batch_ensemble(seed, R=256, n_min=1024, n_max=16384, nodes_per_loop=32,
+                   stress_max=200e6, sessile_min=0.1, sessile_max=0.9,
+                   loops_per_um3=16.0):
+    """Batched ensemble of R independent realisations.
+
+    Per realisation: N_r ~ U{n_min..n_max} rounded to a multiple of
+    nodes_per_loop; each of the 6 stress components ~ U(-stress_max,
+    stress_max); sessile fraction f_r ~ U(sessile_min, sessile_max): whole
+    loops, in random order, are marked pinned until the pinned line length
+    reaches f_r of the total.  The cube edge keeps the loop density at
+    loops_per_um3, i.e. edge = (n_loops / loops_per_um3)^(1/3) um.
+    """
+    rng = np.random.default_rng(seed)
+    xs, bvs, nvs, pins, offs = [], [], [], [], []
+    loop_base = [0]
+    node_off = [0]
+    sig6 = np.empty((R, 6))
+    vol = np.empty(R)
+    for r in range(R):
+        n_r = int(rng.integers(n_min, n_max + 1))
+        n_loops = max(1, int(round(n_r / nodes_per_loop)))
+        edge = (n_loops / loops_per_um3) ** (1.0 / 3.0) * MICRON
+        xyz, off, bv, nv = circular_loops(rng, n_loops, edge, nodes_per_loop=nodes_per_loop)
+        sig6[r] = rng.uniform(-stress_max, stress_max, size=6)
+        frac = rng.uniform(sessile_min, sessile_max)
+        # pinned loops: random order until the pinned length fraction reaches frac
+        seg = np.roll(xyz.reshape(n_loops, nodes_per_loop, 3), -1, axis=1) - xyz.reshape(n_loops, nodes_per_loop, 3)
+        loop_len = np.sqrt((seg ** 2).sum(-1)).sum(-1)
+        order = rng.permutation(n_loops)
+        pinned_loop = np.zeros(n_loops, bool)
+        acc, tot = 0.0, loop_len.sum()
+        for k in order:
+            if acc >= frac * tot:
+                break
+            pinned_loop[k] = True
+            acc += loop_len[k]
+        pin = np.repeat(pinned_loop, nodes_per_loop).astype(np.uint8)
+        xs.append(xyz)
+        bvs.append(bv)
+        nvs.append(nv)
+        pins.append(pin)
+        offs.append(off[:-1] + node_off[-1])
+        node_off.append(node_off[-1] + xyz.shape[0])
+        loop_base.append(loop_base[-1] + n_loops)
+        vol[r] = edge ** 3
+    loop_off = np.concatenate(offs + [np.array([node_off[-1]], np.int64)]).astype(np.int64)
+    return Batch(np.ascontiguousarray(np.concatenate(xs)), loop_off,
+                 np.asarray(loop_base, np.int64), np.asarray(node_off, np.int64),
+                 np.ascontiguousarray(np.concatenate(bvs)), np.ascontiguousarray(np.concatenate(nvs)),
+                 np.concatenate(pins), sig6, vol)
