@@ -1,0 +1,340 @@
+#!/usr/bin/env python3
+"""Benchmark of the DD burst: segment-pair evaluations per second.
+
+Workload: 1024 circular FCC glide loops x 32 segments (32768 segments) in a
+5 um cube, isotropic FCC (mu 48 GPa, nu 0.34, b 0.2556 nm, a = b), drag
+B = 1e-4 Pa s, 50 MPa uniaxial [001], dt = 1e-11 s.  One benchmark step is
+one pass of the whole burst hot path -- pair stress at 4 Gauss points of
+every segment from every segment, Peach-Koehler nodal forces, glide
+mobility, Lp/rho averaging, explicit Euler -- over `--dd-steps` DD steps.
+
+  value   : device time (CUDA events on the library's stream) of the K
+            timed steps, inputs resident in HBM, L2 flushed between steps;
+  e2e     : the same metric through the C ABI with host buffers: per step
+            positions copied in from pinned host memory (ptadd_set_nodes),
+            the burst, positions and averages copied back;
+  roofline: the pair-stress kernel, algorithmic FP64/FP32 FLOPs per launch
+            over its CUDA-event time, against the measured FMA peak;
+  cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): every rank runs its own realisation (seed + rank);
+no data-path collective; the timed region is bracketed by barriers and the
+maximum time over ranks is reported ("scaling": "weak").
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2005_02498_gb300 import workloads as W  # noqa: E402
+
+# Algorithmic FLOPs of one segment-pair evaluation (one source segment at the
+# 4 Gauss points of one target segment), counted from the formulation in
+# csrc/seg_field.cuh with an FMA as 2 FLOPs and each reciprocal or
+# reciprocal square root as 1: 4 x 165 per field point + 19 per pair.
+FLOPS_PER_PAIR = 4 * 165 + 19
+L2_FLUSH_BYTES = 256 << 20
+WORKLOAD = ("1024 circular FCC glide loops x 32 segments = 32768 segments, 5 um cube, "
+            "mu 48 GPa, nu 0.34, b 0.2556 nm, a = b, B 1e-4 Pa s, 50 MPa [001], dt 1e-11 s")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--dd-steps", type=int, default=1, help="DD steps per benchmark step")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU-baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+
+        sm = [num(r[1]) for r in rows]
+        mx = [num(r[2]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": float(np.nanmax(mx)), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- helpers
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("seg_field.cuh", "dd_kernels.cu"):
+        h.update(open(os.path.join(ROOT, "paper_2005_02498_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(precision):
+    """DRAM bytes per pair launch from a committed ncu capture, if the kernel
+    source is unchanged since it was taken."""
+    path = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    e = rec.get(precision)
+    if not e or e.get("kernel_src_sha") != kernel_source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def cpu_sample(net, seconds, mat):
+    """Oracle forces on a random node sample sized to take about `seconds`."""
+    import oracle  # test infrastructure: only this baseline leg uses it
+    rng = np.random.default_rng(7)
+    k = 8
+    t0 = time.perf_counter()
+    oracle.nodal_forces_subset(mat, net, rng.choice(net.n_nodes, k, replace=False))
+    dt = time.perf_counter() - t0
+    k = int(max(8, min(net.n_nodes, k * seconds / max(dt, 1e-3))))
+    sel = rng.choice(net.n_nodes, k, replace=False)
+    t0 = time.perf_counter()
+    oracle.nodal_forces_subset(mat, net, sel)
+    dt = time.perf_counter() - t0
+    pairs = 2 * k * net.n_nodes  # two target segments per node, every source
+    return pairs / dt, oracle.num_threads(), k, dt
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+# --------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    net = W.large_loop_network()
+    mat = W.Material().as_tuple()
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_sample(net, per_step / 4, mat)
+    vals, cores, ks, secs = [], 0, [], 0.0
+    for _ in range(args.steps):
+        v, cores, k, dt = cpu_sample(net, per_step, mat)
+        vals.append(v)
+        ks.append(k)
+        secs += dt
+    value = float(np.mean(vals))
+    sample = ("FP64 CPU oracle: nodal forces of %d-%d randomly sampled nodes (2 target segments each) "
+              "against all 32768 source segments per step" % (min(ks), max(ks)))
+    emit({"impl": "reference", "metric": "segment-pair evals/s", "value": value, "unit": "pair-evals/s",
+          "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+          "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+          "config": {"workload": WORKLOAD, "precision": "fp64", "sampled": True},
+          "cpu_baseline": {"value": value, "unit": "pair-evals/s", "cores": cores, "kind": "oracle",
+                           "sample": sample},
+          "e2e": {"value": value, "unit": "pair-evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+    return 0
+
+
+# -------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+
+    from paper_2005_02498_gb300 import ptadd
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    ptadd.load()
+    prec = ptadd.PTADD_FP64 if args.precision == "fp64" else ptadd.PTADD_MIXED
+    mat = W.Material()
+    net = W.large_loop_network(seed=W.LARGE_LOOPS["seed"] + rank)
+    dt = W.LARGE_LOOPS["dt"]
+    stream = torch.cuda.current_stream()
+    ctx = ptadd.Context(mat.as_tuple(), prec, local)
+    ctx.set_stream(stream.cuda_stream)
+    ctx.set_network(net)
+    info = ctx.info()
+    pairs_per_bench_step = info["pairs_per_step"] * args.dd_steps
+
+    peak_fp64 = ptadd.fma_peak(local, fp64=True, seconds=2.0)
+    peak_fp32 = ptadd.fma_peak(local, fp64=False, seconds=2.0)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        ctx.advance(args.dd_steps, dt)
+    torch.cuda.synchronize()
+
+    # ---- device-timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.profile_reset(timing=True)
+    evs = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # evict L2 between timed steps
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.advance(args.dd_steps, dt)
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = sum(a.elapsed_time(b) for a, b in evs)
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = world * pairs_per_bench_step * args.steps / (elapsed_ms * 1e-3)
+
+    # ---- end to end through the C ABI with pinned host buffers
+    n = info["n_nodes"]
+    host_in = torch.from_numpy(net.xyz.copy()).pin_memory()
+    host_out = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    ctx.profile_reset(timing=False)
+    e2e_times = []
+    for i in range(args.e2e_steps + 1):
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        ctx.set_nodes(host_in.data_ptr())
+        ctx.advance(args.dd_steps, dt)
+        ctx.get_nodes_into(host_out.data_ptr())
+        t1 = time.perf_counter()
+        if i > 0:  # the first round trip is a warm-up
+            e2e_times.append(t1 - t0)
+    e2e_s = float(np.sum(e2e_times))
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * pairs_per_bench_step * len(e2e_times) / e2e_s
+    h2d = 3 * n * 8
+    d2h = 3 * n * 8 + 10 * 8 + 4
+
+    # ---- roofline of the dominant kernel (pair stress)
+    avg_ms = prof["pair_ms"] / max(1, prof["pair_launches"])
+    evals_per_launch = prof["pair_evals"] / max(1, prof["pair_launches"])
+    achieved = FLOPS_PER_PAIR * evals_per_launch / (avg_ms * 1e-3)
+    peak = peak_fp64 if args.precision == "fp64" else peak_fp32
+    roof = {"kernel": "pair_fp64_kernel" if args.precision == "fp64" else "pair_mixed_kernel",
+            "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": recorded_traffic(args.precision),
+            "flops_per_pair": FLOPS_PER_PAIR, "pair_evals_per_launch": evals_per_launch,
+            "avg_launch_ms": avg_ms,
+            "peak_source": "measured in this run: ptadd_fma_peak, %s FMA chains on every SM for ~2 s "
+                           "(no FP64/FP32 figure in MEASURED_PEAKS.json)" % ("FP64" if args.precision == "fp64" else "FP32"),
+            "peak_fp64_tflops": peak_fp64 / 1e12, "peak_fp32_tflops": peak_fp32 / 1e12}
+
+    out = {"metric": "segment-pair evals/s", "value": value, "unit": "pair-evals/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "precision": args.precision, "dd_steps_per_step": args.dd_steps,
+                      "pairs_per_step": pairs_per_bench_step, "segments": n,
+                      "l2": "flushed between timed steps (256 MB device write)",
+                      "parallelism": "one independent realisation per GPU" if world > 1 else "single GPU"},
+           "roofline": roof,
+           "e2e": {"value": e2e_value, "unit": "pair-evals/s", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h},
+           "gpu_launches": int(prof["kernel_launches"]),
+           "clocks": clk}
+    ctx.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, k, secs = cpu_sample(net, args.cpu_seconds, mat.as_tuple())
+        out["cpu_baseline"] = {"value": v, "unit": "pair-evals/s", "cores": cores, "kind": "oracle",
+                               "sample": "FP64 CPU oracle, nodal forces of %d random nodes (%d target segments) "
+                                         "against all %d sources, %.1f s" % (k, 2 * k, n, secs)}
+    if rank == 0:
+        emit(out)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,191 @@
+/*
+ * ptadd.h -- C ABI of the GPU discrete-dislocation-dynamics (DD) burst used
+ * by Practical Time Averaging (PTA) to close mesoscale plasticity
+ * (arXiv:2005.02498, "Plasticity without phenomenology: a first step").
+ *
+ * The problem the calls follow (Sec. 2.1, 2.3, 2.4): given a network of
+ * closed dislocation loops (straight segments between nodes), their Burgers
+ * vectors and glide normals, and an applied stress held fixed (the load l_t
+ * of Eq. 2.4), run the fast DD dynamics for a burst of explicit Euler steps
+ * and return the running time averages (Eq. 2.5) of the plastic distortion
+ * rate Lp (Sec. 2.2, Eq. 2.9) and of the line density rho (Sec. 2.4).
+ *
+ * One DD step (Sec. 2.1):
+ *   1. sigma(x_q) = sigma_app + sum over ALL segments of the nonsingular
+ *      isotropic stress of a straight segment (sigma = S R * alpha, Sec. 2.1;
+ *      R replaced by R_a = sqrt(R.R + a^2)), at the 4 Gauss-Legendre points
+ *      x_q of every target segment;
+ *   2. Peach-Koehler force per length f_q = (sigma(x_q) b) x t (Sec. 2.1),
+ *      assembled to nodes with linear shape functions;
+ *   3. lumped glide mobility v_a = (I - n n) F_a / (B M_a),
+ *      M_a = (L_prev + L_next)/2, v_a = 0 at pinned nodes (Eq. 2.1);
+ *   4. Lp_i = (1/V) sum_s L_s b_s (x) (t_s x vbar_s), rho_i = (1/V) sum_s L_s,
+ *      evaluated on the step-start state and accumulated with weight dt;
+ *   5. x_a <- x_a + v_a dt for all nodes at once.
+ *
+ * Conventions
+ *   - SI units at the boundary: m, Pa, s, N.  Stresses are Voigt 6-vectors in
+ *     the order xx, yy, zz, yz, xz, xy.  Lp is a row-major 3x3 matrix (1/s).
+ *   - Every call returns a ptadd_status.  Nothing aborts the process.  After
+ *     an error the message is available from ptadd_last_error(); the context
+ *     stays usable unless the status is PTADD_ERR_CUDA from a sticky device
+ *     error.
+ *   - Host arrays passed in are copied; the caller keeps ownership.  Device
+ *     pointers ("_dev" calls) must stay valid until the call's work on the
+ *     context's stream has completed.
+ *   - A context is not thread-safe; use one context per host thread.
+ *   - All device memory a context needs is allocated by ptadd_create /
+ *     ptadd_set_network / ptadd_batch_run and freed by ptadd_destroy.
+ */
+#ifndef PTADD_H
+#define PTADD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PTADD_VERSION_MAJOR 0
+#define PTADD_VERSION_MINOR 1
+
+typedef struct ptadd_ctx ptadd_ctx; /* opaque; owns its device memory and stream */
+
+typedef enum {
+    PTADD_OK = 0,
+    PTADD_ERR_ARG = 1,       /* invalid argument (size, pointer, non-unit normal, ...) */
+    PTADD_ERR_CUDA = 2,      /* a CUDA runtime call failed                              */
+    PTADD_ERR_NONFINITE = 3, /* a burst produced NaN/Inf (positions or averages)        */
+    PTADD_ERR_TIMEOUT = 4,   /* a bounded device-side wait gave up                      */
+    PTADD_ERR_STATE = 5,     /* call out of order (e.g. advance before set_network)     */
+    PTADD_ERR_NOMEM = 6      /* device allocation failed                                */
+} ptadd_status;
+
+/* Isotropic material and the drag law (SI).  a is the core width of the
+ * nonsingular field; b the reference Burgers-vector magnitude (the unit of
+ * length inside the kernels); B the scalar drag coefficient of Eq. 2.1. */
+typedef struct {
+    double mu; /* shear modulus, Pa */
+    double nu; /* Poisson ratio     */
+    double b;  /* |b|, m            */
+    double a;  /* core width, m     */
+    double B;  /* drag, Pa s        */
+} ptadd_material;
+
+typedef enum {
+    PTADD_FP64 = 0, /* every pair interaction in FP64                                  */
+    PTADD_MIXED = 1 /* pairs farther than 10a in FP32 (compensated), nearer in FP64;   *
+                     * positions, forces and averages always FP64                      */
+} ptadd_precision;
+
+/* Static description of the loaded network and of the work of one step. */
+typedef struct {
+    int64_t n_nodes;
+    int64_t n_loops;
+    int64_t n_targets;      /* segments whose force is evaluated (>= 1 unpinned node) */
+    int64_t pairs_per_step; /* n_targets * n_nodes: segment-pair evaluations per step */
+    int32_t precision;      /* ptadd_precision                                        */
+    int32_t device;
+} ptadd_info;
+
+/* ---------------------------------------------------------------- lifetime */
+/* Library version as major*1000 + minor. */
+int ptadd_version(void);
+
+/* Create a context on CUDA device `device` (it is made current).  mat must
+ * have mu > 0, -1 < nu < 0.5, b > 0, a > 0, B > 0. */
+ptadd_status ptadd_create(ptadd_ctx** out, const ptadd_material* mat, ptadd_precision prec, int device);
+void ptadd_destroy(ptadd_ctx* ctx);
+
+/* Message of the last failed call on this host thread (never NULL). */
+const char* ptadd_last_error(void);
+
+/* Switch precision of later bursts. */
+ptadd_status ptadd_set_precision(ptadd_ctx* ctx, ptadd_precision prec);
+
+/* Run the context's work on a caller-owned stream (a cudaStream_t passed as
+ * void*; NULL restores the context's own stream). */
+ptadd_status ptadd_set_stream(ptadd_ctx* ctx, void* stream);
+
+/* ----------------------------------------------------------------- network */
+/* Load one realisation (host arrays, copied).  Loops are closed rings: loop k
+ * owns nodes [loop_off[k], loop_off[k+1]) in order (line sense = node order,
+ * segment i runs from node i to the next node of its loop, wrapping).
+ *   xyz[n_nodes*3]       node positions, m
+ *   loop_off[n_loops+1]  loop_off[0] = 0, increasing, loop_off[n_loops] = n_nodes,
+ *                        every loop has >= 2 nodes
+ *   burgers[n_loops*3]   Burgers vector per loop, m
+ *   normal[n_loops*3]    glide normal per loop, | |n| - 1 | <= 1e-9
+ *   pinned[n_nodes]      1 = sessile node (never moves); NULL = none pinned.
+ *                        Segments whose two nodes are pinned act as sources
+ *                        only: their own force is not evaluated.
+ *   volume               averaging volume |B_x| of Sec. 2.2, m^3, > 0
+ * Resets the running averages and the applied stress to zero. */
+ptadd_status ptadd_set_network(ptadd_ctx* ctx, int64_t n_nodes, const double* xyz,
+                               int64_t n_loops, const int64_t* loop_off,
+                               const double* burgers, const double* normal,
+                               const uint8_t* pinned, double volume);
+
+/* Applied stress sigma_app (Pa, Voigt order), uniform over the box. */
+ptadd_status ptadd_set_applied_stress(ptadd_ctx* ctx, const double sig[6]);
+
+ptadd_status ptadd_get_info(const ptadd_ctx* ctx, ptadd_info* info);
+
+/* ------------------------------------------------------------------- burst */
+/* Advance the loaded network by n_steps >= 0 Euler steps of dt > 0 s and
+ * return R^Lp (row-major 3x3, 1/s) and R^rho (1/m^2), the averages of Eq. 2.5
+ * over the n_steps step-start states of this call.  Either output may be
+ * NULL.  Positions stay on the device.  Returns PTADD_ERR_NONFINITE if a
+ * position or an average is not finite (the positions are then undefined). */
+ptadd_status ptadd_advance(ptadd_ctx* ctx, int64_t n_steps, double dt,
+                           double Lp_avg[9], double* rho_avg);
+
+/* Current node positions (m) into host xyz[n_nodes*3]. */
+ptadd_status ptadd_get_nodes(ptadd_ctx* ctx, double* xyz);
+
+/* Replace the positions of the loaded network (host xyz[n_nodes*3], m; same
+ * topology).  The array is copied to the device as is (pinned host memory
+ * gives a direct DMA) and converted there.  Resets nothing else. */
+ptadd_status ptadd_set_nodes(ptadd_ctx* ctx, const double* xyz);
+
+/* Nodal forces (N) at the current positions into host F[n_nodes*3]; every
+ * segment is evaluated (pinned ones included). */
+ptadd_status ptadd_get_forces(ptadd_ctx* ctx, double* F);
+
+/* Same as ptadd_get_forces into a device buffer F_dev[n_nodes*3] (N),
+ * enqueued on the context's stream; returns without synchronising. */
+ptadd_status ptadd_get_forces_dev(ptadd_ctx* ctx, double* F_dev);
+
+/* Serialise the positions (so a burst can resume where the last ended, the
+ * PTA carry-over of Sec. 2.5) into buf.  Call with buf = NULL to get the size
+ * in *bytes; otherwise *bytes must hold the buffer size. */
+ptadd_status ptadd_get_state(ptadd_ctx* ctx, void* buf, size_t* bytes);
+ptadd_status ptadd_set_state(ptadd_ctx* ctx, const void* buf, size_t bytes);
+
+/* ------------------------------------------------------------- measurement */
+/* Launch counters and CUDA-event timing of the pair-stress kernels, recorded
+ * on the stream they are launched on.  Timing costs two event records per
+ * pair launch and is off by default. */
+typedef struct {
+    int64_t kernel_launches; /* kernels this context launched since the last reset */
+    int64_t pair_launches;   /* of which pair-stress kernels                         */
+    int64_t pair_evals;      /* segment-pair evaluations those launches performed    */
+    double pair_ms;          /* summed event time of the pair launches (timing on)   */
+} ptadd_profile;
+
+/* Reset the counters; enable (1) or disable (0) the event timing. */
+ptadd_status ptadd_profile_reset(ptadd_ctx* ctx, int timing);
+/* Read the counters (synchronises the context's stream). */
+ptadd_status ptadd_profile_read(ptadd_ctx* ctx, ptadd_profile* out);
+
+/* Throughput of dependent fused multiply-add chains on every SM of `device`
+ * (FP64 if fp64 != 0, else FP32), run for about `seconds`; *flops receives
+ * FLOP/s counting an FMA as 2.  The non-tensor arithmetic peak the pair
+ * kernels are compared against. */
+ptadd_status ptadd_fma_peak(int device, int fp64, double seconds, double* flops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PTADD_H */

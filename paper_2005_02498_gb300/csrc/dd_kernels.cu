@@ -1,0 +1,310 @@
+// dd_kernels.cu -- one explicit DD step on the GPU (Sec. 2.1 of the paper):
+//   seg_prep      : per-segment source records from the current positions
+//   pair_fp64     : O(N^2) stress at the 4 Gauss points of every target
+//                   segment, contracted with its Burgers vector, folded into
+//                   the two nodal force parts of the segment (PK force, linear
+//                   shape functions)
+//   node_velocity : nodal force = own part + previous segment's part,
+//                   glide-projected lumped mobility
+//   lp_euler      : Lp / rho sample of the step-start state (Sec. 2.2, 2.4),
+//                   explicit Euler into the other position buffer, block
+//                   partial sums; lp_finish sums them in a fixed order into
+//                   the running averages of Eq. 2.5.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "ptadd_internal.cuh"
+#include "seg_field.cuh"
+
+namespace ptadd {
+
+// ----------------------------------------------------------- seg_prep
+__global__ void seg_prep_kernel(int64_t n, const double* __restrict__ pos, const int32_t* __restrict__ nxt,
+                                const int32_t* __restrict__ loop_of, const double* __restrict__ loop_b,
+                                double* __restrict__ src)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t j = nxt[i];
+    const double x1 = pos[i], y1 = pos[n + i], z1 = pos[2 * n + i];
+    const double dx = pos[j] - x1, dy = pos[n + j] - y1, dz = pos[2 * n + j] - z1;
+    const double L = sqrt(dx * dx + dy * dy + dz * dz);
+    const int k = loop_of[i];
+    double bx = loop_b[3 * k], by = loop_b[3 * k + 1], bz = loop_b[3 * k + 2];
+    double tx = 1.0, ty = 0.0, tz = 0.0;
+    if (L > 0.0) {
+        tx = dx / L;
+        ty = dy / L;
+        tz = dz / L;
+    }
+    double* r = src + (int64_t)SRC_STRIDE * i;
+    r[0] = x1; r[1] = y1; r[2] = z1; r[3] = L;
+    r[4] = tx; r[5] = ty; r[6] = tz; r[7] = 0.0;
+    r[8] = bx; r[9] = by; r[10] = bz; r[11] = 0.0;
+    r[12] = by * tz - bz * ty;
+    r[13] = bz * tx - bx * tz;
+    r[14] = bx * ty - by * tx;
+    r[15] = 0.0;
+}
+
+cudaError_t launch_seg_prep(const DevNetwork& net, cudaStream_t st)
+{
+    const int64_t n = net.n_nodes;
+    if (n == 0) return cudaSuccess;
+    seg_prep_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, net.pos[net.cur], net.nxt, net.loop_of,
+                                                                  net.loop_b, net.src);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------- pair_fp64
+// Grid: x = target tiles of PAIR_TPB threads (one target segment each),
+//       y = source chunks.  Each block stages PAIR_TILE source records at a
+// time through shared memory; every thread walks them in the same order
+// (broadcast reads) and accumulates (sigma b') at its 4 Gauss points.
+constexpr int PAIR_TPB = 128;
+constexpr int PAIR_TILE = 128;
+
+__global__ void __launch_bounds__(PAIR_TPB) pair_fp64_kernel(
+    int64_t n, const double* __restrict__ pos, const int32_t* __restrict__ nxt,
+    const double* __restrict__ src, const int32_t* __restrict__ tgt, int64_t n_tgt, int64_t chunk_len,
+    Consts c, double s0, double s1, double s2, double s3, double s4, double s5, double* __restrict__ fpart)
+{
+    __shared__ double2 tile[PAIR_TILE * SRC_STRIDE / 2];
+    const int64_t kt = blockIdx.x * (int64_t)PAIR_TPB + threadIdx.x;
+    const int chunk = blockIdx.y;
+    const int64_t js = (int64_t)chunk * chunk_len;
+    const int64_t je = min(n, js + chunk_len);
+    const bool active = kt < n_tgt;
+    const int64_t seg = active ? tgt[kt] : 0;
+
+    // target segment: start node, chord, Burgers vector, 4 Gauss points
+    const double* tr = src + (int64_t)SRC_STRIDE * seg;
+    const int64_t sb = nxt[seg];
+    const double xa = pos[seg], ya = pos[n + seg], za = pos[2 * n + seg];
+    const double Dx = pos[sb] - xa, Dy = pos[n + sb] - ya, Dz = pos[2 * n + sb] - za;
+    const double bt[3] = {tr[8], tr[9], tr[10]};
+    double xq[4][3];
+#pragma unroll
+    for (int qp = 0; qp < 4; ++qp) {
+        const double xi = gl4_xi(qp);
+        xq[qp][0] = fma(xi, Dx, xa);
+        xq[qp][1] = fma(xi, Dy, ya);
+        xq[qp][2] = fma(xi, Dz, za);
+    }
+    double acc[4][3];
+#pragma unroll
+    for (int qp = 0; qp < 4; ++qp) acc[qp][0] = acc[qp][1] = acc[qp][2] = 0.0;
+
+    for (int64_t j0 = js; j0 < je; j0 += PAIR_TILE) {
+        const int cnt = (int)min((int64_t)PAIR_TILE, je - j0);
+        __syncthreads();
+        const double2* g = reinterpret_cast<const double2*>(src + (int64_t)SRC_STRIDE * j0);
+        for (int e = threadIdx.x; e < cnt * (SRC_STRIDE / 2); e += PAIR_TPB) tile[e] = g[e];
+        __syncthreads();
+        for (int jj = 0; jj < cnt; ++jj) {
+            const double* r = reinterpret_cast<const double*>(tile + jj * (SRC_STRIDE / 2));
+            const double L = r[3];
+            if (!(L > 0.0)) continue;  // zero-length source: no field (uniform branch)
+            const double x1[3] = {r[0], r[1], r[2]};
+            const double t[3] = {r[4], r[5], r[6]};
+            const double b[3] = {r[8], r[9], r[10]};
+            const double q[3] = {r[12], r[13], r[14]};
+            PairK<double> k;
+            pair_constants(t, b, q, bt, k);
+#pragma unroll
+            for (int qp = 0; qp < 4; ++qp)
+                seg_sigma_b(xq[qp][0] - x1[0], xq[qp][1] - x1[1], xq[qp][2] - x1[2], t, L, b, q, bt, k, c.a2,
+                            c.c1, c.c2, acc[qp]);
+        }
+    }
+    if (!active) return;
+    if (chunk == 0) {  // applied stress, once per target
+        const double sb0 = s0 * bt[0] + s5 * bt[1] + s4 * bt[2];
+        const double sb1 = s5 * bt[0] + s1 * bt[1] + s3 * bt[2];
+        const double sb2 = s4 * bt[0] + s3 * bt[1] + s2 * bt[2];
+#pragma unroll
+        for (int qp = 0; qp < 4; ++qp) {
+            acc[qp][0] += sb0;
+            acc[qp][1] += sb1;
+            acc[qp][2] += sb2;
+        }
+    }
+    // F_start = sum_q w_q (1 - xi_q) (s_q x D), F_end = sum_q w_q xi_q (s_q x D)   (L t = D)
+    double Fs[3] = {0, 0, 0}, Fe[3] = {0, 0, 0};
+#pragma unroll
+    for (int qp = 0; qp < 4; ++qp) {
+        const double fx = acc[qp][1] * Dz - acc[qp][2] * Dy;
+        const double fy = acc[qp][2] * Dx - acc[qp][0] * Dz;
+        const double fz = acc[qp][0] * Dy - acc[qp][1] * Dx;
+        const double we = gl4_w(qp) * gl4_xi(qp), ws = gl4_w(qp) - we;
+        Fs[0] = fma(ws, fx, Fs[0]); Fs[1] = fma(ws, fy, Fs[1]); Fs[2] = fma(ws, fz, Fs[2]);
+        Fe[0] = fma(we, fx, Fe[0]); Fe[1] = fma(we, fy, Fe[1]); Fe[2] = fma(we, fz, Fe[2]);
+    }
+    double* fp = fpart + (int64_t)chunk * 6 * n;
+    fp[0 * n + seg] = Fs[0];
+    fp[1 * n + seg] = Fs[1];
+    fp[2 * n + seg] = Fs[2];
+    fp[3 * n + seg] = Fe[0];
+    fp[4 * n + seg] = Fe[1];
+    fp[5 * n + seg] = Fe[2];
+}
+
+int choose_chunks(int64_t n_tgt, int64_t n_src, int max_chunks)
+{
+    // enough blocks to fill 152 SMs several times over, chunks of >= 1 tile
+    const int64_t tiles_t = (n_tgt + PAIR_TPB - 1) / PAIR_TPB;
+    const int64_t want_blocks = 152 * 8;
+    int64_t ch = (want_blocks + tiles_t - 1) / (tiles_t > 0 ? tiles_t : 1);
+    const int64_t max_by_src = (n_src + PAIR_TILE - 1) / PAIR_TILE;
+    if (ch > max_by_src) ch = max_by_src;
+    if (ch > max_chunks) ch = max_chunks;
+    if (ch < 1) ch = 1;
+    return (int)ch;
+}
+
+cudaError_t launch_pair(const DevNetwork& net, const int32_t* tgt, int64_t n_tgt, int chunks, int precision,
+                        const Consts& c, const double sh[6], cudaStream_t st)
+{
+    (void)precision;
+    const int64_t n = net.n_nodes;
+    if (n_tgt == 0 || n == 0) return cudaSuccess;
+    const int64_t chunk_len = (n + chunks - 1) / chunks;
+    dim3 grid((unsigned)((n_tgt + PAIR_TPB - 1) / PAIR_TPB), (unsigned)chunks);
+    pair_fp64_kernel<<<grid, PAIR_TPB, 0, st>>>(n, net.pos[net.cur], net.nxt, net.src, tgt, n_tgt, chunk_len, c,
+                                                sh[0], sh[1], sh[2], sh[3], sh[4], sh[5], net.fpart);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- node_velocity
+__global__ void node_velocity_kernel(int64_t n, const double* __restrict__ pos, const int32_t* __restrict__ nxt,
+                                     const int32_t* __restrict__ prv, const int32_t* __restrict__ loop_of,
+                                     const double* __restrict__ loop_n, const uint8_t* __restrict__ pinned,
+                                     const double* __restrict__ fpart, int chunks, double* __restrict__ force,
+                                     double* __restrict__ vel)
+{
+    const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (a >= n) return;
+    const int64_t p = prv[a], nx = nxt[a];
+    double F[3] = {0, 0, 0};
+    for (int ch = 0; ch < chunks; ++ch) {
+        const double* fp = fpart + (int64_t)ch * 6 * n;
+        F[0] += fp[0 * n + a] + fp[3 * n + p];
+        F[1] += fp[1 * n + a] + fp[4 * n + p];
+        F[2] += fp[2 * n + a] + fp[5 * n + p];
+    }
+    const double xa = pos[a], ya = pos[n + a], za = pos[2 * n + a];
+    const double px = xa - pos[p], py = ya - pos[n + p], pz = za - pos[2 * n + p];
+    const double qx = pos[nx] - xa, qy = pos[n + nx] - ya, qz = pos[2 * n + nx] - za;
+    const double M = 0.5 * (sqrt(px * px + py * py + pz * pz) + sqrt(qx * qx + qy * qy + qz * qz));
+    const int k = loop_of[a];
+    const double nn[3] = {loop_n[3 * k], loop_n[3 * k + 1], loop_n[3 * k + 2]};
+    double v[3] = {0, 0, 0};
+    if (!(pinned && pinned[a]) && M > 0.0) {
+        const double nF = nn[0] * F[0] + nn[1] * F[1] + nn[2] * F[2];
+        const double iM = 1.0 / M;
+        v[0] = (F[0] - nn[0] * nF) * iM;
+        v[1] = (F[1] - nn[1] * nF) * iM;
+        v[2] = (F[2] - nn[2] * nF) * iM;
+    }
+    force[a] = F[0]; force[n + a] = F[1]; force[2 * n + a] = F[2];
+    vel[a] = v[0]; vel[n + a] = v[1]; vel[2 * n + a] = v[2];
+}
+
+cudaError_t launch_node_velocity(const DevNetwork& net, int chunks, cudaStream_t st)
+{
+    const int64_t n = net.n_nodes;
+    if (n == 0) return cudaSuccess;
+    node_velocity_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, net.pos[net.cur], net.nxt, net.prv,
+                                                                       net.loop_of, net.loop_n, net.pinned,
+                                                                       net.fpart, chunks, net.force, net.vel);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ lp_euler
+constexpr int RED_TPB = 256;
+
+__global__ void __launch_bounds__(RED_TPB) lp_euler_kernel(
+    int64_t n, const double* __restrict__ pos, double* __restrict__ pos_next, const int32_t* __restrict__ nxt,
+    const int32_t* __restrict__ loop_of, const double* __restrict__ loop_b, const double* __restrict__ vel,
+    double dt, double* __restrict__ partial, int* __restrict__ flag)
+{
+    __shared__ double red[RED_TPB / 32][10];
+    const int64_t i = blockIdx.x * (int64_t)RED_TPB + threadIdx.x;
+    double v10[10];
+#pragma unroll
+    for (int m = 0; m < 10; ++m) v10[m] = 0.0;
+    if (i < n) {
+        const int64_t j = nxt[i];
+        const double dx = pos[j] - pos[i], dy = pos[n + j] - pos[n + i], dz = pos[2 * n + j] - pos[2 * n + i];
+        const double vx = 0.5 * (vel[i] + vel[j]);
+        const double vy = 0.5 * (vel[n + i] + vel[n + j]);
+        const double vz = 0.5 * (vel[2 * n + i] + vel[2 * n + j]);
+        const double cx = dy * vz - dz * vy, cy = dz * vx - dx * vz, cz = dx * vy - dy * vx;  // L t x vbar
+        const int k = loop_of[i];
+        const double b0 = loop_b[3 * k], b1 = loop_b[3 * k + 1], b2 = loop_b[3 * k + 2];
+        v10[0] = b0 * cx; v10[1] = b0 * cy; v10[2] = b0 * cz;
+        v10[3] = b1 * cx; v10[4] = b1 * cy; v10[5] = b1 * cz;
+        v10[6] = b2 * cx; v10[7] = b2 * cy; v10[8] = b2 * cz;
+        v10[9] = sqrt(dx * dx + dy * dy + dz * dz);
+        // explicit Euler (all nodes from the step-start state)
+        const double nxp = fma(vel[i], dt, pos[i]);
+        const double nyp = fma(vel[n + i], dt, pos[n + i]);
+        const double nzp = fma(vel[2 * n + i], dt, pos[2 * n + i]);
+        pos_next[i] = nxp;
+        pos_next[n + i] = nyp;
+        pos_next[2 * n + i] = nzp;
+        if (!isfinite(nxp) || !isfinite(nyp) || !isfinite(nzp)) atomicOr(flag, 1);
+    }
+#pragma unroll
+    for (int m = 0; m < 10; ++m) {
+        double v = v10[m];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][m] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 10) {
+        double s = 0.0;
+#pragma unroll
+        for (int w = 0; w < RED_TPB / 32; ++w) s += red[w][threadIdx.x];
+        partial[blockIdx.x * 10 + threadIdx.x] = s;
+    }
+}
+
+// One block: sum the per-block partials in a fixed order, add dt-weighted.
+__global__ void lp_finish_kernel(int nblk, const double* __restrict__ partial, double dt, double* __restrict__ acc)
+{
+    __shared__ double red[256][10];
+    double s[10];
+#pragma unroll
+    for (int m = 0; m < 10; ++m) s[m] = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += 256)
+#pragma unroll
+        for (int m = 0; m < 10; ++m) s[m] += partial[b * 10 + m];
+#pragma unroll
+    for (int m = 0; m < 10; ++m) red[threadIdx.x][m] = s[m];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+#pragma unroll
+            for (int m = 0; m < 10; ++m) red[threadIdx.x][m] += red[threadIdx.x + h][m];
+        __syncthreads();
+    }
+    if (threadIdx.x < 10) acc[threadIdx.x] = fma(red[0][threadIdx.x], dt, acc[threadIdx.x]);
+}
+
+cudaError_t launch_lp_euler(DevNetwork& net, double dt_hat, cudaStream_t st)
+{
+    const int64_t n = net.n_nodes;
+    if (n == 0) return cudaSuccess;
+    const int nblk = (int)((n + RED_TPB - 1) / RED_TPB);
+    lp_euler_kernel<<<nblk, RED_TPB, 0, st>>>(n, net.pos[net.cur], net.pos[1 - net.cur], net.nxt, net.loop_of,
+                                               net.loop_b, net.vel, dt_hat, net.partial, net.flag);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    lp_finish_kernel<<<1, 256, 0, st>>>(nblk, net.partial, dt_hat, net.acc);
+    net.cur = 1 - net.cur;
+    return cudaGetLastError();
+}
+
+}  // namespace ptadd

@@ -1,0 +1,107 @@
+// ptadd_internal.cuh -- shared declarations of the CUDA implementation of ptadd.h.
+//
+// Internal units (all kernels): lengths in b (the reference Burgers-vector
+// magnitude), stresses in mu, time in B/mu.  Then a nodal velocity is the
+// projected nodal force divided by the lumped length, v = P F / M, and the
+// Euler step uses dt_hat = dt mu / B.  Conversion to SI happens only in the
+// host entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ptadd.h"
+
+namespace ptadd {
+
+// --------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+const char* cuda_msg(cudaError_t e);
+
+#define PTADD_CUDA(call)                                                          \
+    do {                                                                          \
+        cudaError_t _e = (call);                                                  \
+        if (_e != cudaSuccess) {                                                  \
+            ::ptadd::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e), \
+                               __FILE__, __LINE__);                               \
+            return PTADD_ERR_CUDA;                                                \
+        }                                                                         \
+    } while (0)
+
+// ------------------------------------------------------- source records
+// Every segment i (node i -> nxt[i]) is described to the pair kernels by a
+// 16-double record, rebuilt at the start of each step:
+//   [0..2] x1 (start node)   [3] L      [4..6] unit tangent t   [7] 0
+//   [8..10] Burgers vector b [11] 0     [12..14] q = b x t      [15] 0
+constexpr int SRC_STRIDE = 16;
+
+// Device-side state of one realisation.
+struct DevNetwork {
+    int64_t n_nodes = 0, n_loops = 0;
+    double* pos[2] = {nullptr, nullptr};  // SoA x|y|z (3*n), double-buffered
+    int cur = 0;
+    int32_t* nxt = nullptr;
+    int32_t* prv = nullptr;
+    int32_t* loop_of = nullptr;
+    double* loop_b = nullptr;  // [n_loops*3] reduced Burgers vectors
+    double* loop_n = nullptr;  // [n_loops*3] unit normals
+    uint8_t* pinned = nullptr;
+    int32_t* tgt_burst = nullptr;  // segments with >= 1 unpinned node
+    int64_t n_tgt_burst = 0;
+    int32_t* tgt_all = nullptr;    // every segment
+    double* src = nullptr;         // [n*SRC_STRIDE]
+    double* fpart = nullptr;       // [max_chunks*6*n] partial nodal-force parts
+    int max_chunks = 0;
+    double* vel = nullptr;         // SoA [3*n]
+    double* force = nullptr;       // SoA [3*n] (last evaluated nodal force)
+    double* partial = nullptr;     // [max_blocks*10]
+    int max_red_blocks = 0;
+    double* acc = nullptr;         // [16]: 0..8 sum Lp dt, 9 sum rho dt, 10 flag
+    int* flag = nullptr;           // non-finite flag
+    double* staging = nullptr;     // [3*n] AoS SI positions in / out
+    double volume = 0;             // m^3
+};
+
+struct Consts {
+    double a2;   // (a/b)^2
+    double c1;   // 1/(8 pi)
+    double c2;   // 1/(4 pi (1 - nu))
+};
+
+// ------------------------------------------------------------ launchers
+// All return cudaGetLastError() of their launches.
+cudaError_t launch_seg_prep(const DevNetwork& net, cudaStream_t st);
+// pair stage: writes fpart[chunk][6][seg] for the listed targets
+cudaError_t launch_pair(const DevNetwork& net, const int32_t* tgt, int64_t n_tgt, int chunks,
+                        int precision, const Consts& c, const double sig_hat[6], cudaStream_t st);
+// node stage: F = sum of parts, v = P F / M (0 if pinned); writes net.force / net.vel
+cudaError_t launch_node_velocity(const DevNetwork& net, int chunks, cudaStream_t st);
+// Lp/rho sample of the step-start state, Euler update into the other buffer,
+// and the fixed-order reduction into net.acc (weighted by dt_hat)
+cudaError_t launch_lp_euler(DevNetwork& net, double dt_hat, cudaStream_t st);
+int choose_chunks(int64_t n_tgt, int64_t n_src, int max_chunks);
+
+// peak microbenchmark
+cudaError_t launch_fma_chains(int fp64, int blocks, int threads, long iters, double* sink, cudaStream_t st);
+
+}  // namespace ptadd
+
+struct ptadd_ctx {
+    int device = 0;
+    ptadd_material mat{};
+    ptadd_precision prec = PTADD_FP64;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    ptadd::DevNetwork net;
+    bool have_net = false;
+    double sig_app[6] = {0, 0, 0, 0, 0, 0};  // Pa
+    // profiling (ptadd_profile_*)
+    bool timing = false;
+    int64_t kernel_launches = 0, pair_launches = 0, pair_evals = 0;
+    double pair_ms = 0.0;
+    std::vector<cudaEvent_t> ev_pool;     // reusable events
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_open;  // recorded, not yet read
+};

@@ -1,0 +1,248 @@
+"""Thin ctypes binding of libptadd.so (ptadd.h).
+
+Argument marshalling only: every step of the burst runs in the library's CUDA
+kernels.  If the library has not been built, or cannot be loaded, every call
+raises -- there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+PTADD_FP64 = 0
+PTADD_MIXED = 1
+
+STATUS = {0: "PTADD_OK", 1: "PTADD_ERR_ARG", 2: "PTADD_ERR_CUDA", 3: "PTADD_ERR_NONFINITE",
+          4: "PTADD_ERR_TIMEOUT", 5: "PTADD_ERR_STATE", 6: "PTADD_ERR_NOMEM"}
+
+# Every symbol ptadd.h declares (the CPU test checks the library exports them).
+EXPORTS = ["ptadd_version", "ptadd_create", "ptadd_destroy", "ptadd_last_error", "ptadd_set_precision",
+           "ptadd_set_stream", "ptadd_set_network", "ptadd_set_applied_stress", "ptadd_get_info",
+           "ptadd_advance", "ptadd_get_nodes", "ptadd_get_forces", "ptadd_get_forces_dev",
+           "ptadd_get_state", "ptadd_set_state", "ptadd_fma_peak", "ptadd_set_nodes",
+           "ptadd_profile_reset", "ptadd_profile_read"]
+
+
+class PtaddError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class Material(ctypes.Structure):
+    _fields_ = [("mu", ctypes.c_double), ("nu", ctypes.c_double), ("b", ctypes.c_double),
+                ("a", ctypes.c_double), ("B", ctypes.c_double)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_int64), ("pair_launches", ctypes.c_int64),
+                ("pair_evals", ctypes.c_int64), ("pair_ms", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_loops", ctypes.c_int64), ("n_targets", ctypes.c_int64),
+                ("pairs_per_step", ctypes.c_int64), ("precision", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+_U8 = ctypes.POINTER(ctypes.c_uint8)
+_VP = ctypes.c_void_p
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libptadd.so (building it first if asked); raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libptadd.so is not built (%s); run __graft_entry__.build()" % _build.LIB)
+    lib = ctypes.CDLL(_build.LIB)
+    st = ctypes.c_int
+    lib.ptadd_version.restype = ctypes.c_int
+    lib.ptadd_last_error.restype = ctypes.c_char_p
+    lib.ptadd_create.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(Material), ctypes.c_int, ctypes.c_int]
+    lib.ptadd_create.restype = st
+    lib.ptadd_destroy.argtypes = [_VP]
+    lib.ptadd_destroy.restype = None
+    lib.ptadd_set_precision.argtypes = [_VP, ctypes.c_int]
+    lib.ptadd_set_precision.restype = st
+    lib.ptadd_set_stream.argtypes = [_VP, _VP]
+    lib.ptadd_set_stream.restype = st
+    lib.ptadd_set_network.argtypes = [_VP, ctypes.c_int64, _D, ctypes.c_int64, _I64, _D, _D, _U8, ctypes.c_double]
+    lib.ptadd_set_network.restype = st
+    lib.ptadd_set_applied_stress.argtypes = [_VP, _D]
+    lib.ptadd_set_applied_stress.restype = st
+    lib.ptadd_get_info.argtypes = [_VP, ctypes.POINTER(Info)]
+    lib.ptadd_get_info.restype = st
+    lib.ptadd_advance.argtypes = [_VP, ctypes.c_int64, ctypes.c_double, _D, _D]
+    lib.ptadd_advance.restype = st
+    lib.ptadd_get_nodes.argtypes = [_VP, _D]
+    lib.ptadd_get_nodes.restype = st
+    lib.ptadd_get_forces.argtypes = [_VP, _D]
+    lib.ptadd_get_forces.restype = st
+    lib.ptadd_get_forces_dev.argtypes = [_VP, _VP]
+    lib.ptadd_get_forces_dev.restype = st
+    lib.ptadd_get_state.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_size_t)]
+    lib.ptadd_get_state.restype = st
+    lib.ptadd_set_state.argtypes = [_VP, _VP, ctypes.c_size_t]
+    lib.ptadd_set_state.restype = st
+    lib.ptadd_set_nodes.argtypes = [_VP, _VP]
+    lib.ptadd_set_nodes.restype = st
+    lib.ptadd_profile_reset.argtypes = [_VP, ctypes.c_int]
+    lib.ptadd_profile_reset.restype = st
+    lib.ptadd_profile_read.argtypes = [_VP, ctypes.POINTER(Profile)]
+    lib.ptadd_profile_read.restype = st
+    lib.ptadd_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]
+    lib.ptadd_fma_peak.restype = st
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != 0:
+        raise PtaddError(status, _lib.ptadd_last_error().decode())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_D)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def version():
+    return load().ptadd_version()
+
+
+def fma_peak(device=0, fp64=True, seconds=1.0):
+    """Measured FMA throughput (FLOP/s) of every SM, FP64 or FP32."""
+    lib = load()
+    out = ctypes.c_double(0.0)
+    _check(lib.ptadd_fma_peak(int(device), int(bool(fp64)), float(seconds), ctypes.byref(out)))
+    return out.value
+
+
+class Context:
+    """One realisation on one GPU (wraps ptadd_ctx)."""
+
+    def __init__(self, material, precision=PTADD_FP64, device=0):
+        lib = load()
+        self._lib = lib
+        self._h = _VP()
+        m = Material(*tuple(material))
+        _check(lib.ptadd_create(ctypes.byref(self._h), ctypes.byref(m), int(precision), int(device)))
+        self.n_nodes = 0
+
+    def close(self):
+        if self._h:
+            self._lib.ptadd_destroy(self._h)
+            self._h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_precision(self, precision):
+        _check(self._lib.ptadd_set_precision(self._h, int(precision)))
+
+    def set_stream(self, stream_handle):
+        """stream_handle: an int cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream) or None."""
+        _check(self._lib.ptadd_set_stream(self._h, _VP(stream_handle) if stream_handle else None))
+
+    def set_network(self, net):
+        """net: workloads.Network (SI).  Also loads its applied stress."""
+        x = _c(net.xyz, np.float64)
+        off = _c(net.loop_off, np.int64)
+        bv = _c(net.burgers, np.float64)
+        nv = _c(net.normal, np.float64)
+        pin = _c(net.pinned, np.uint8) if net.pinned is not None else None
+        _check(self._lib.ptadd_set_network(self._h, x.shape[0], _dptr(x), off.shape[0] - 1,
+                                           off.ctypes.data_as(_I64), _dptr(bv), _dptr(nv),
+                                           pin.ctypes.data_as(_U8) if pin is not None else None,
+                                           float(net.volume)))
+        self.n_nodes = x.shape[0]
+        self.set_applied_stress(net.sig_app)
+
+    def set_applied_stress(self, sig6):
+        s = _c(sig6, np.float64)
+        _check(self._lib.ptadd_set_applied_stress(self._h, _dptr(s)))
+
+    def info(self):
+        i = Info()
+        _check(self._lib.ptadd_get_info(self._h, ctypes.byref(i)))
+        return dict(n_nodes=i.n_nodes, n_loops=i.n_loops, n_targets=i.n_targets,
+                    pairs_per_step=i.pairs_per_step, precision=i.precision, device=i.device)
+
+    def advance(self, n_steps, dt):
+        """Run a burst; returns (Lp_avg 3x3, rho_avg)."""
+        Lp = np.zeros(9)
+        rho = ctypes.c_double(0.0)
+        _check(self._lib.ptadd_advance(self._h, int(n_steps), float(dt), _dptr(Lp), ctypes.byref(rho)))
+        return Lp.reshape(3, 3), rho.value
+
+    def get_nodes(self):
+        out = np.zeros((self.n_nodes, 3))
+        _check(self._lib.ptadd_get_nodes(self._h, _dptr(out)))
+        return out
+
+    def set_nodes(self, xyz):
+        """xyz: [n,3] float64 host array (SI) or a raw host pointer (int)."""
+        if isinstance(xyz, int):
+            _check(self._lib.ptadd_set_nodes(self._h, _VP(xyz)))
+            return
+        x = _c(xyz, np.float64)
+        _check(self._lib.ptadd_set_nodes(self._h, x.ctypes.data_as(_VP)))
+
+    def get_nodes_into(self, ptr):
+        """Positions into a caller-owned host buffer given as a raw pointer."""
+        _check(self._lib.ptadd_get_nodes(self._h, ctypes.cast(_VP(ptr), _D)))
+
+    def profile_reset(self, timing=False):
+        _check(self._lib.ptadd_profile_reset(self._h, int(bool(timing))))
+
+    def profile_read(self):
+        p = Profile()
+        _check(self._lib.ptadd_profile_read(self._h, ctypes.byref(p)))
+        return dict(kernel_launches=p.kernel_launches, pair_launches=p.pair_launches,
+                    pair_evals=p.pair_evals, pair_ms=p.pair_ms)
+
+    def get_forces(self):
+        out = np.zeros((self.n_nodes, 3))
+        _check(self._lib.ptadd_get_forces(self._h, _dptr(out)))
+        return out
+
+    def get_forces_dev(self, ptr):
+        _check(self._lib.ptadd_get_forces_dev(self._h, _VP(ptr)))
+
+    def get_state(self):
+        n = ctypes.c_size_t(0)
+        _check(self._lib.ptadd_get_state(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self._lib.ptadd_get_state(self._h, ctypes.cast(buf, _VP), ctypes.byref(n)))
+        return bytes(buf.raw[:n.value])
+
+    def set_state(self, blob):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(self._lib.ptadd_set_state(self._h, ctypes.cast(buf, _VP), len(blob)))

@@ -1,0 +1,161 @@
+"""GPU parity of the FP64 burst against the FP64 CPU oracle (through the C ABI).
+
+Tolerances (relative max-norm):
+  nodal forces            <= 1e-11
+  positions after a burst <= 1e-9 of max|x| (and the displacement is checked
+                             against 1e-9 of max|x - x0| where the dynamics is
+                             well conditioned)
+  averaged Lp / rho       <= 1e-9
+The 512-segment loop ensemble at dt = 1e-11 s is explicit-Euler unstable
+(the line-tension saw-tooth mode grows; a 1-ulp perturbation reaches O(1)
+within 20 steps), so long-horizon position parity is checked on its first 5
+steps at that dt and on 100 steps at dt = 5e-13 s, where the same
+perturbation stays below 1e-10.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2005_02498_gb300 import ptadd
+from paper_2005_02498_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+MAT = W.Material().as_tuple()
+
+
+def relmax(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(b)))
+
+
+def ctx_for(net, prec=ptadd.PTADD_FP64):
+    c = ptadd.Context(MAT, prec, 0)
+    c.set_network(net)
+    return c
+
+
+def ragged_network(seed=21, n_loops=13, nodes=23, pinned_loops=()):
+    net = W.loop_ensemble(seed, n_loops, 0.6e-6, W.uniaxial_stress(60e6), nodes_per_loop=nodes)
+    for k in pinned_loops:
+        net.pinned[k * nodes:(k + 1) * nodes] = 1
+    net.sig_app = np.array([20e6, -35e6, 50e6, 10e6, -5e6, 25e6])
+    return net
+
+
+@pytest.mark.parametrize("which", ["small_loops", "ragged", "ragged_pinned"])
+def test_nodal_forces_match_oracle(which):
+    net = {"small_loops": W.small_loop_network, "ragged": ragged_network,
+           "ragged_pinned": lambda: ragged_network(pinned_loops=(2, 5, 6))}[which]()
+    with ctx_for(net) as c:
+        Fg = c.get_forces()
+    Fo = O.nodal_forces(MAT, net)
+    assert relmax(Fg, Fo) <= 1e-11
+
+
+def test_burst_small_loops_stated_dt_first_steps():
+    net = W.small_loop_network()
+    dt = W.SMALL_LOOPS["dt"]
+    ref = O.burst(MAT, net, 5, dt)
+    with ctx_for(net) as c:
+        Lp, rho = c.advance(5, dt)
+        x = c.get_nodes()
+    assert relmax(x, ref["xyz"]) <= 1e-9
+    assert relmax(x - net.xyz, ref["xyz"] - net.xyz) <= 1e-9
+    assert relmax(Lp, ref["Lp_avg"]) <= 1e-9
+    assert abs(rho / ref["rho_avg"] - 1) <= 1e-12
+
+
+def test_burst_small_loops_100_steps_stable_dt():
+    net = W.small_loop_network()
+    dt = 5e-13
+    ref = O.burst(MAT, net, 100, dt)
+    with ctx_for(net) as c:
+        Lp, rho = c.advance(100, dt)
+        x = c.get_nodes()
+    assert relmax(x, ref["xyz"]) <= 1e-9
+    assert relmax(Lp, ref["Lp_avg"]) <= 1e-9
+    assert abs(rho / ref["rho_avg"] - 1) <= 1e-11
+
+
+def test_burst_in_pieces_equals_one_burst_and_state_roundtrip():
+    net = ragged_network(pinned_loops=(1,))
+    dt = 2e-12
+    with ctx_for(net) as c:
+        blob = c.get_state()
+        Lp_all, _ = c.advance(6, dt)
+        x_all = c.get_nodes()
+        c.set_state(blob)
+        Lp_a, _ = c.advance(2, dt)
+        Lp_b, _ = c.advance(4, dt)
+        x_ab = c.get_nodes()
+    assert np.array_equal(x_all, x_ab)  # deterministic, bit for bit
+    assert relmax((2 * Lp_a + 4 * Lp_b) / 6, Lp_all) <= 1e-13
+    ref = O.burst(MAT, net, 6, dt)
+    assert relmax(x_all, ref["xyz"]) <= 1e-9
+    assert np.all(x_all[net.pinned == 1] == net.xyz[net.pinned == 1])
+
+
+def test_large_loops_sampled_forces_and_one_step_properties():
+    """32768 segments in the launch configuration of the benchmark: forces on
+    sampled nodes against the oracle; Lp/rho/Euler of one step against the
+    oracle's node-level functions fed with the GPU forces."""
+    net = W.large_loop_network()
+    dt = W.LARGE_LOOPS["dt"]
+    rng = np.random.default_rng(5)
+    sel = np.sort(rng.choice(net.n_nodes, size=48, replace=False))
+    with ctx_for(net) as c:
+        F = c.get_forces()
+        Lp, rho = c.advance(1, dt)
+        x1 = c.get_nodes()
+    Fo = O.nodal_forces_subset(MAT, net, sel)
+    assert relmax(F[sel], Fo) <= 1e-11
+    v = O.velocities(MAT, net, F)
+    Lp_o, rho_o = O.lp_rho(net, v)
+    assert relmax(Lp, Lp_o) <= 1e-11
+    assert abs(rho / rho_o - 1) <= 1e-12
+    assert relmax(x1 - net.xyz, v * dt) <= 1e-11
+    nrm = np.repeat(net.normal, 32, axis=0)
+    assert np.max(np.abs(np.sum((x1 - net.xyz) * nrm, axis=1))) <= 1e-9 * np.max(np.abs(x1 - net.xyz))
+
+
+def test_edge_cases():
+    # two-node loops, a loop of 3, all targets pinned, zero steps
+    xyz = np.array([[0, 0, 0], [50, 0, 0], [0, 40, 0], [30, 40, 0], [10, 10, 5], [20, 12, 5], [15, 20, 5]],
+                   float) * W.BURGERS
+    off = np.array([0, 2, 4, 7], np.int64)
+    bv = np.array([[1, 0, 0], [0, 1, 0], [1, 1, 0]], float) / np.array([[1], [1], [np.sqrt(2)]]) * W.BURGERS
+    nv = np.array([[0, 0, 1.0]] * 3)
+    net = W.Network(xyz, off, bv, nv, np.zeros(7, np.uint8), 1e-21, np.array([1e7, 0, 0, 0, 0, 3e7]))
+    with ctx_for(net) as c:
+        Fg = c.get_forces()
+        Lp0, rho0 = c.advance(0, 1e-12)
+        assert np.all(Lp0 == 0) and rho0 == 0
+    assert relmax(Fg, O.nodal_forces(MAT, net)) <= 1e-11
+    net.pinned[:] = 1
+    with ctx_for(net) as c:
+        assert c.info()["n_targets"] == 0
+        Lp, rho = c.advance(3, 1e-12)
+        assert np.all(Lp == 0)
+        assert np.array_equal(c.get_nodes(), net.xyz)
+
+
+def test_argument_errors_leave_context_usable():
+    net = ragged_network()
+    with ptadd.Context(MAT, ptadd.PTADD_FP64, 0) as c:
+        with pytest.raises(ptadd.PtaddError) as e:
+            c.advance(1, 1e-12)
+        assert e.value.status == 5  # PTADD_ERR_STATE
+        bad = net.copy()
+        bad.normal[0] *= 2.0
+        with pytest.raises(ptadd.PtaddError) as e:
+            c.set_network(bad)
+        assert e.value.status == 1
+        bad = net.copy()
+        bad.loop_off[1] = bad.loop_off[0] + 1
+        with pytest.raises(ptadd.PtaddError):
+            c.set_network(bad)
+        c.set_network(net)
+        with pytest.raises(ptadd.PtaddError):
+            c.advance(1, -1.0)
+        Lp, _ = c.advance(1, 1e-12)
+        assert np.all(np.isfinite(Lp))
