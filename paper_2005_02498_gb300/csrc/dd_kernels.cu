@@ -86,10 +86,11 @@ __global__ void __launch_bounds__(PAIR_TPB) pair_fp64_kernel(
     double xq[4][3];
 #pragma unroll
     for (int qp = 0; qp < 4; ++qp) {
+        // x_q = x_a + xi_q (x_b - x_a), rounded as written (no contraction)
         const double xi = gl4_xi(qp);
-        xq[qp][0] = fma(xi, Dx, xa);
-        xq[qp][1] = fma(xi, Dy, ya);
-        xq[qp][2] = fma(xi, Dz, za);
+        xq[qp][0] = __dadd_rn(xa, __dmul_rn(xi, Dx));
+        xq[qp][1] = __dadd_rn(ya, __dmul_rn(xi, Dy));
+        xq[qp][2] = __dadd_rn(za, __dmul_rn(xi, Dz));
     }
     double acc[4][3];
 #pragma unroll
@@ -201,10 +202,9 @@ __global__ void node_velocity_kernel(int64_t n, const double* __restrict__ pos, 
     double v[3] = {0, 0, 0};
     if (!(pinned && pinned[a]) && M > 0.0) {
         const double nF = nn[0] * F[0] + nn[1] * F[1] + nn[2] * F[2];
-        const double iM = 1.0 / M;
-        v[0] = (F[0] - nn[0] * nF) * iM;
-        v[1] = (F[1] - nn[1] * nF) * iM;
-        v[2] = (F[2] - nn[2] * nF) * iM;
+        v[0] = (F[0] - nn[0] * nF) / M;
+        v[1] = (F[1] - nn[1] * nF) / M;
+        v[2] = (F[2] - nn[2] * nF) / M;
     }
     force[a] = F[0]; force[n + a] = F[1]; force[2 * n + a] = F[2];
     vel[a] = v[0]; vel[n + a] = v[1]; vel[2 * n + a] = v[2];
@@ -247,9 +247,9 @@ __global__ void __launch_bounds__(RED_TPB) lp_euler_kernel(
         v10[6] = b2 * cx; v10[7] = b2 * cy; v10[8] = b2 * cz;
         v10[9] = sqrt(dx * dx + dy * dy + dz * dz);
         // explicit Euler (all nodes from the step-start state)
-        const double nxp = fma(vel[i], dt, pos[i]);
-        const double nyp = fma(vel[n + i], dt, pos[n + i]);
-        const double nzp = fma(vel[2 * n + i], dt, pos[2 * n + i]);
+        const double nxp = __dadd_rn(pos[i], __dmul_rn(vel[i], dt));
+        const double nyp = __dadd_rn(pos[n + i], __dmul_rn(vel[n + i], dt));
+        const double nzp = __dadd_rn(pos[2 * n + i], __dmul_rn(vel[2 * n + i], dt));
         pos_next[i] = nxp;
         pos_next[n + i] = nyp;
         pos_next[2 * n + i] = nzp;

@@ -52,10 +52,11 @@ static void free_network(DevNetwork& n)
     n = DevNetwork{};
 }
 
-static Consts make_consts(const ptadd_material& m)
+static Consts make_consts(const ptadd_ctx* ctx)
 {
+    const ptadd_material& m = ctx->mat;
     Consts c;
-    const double r = m.a / m.b;
+    const double r = m.a / ctx->len_unit;
     c.a2 = r * r;
     c.c1 = 1.0 / (8.0 * M_PI);
     c.c2 = 1.0 / (4.0 * M_PI * (1.0 - m.nu));
@@ -94,6 +95,8 @@ ptadd_status ptadd_create(ptadd_ctx** out, const ptadd_material* mat, ptadd_prec
     if (!c) return arg_error("host allocation failed");
     c->device = device;
     c->mat = *mat;
+    c->len_exp = (int)lround(log2(mat->b));
+    c->len_unit = ldexp(1.0, c->len_exp);
     c->prec = prec;
     cudaError_t e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
@@ -179,10 +182,11 @@ ptadd_status ptadd_set_network(ptadd_ctx* ctx, int64_t n_nodes, const double* xy
     std::vector<double> pos(3 * n);
     std::vector<int32_t> nxt(n), prv(n), lof(n), tb, ta(n);
     std::vector<double> lb(3 * n_loops), ln(3 * n_loops);
+    const int ie = -ctx->len_exp;  // exact scaling to internal units
     for (int64_t i = 0; i < n; ++i) {
-        pos[i] = xyz[3 * i] / b;
-        pos[n + i] = xyz[3 * i + 1] / b;
-        pos[2 * n + i] = xyz[3 * i + 2] / b;
+        pos[i] = ldexp(xyz[3 * i], ie);
+        pos[n + i] = ldexp(xyz[3 * i + 1], ie);
+        pos[2 * n + i] = ldexp(xyz[3 * i + 2], ie);
     }
     for (int64_t k = 0; k < n_loops; ++k) {
         const int64_t s = loop_off[k], e = loop_off[k + 1];
@@ -192,7 +196,7 @@ ptadd_status ptadd_set_network(ptadd_ctx* ctx, int64_t n_nodes, const double* xy
             lof[i] = (int32_t)k;
         }
         for (int c = 0; c < 3; ++c) {
-            lb[3 * k + c] = burgers[3 * k + c] / b;
+            lb[3 * k + c] = burgers[3 * k + c] / ctx->len_unit;
             ln[3 * k + c] = normal[3 * k + c];
         }
     }
@@ -299,7 +303,7 @@ static ptadd_status take_events(ptadd_ctx* ctx, std::pair<cudaEvent_t, cudaEvent
 static ptadd_status eval_forces(ptadd_ctx* ctx, const int32_t* tgt, int64_t n_tgt)
 {
     DevNetwork& net = ctx->net;
-    const Consts c = make_consts(ctx->mat);
+    const Consts c = make_consts(ctx);
     double sh[6];
     for (int k = 0; k < 6; ++k) sh[k] = ctx->sig_app[k] / ctx->mat.mu;
     const int chunks = choose_chunks(n_tgt, net.n_nodes, net.max_chunks);
@@ -371,10 +375,10 @@ ptadd_status ptadd_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, double Lp
         if (st != PTADD_OK) return st;
     }
     // Eq. 2.5 with internal sums: R = (sum Lambda_hat dt_hat) / (sum dt_hat), then SI scale
-    const double b = ctx->mat.b;
+    const double l = ctx->len_unit;
     const double St = dt_hat * (double)n_steps;
-    const double lp_scale = b * b * b * ctx->mat.mu / (ctx->mat.B * net.volume);
-    const double rho_scale = b / net.volume;
+    const double lp_scale = l * l * l * ctx->mat.mu / (ctx->mat.B * net.volume);
+    const double rho_scale = l / net.volume;
     bool finite = (flag == 0);
     for (int m = 0; m < 10; ++m) finite = finite && isfinite(acc[m]);
     if (Lp_avg)
@@ -423,7 +427,7 @@ ptadd_status ptadd_get_nodes(ptadd_ctx* ctx, double* xyz)
         return PTADD_ERR_STATE;
     }
     if (!xyz) return arg_error("xyz is NULL");
-    return read_soa(ctx, ctx->net.pos[ctx->net.cur], ctx->mat.b, xyz);
+    return read_soa(ctx, ctx->net.pos[ctx->net.cur], ctx->len_unit, xyz);
 }
 
 ptadd_status ptadd_set_nodes(ptadd_ctx* ctx, const double* xyz)
@@ -436,7 +440,7 @@ ptadd_status ptadd_set_nodes(ptadd_ctx* ctx, const double* xyz)
     if (!xyz) return arg_error("xyz is NULL");
     const int64_t n = ctx->net.n_nodes;
     PTADD_CUDA(cudaMemcpyAsync(ctx->net.staging, xyz, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
-    aos_to_soa_scaled<<<(unsigned)((3 * n + 255) / 256), 256, 0, ctx->stream>>>(n, ctx->net.staging, 1.0 / ctx->mat.b,
+    aos_to_soa_scaled<<<(unsigned)((3 * n + 255) / 256), 256, 0, ctx->stream>>>(n, ctx->net.staging, 1.0 / ctx->len_unit,
                                                                                 ctx->net.pos[ctx->net.cur]);
     PTADD_CUDA(cudaGetLastError());
     ctx->kernel_launches += 1;
@@ -481,7 +485,7 @@ ptadd_status ptadd_get_forces(ptadd_ctx* ctx, double* F)
     if (!F) return arg_error("F is NULL");
     ptadd_status st = eval_forces(ctx, ctx->net.tgt_all, ctx->net.n_nodes);
     if (st != PTADD_OK) return st;
-    return read_soa(ctx, ctx->net.force, ctx->mat.mu * ctx->mat.b * ctx->mat.b, F);
+    return read_soa(ctx, ctx->net.force, ctx->mat.mu * ctx->len_unit * ctx->len_unit, F);
 }
 
 ptadd_status ptadd_get_forces_dev(ptadd_ctx* ctx, double* F_dev)
@@ -496,7 +500,7 @@ ptadd_status ptadd_get_forces_dev(ptadd_ctx* ctx, double* F_dev)
     if (st != PTADD_OK) return st;
     const int64_t n = ctx->net.n_nodes;
     soa_to_aos_scaled<<<(unsigned)((3 * n + 255) / 256), 256, 0, ctx->stream>>>(
-        n, ctx->net.force, ctx->mat.mu * ctx->mat.b * ctx->mat.b, F_dev);
+        n, ctx->net.force, ctx->mat.mu * ctx->len_unit * ctx->len_unit, F_dev);
     PTADD_CUDA(cudaGetLastError());
     ctx->kernel_launches += 1;
     return PTADD_OK;

@@ -1,10 +1,12 @@
 // ptadd_internal.cuh -- shared declarations of the CUDA implementation of ptadd.h.
 //
-// Internal units (all kernels): lengths in b (the reference Burgers-vector
-// magnitude), stresses in mu, time in B/mu.  Then a nodal velocity is the
-// projected nodal force divided by the lumped length, v = P F / M, and the
-// Euler step uses dt_hat = dt mu / B.  Conversion to SI happens only in the
-// host entry points.
+// Internal units (all kernels): lengths in l = 2^e metres with e the integer
+// nearest log2(b) (so converting positions is an exact scaling: the kernels
+// see the caller's geometry without rounding -- the nodal forces of a loop
+// network change by ~3e-11 relative under a 1-ulp change of the positions),
+// stresses in mu, time in B/mu.  Then a nodal velocity is the projected nodal
+// force divided by the lumped length, v = P F / M, and the Euler step uses
+// dt_hat = dt mu / B.  Conversion to SI happens only in the host entry points.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -46,7 +48,7 @@ struct DevNetwork {
     int32_t* nxt = nullptr;
     int32_t* prv = nullptr;
     int32_t* loop_of = nullptr;
-    double* loop_b = nullptr;  // [n_loops*3] reduced Burgers vectors
+    double* loop_b = nullptr;  // [n_loops*3] Burgers vectors in units of l
     double* loop_n = nullptr;  // [n_loops*3] unit normals
     uint8_t* pinned = nullptr;
     int32_t* tgt_burst = nullptr;  // segments with >= 1 unpinned node
@@ -66,7 +68,7 @@ struct DevNetwork {
 };
 
 struct Consts {
-    double a2;   // (a/b)^2
+    double a2;   // (a/l)^2
     double c1;   // 1/(8 pi)
     double c2;   // 1/(4 pi (1 - nu))
 };
@@ -92,6 +94,8 @@ cudaError_t launch_fma_chains(int fp64, int blocks, int threads, long iters, dou
 struct ptadd_ctx {
     int device = 0;
     ptadd_material mat{};
+    int len_exp = 0;       // internal length unit l = 2^len_exp m
+    double len_unit = 1.0; // l in metres
     ptadd_precision prec = PTADD_FP64;
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;

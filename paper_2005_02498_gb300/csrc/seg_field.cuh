@@ -148,14 +148,17 @@ __device__ __forceinline__ void seg_sigma_b(T R0x, T R0y, T R0z, const T t[3], T
     s[2] = fma(cRxb, Xz, fma(cq, q[2], fma(cRp, Rpz, fma(ct, t[2], fma(cb, bt[2], s[2])))));
 }
 
-// Gauss-Legendre points and weights on [0,1] (textbook 4-point rule).
+// Gauss-Legendre rule on [0,1]: the textbook 4-point abscissae z and
+// weights W on [-1,1] mapped by xi = (1 + z)/2, w = W/2.
 __device__ __forceinline__ double gl4_xi(int qp)
 {
-    return qp == 0 ? 0.0694318442029737 : qp == 1 ? 0.3300094782075719 : qp == 2 ? 0.6699905217924281 : 0.9305681557970263;
+    constexpr double z0 = 0.8611363115940526, z1 = 0.3399810435848563;
+    return qp == 0 ? 0.5 * (1.0 - z0) : qp == 1 ? 0.5 * (1.0 - z1) : qp == 2 ? 0.5 * (1.0 + z1) : 0.5 * (1.0 + z0);
 }
 __device__ __forceinline__ double gl4_w(int qp)
 {
-    return (qp == 0 || qp == 3) ? 0.1739274225687269 : 0.3260725774312731;
+    constexpr double W0 = 0.3478548451374538, W1 = 0.6521451548625461;
+    return (qp == 0 || qp == 3) ? 0.5 * W0 : 0.5 * W1;
 }
 
 }  // namespace ptadd

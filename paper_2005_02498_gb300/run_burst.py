@@ -19,14 +19,15 @@ from . import workloads as W
 
 def main(argv=None):
     p = argparse.ArgumentParser()
-    p.add_argument("--workload", default="large", choices=["small", "large"])
+    p.add_argument("--workload", default="large", choices=["small", "medium", "large"])
     p.add_argument("--steps", type=int, default=2)
     p.add_argument("--dt", type=float, default=None)
     p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     p.add_argument("--device", type=int, default=0)
     a = p.parse_args(argv)
-    net = W.small_loop_network() if a.workload == "small" else W.large_loop_network()
-    dt = a.dt if a.dt else (W.SMALL_LOOPS if a.workload == "small" else W.LARGE_LOOPS)["dt"]
+    net = {"small": W.small_loop_network, "medium": W.medium_loop_network,
+           "large": W.large_loop_network}[a.workload]()
+    dt = a.dt if a.dt else {"small": W.SMALL_LOOPS, "medium": W.MEDIUM_LOOPS, "large": W.LARGE_LOOPS}[a.workload]["dt"]
     prec = ptadd.PTADD_FP64 if a.precision == "fp64" else ptadd.PTADD_MIXED
     with ptadd.Context(W.Material().as_tuple(), prec, a.device) as ctx:
         ctx.set_network(net)

@@ -154,6 +154,8 @@ def loop_ensemble(seed, n_loops, box_edge, sig_app, nodes_per_loop=32,
 # --------------------------------------------------------------------------
 SMALL_LOOPS = dict(n_loops=16, box_edge=1.0 * MICRON, steps=100, dt=1e-11, seed=1001)
 LARGE_LOOPS = dict(n_loops=1024, box_edge=5.0 * MICRON, steps=1000, dt=1e-11, seed=1002)
+# same loop density as LARGE_LOOPS, a quarter of the loops (profiling-sized case)
+MEDIUM_LOOPS = dict(n_loops=256, box_edge=5.0 * MICRON * 0.25 ** (1.0 / 3.0), dt=1e-11, seed=1006)
 
 
 def small_loop_network(seed=SMALL_LOOPS["seed"]):
@@ -165,6 +167,12 @@ def small_loop_network(seed=SMALL_LOOPS["seed"]):
 def large_loop_network(seed=LARGE_LOOPS["seed"]):
     """1024 loops x 32 segments (32768) in a 5 um cube, 50 MPa uniaxial along [001]."""
     return loop_ensemble(seed, LARGE_LOOPS["n_loops"], LARGE_LOOPS["box_edge"],
+                         uniaxial_stress(50e6))
+
+
+def medium_loop_network(seed=MEDIUM_LOOPS["seed"]):
+    """256 loops x 32 segments (8192) at the loop density of the large workload."""
+    return loop_ensemble(seed, MEDIUM_LOOPS["n_loops"], MEDIUM_LOOPS["box_edge"],
                          uniaxial_stress(50e6))
 
 
