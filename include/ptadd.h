@@ -185,6 +185,42 @@ ptadd_status ptadd_profile_read(ptadd_ctx* ctx, ptadd_profile* out);
  * kernels are compared against. */
 ptadd_status ptadd_fma_peak(int device, int fp64, double seconds, double* flops);
 
+/* ------------------------------------------------------ no device allocation */
+/* Largest network ptadd_forces_noalloc accepts. */
+#define PTADD_NOALLOC_MAX_SEGMENTS 16384
+
+/* Nodal forces (N) of a network whose arrays are already on the device,
+ * computed without allocating any device memory.  This call has no
+ * counterpart in the paper; it exists for callers that cannot call
+ * cudaMalloc: code running under another framework's memory pool, which owns
+ * the device memory budget (a hidden cudaMalloc can fail there, or fragment
+ * the pool), and latency-critical loops where cudaMalloc's implicit device
+ * synchronisation would stall other streams.
+ *
+ * Same forces as ptadd_get_forces (FP64; every segment is a target).
+ * Inputs and output are caller-owned DEVICE arrays:
+ *   xyz_dev[n*3]      node positions, m
+ *   nxt_dev[n]        index of the node after node i on its loop (segment i
+ *                     runs i -> nxt[i]); prv_dev[n] the node before i
+ *   burgers_dev[n*3]  Burgers vector of segment i, m
+ *   sig_app[6]        HOST array, applied stress, Pa (Voigt order)
+ *   F_dev[n*3]        output nodal forces, N
+ *   stream            cudaStream_t as void* (NULL = legacy default stream)
+ * 2 <= n_nodes <= PTADD_NOALLOC_MAX_SEGMENTS, else PTADD_ERR_ARG.
+ *
+ * Scratch: one fixed array of about 7 MB in the library's device memory
+ * (held by every GPU that loads the library until the process exits).  The
+ * first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call before
+ * any stream capture.  Every call on a device shares the array: calls whose
+ * work overlaps on the GPU (other streams, other host threads) race and
+ * corrupt each other's results -- serialise them.  The call writes every
+ * scratch entry it reads, so nothing carries over from the previous call.
+ * Work is enqueued on `stream`; the call returns without synchronising. */
+ptadd_status ptadd_forces_noalloc(const ptadd_material* mat, int64_t n_nodes, const double* xyz_dev,
+                                  const int32_t* nxt_dev, const int32_t* prv_dev, const double* burgers_dev,
+                                  const double sig_app[6], double* F_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -25,7 +25,8 @@ EXPORTS = ["ptadd_version", "ptadd_create", "ptadd_destroy", "ptadd_last_error",
            "ptadd_set_stream", "ptadd_set_network", "ptadd_set_applied_stress", "ptadd_get_info",
            "ptadd_advance", "ptadd_get_nodes", "ptadd_get_forces", "ptadd_get_forces_dev",
            "ptadd_get_state", "ptadd_set_state", "ptadd_fma_peak", "ptadd_set_nodes",
-           "ptadd_profile_reset", "ptadd_profile_read"]
+           "ptadd_profile_reset", "ptadd_profile_read", "ptadd_forces_noalloc"]
+NOALLOC_MAX_SEGMENTS = 16384
 
 
 class PtaddError(RuntimeError):
@@ -105,6 +106,8 @@ def load(build_if_missing=True):
     lib.ptadd_profile_reset.restype = st
     lib.ptadd_profile_read.argtypes = [_VP, ctypes.POINTER(Profile)]
     lib.ptadd_profile_read.restype = st
+    lib.ptadd_forces_noalloc.argtypes = [ctypes.POINTER(Material), ctypes.c_int64, _VP, _VP, _VP, _VP, _D, _VP, _VP]
+    lib.ptadd_forces_noalloc.restype = st
     lib.ptadd_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]
     lib.ptadd_fma_peak.restype = st
     _lib = lib
@@ -134,6 +137,19 @@ def fma_peak(device=0, fp64=True, seconds=1.0):
     out = ctypes.c_double(0.0)
     _check(lib.ptadd_fma_peak(int(device), int(bool(fp64)), float(seconds), ctypes.byref(out)))
     return out.value
+
+
+def forces_noalloc(material, n_nodes, xyz_ptr, nxt_ptr, prv_ptr, burgers_ptr, sig_app, F_ptr, stream=None):
+    """ptadd_forces_noalloc on caller-owned device buffers (raw device pointers).
+
+    Allocates no device memory; see ptadd.h for the scratch-array contract
+    (fixed maximum size, first call per device before any stream capture,
+    overlapping calls race)."""
+    lib = load()
+    m = Material(*tuple(material))
+    s = _c(sig_app, np.float64)
+    _check(lib.ptadd_forces_noalloc(ctypes.byref(m), int(n_nodes), _VP(xyz_ptr), _VP(nxt_ptr), _VP(prv_ptr),
+                                    _VP(burgers_ptr), _dptr(s), _VP(F_ptr), _VP(stream) if stream else None))
 
 
 class Context:
