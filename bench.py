@@ -56,7 +56,9 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    p.add_argument("--fp64-steps", type=int, default=2,
+                   help="steps of plain FP64 DD timed beside the mixed path (0 = skip)")
     p.add_argument("--dd-steps", type=int, default=1, help="DD steps per benchmark step")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU-baseline sample")
@@ -262,6 +264,32 @@ def run_ours(args):
         elapsed_ms = float(t.item())
     value = world * pairs_per_bench_step * args.steps / (elapsed_ms * 1e-3)
 
+    # ---- plain FP64 DD on the same GPU and workload, for the ratio
+    fp64_cmp = None
+    if args.precision == "mixed" and args.fp64_steps > 0:
+        ctx.set_precision(ptadd.PTADD_FP64)
+        ctx.advance(args.dd_steps, dt)  # warm-up
+        torch.cuda.synchronize()
+        ctx.profile_reset(timing=True)
+        evs64 = []
+        for _ in range(args.fp64_steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.advance(args.dd_steps, dt)
+            e1.record(stream)
+            evs64.append((e0, e1))
+        torch.cuda.synchronize()
+        p64 = ctx.profile_read()
+        ms64 = sum(a.elapsed_time(b) for a, b in evs64)
+        v64 = world * pairs_per_bench_step * args.fp64_steps / (ms64 * 1e-3)
+        fp64_cmp = {"value": v64, "unit": "pair-evals/s", "steps": args.fp64_steps,
+                    "ms_per_step": ms64 / args.fp64_steps, "speedup_of_mixed": value / v64,
+                    "pair_kernel_frac_of_fp64_peak":
+                        FLOPS_PER_PAIR * p64["pair_evals"] / (p64["pair_ms"] * 1e-3) / peak_fp64}
+        ctx.set_precision(prec)
+
     # ---- end to end through the C ABI with pinned host buffers
     n = info["n_nodes"]
     host_in = torch.from_numpy(net.xyz.copy()).pin_memory()
@@ -314,6 +342,8 @@ def run_ours(args):
            "e2e": {"value": e2e_value, "unit": "pair-evals/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h},
            "gpu_launches": int(prof["kernel_launches"]),
+           "fp64_dd": fp64_cmp,
+           "near_field_point_pairs_per_step": prof.get("near_point_pairs", 0) / max(1, args.steps),
            "clocks": clk}
     ctx.close()
 

@@ -172,6 +172,8 @@ typedef struct {
     int64_t pair_launches;   /* of which pair-stress kernels                         */
     int64_t pair_evals;      /* segment-pair evaluations those launches performed    */
     double pair_ms;          /* summed event time of the pair launches (timing on)   */
+    int64_t near_point_pairs;/* PTADD_MIXED: (Gauss point, source) pairs evaluated   *
+                              * in FP64 because nearer than 10a (4 per pair eval)    */
 } ptadd_profile;
 
 /* Reset the counters; enable (1) or disable (0) the event timing. */

@@ -46,7 +46,8 @@ static ptadd_status dalloc(T** p, size_t count)
 static void free_network(DevNetwork& n)
 {
     void* ptrs[] = {n.pos[0], n.pos[1], n.nxt,   n.prv,   n.loop_of, n.loop_b,  n.loop_n, n.pinned, n.tgt_burst,
-                    n.tgt_all, n.src,    n.fpart, n.vel,   n.force,   n.partial, n.acc,    n.flag,   n.staging};
+                    n.tgt_all, n.src,    n.fpart, n.vel,   n.force,   n.partial, n.acc,    n.flag,   n.staging,
+                    n.src32,   n.near_count};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     n = DevNetwork{};
@@ -162,6 +163,8 @@ ptadd_status ptadd_set_network(ptadd_ctx* ctx, int64_t n_nodes, const double* xy
         }
     for (int c = 0; c < 3; ++c)
         if ((hi[c] - lo[c]) / b > 1.0e6) return arg_error("network extent exceeds 1e6 Burgers vectors");
+    double origin[3];
+    for (int c = 0; c < 3; ++c) origin[c] = rint(ldexp(0.5 * (lo[c] + hi[c]), -ctx->len_exp));
     for (int64_t k = 0; k < n_loops; ++k) {
         const double* nn = normal + 3 * k;
         const double nrm = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
@@ -177,6 +180,7 @@ ptadd_status ptadd_set_network(ptadd_ctx* ctx, int64_t n_nodes, const double* xy
     net.n_nodes = n;
     net.n_loops = n_loops;
     net.volume = volume;
+    for (int c = 0; c < 3; ++c) net.origin[c] = origin[c];
 
     // host-side tables
     std::vector<double> pos(3 * n);
@@ -229,6 +233,8 @@ ptadd_status ptadd_set_network(ptadd_ctx* ctx, int64_t n_nodes, const double* xy
     ALLOC(net.acc, 16);
     ALLOC(net.flag, 1);
     ALLOC(net.staging, 3 * n);
+    ALLOC(net.src32, SRC32_STRIDE * n);
+    ALLOC(net.near_count, 1);
 #undef ALLOC
     if (st != PTADD_OK) {
         free_network(net);
@@ -251,6 +257,7 @@ ptadd_status ptadd_set_network(ptadd_ctx* ctx, int64_t n_nodes, const double* xy
     PTADD_CUDA(cudaMemsetAsync(net.fpart, 0, (size_t)net.max_chunks * 6 * n * sizeof(double), s));
     PTADD_CUDA(cudaMemsetAsync(net.acc, 0, 16 * sizeof(double), s));
     PTADD_CUDA(cudaMemsetAsync(net.flag, 0, sizeof(int), s));
+    PTADD_CUDA(cudaMemsetAsync(net.near_count, 0, sizeof(unsigned long long), s));
     // host vectors die at return: make the copies complete first
     PTADD_CUDA(cudaStreamSynchronize(s));
     for (int c = 0; c < 6; ++c) ctx->sig_app[c] = 0.0;
@@ -439,6 +446,19 @@ ptadd_status ptadd_set_nodes(ptadd_ctx* ctx, const double* xyz)
     }
     if (!xyz) return arg_error("xyz is NULL");
     const int64_t n = ctx->net.n_nodes;
+    // new origin of the FP32 hi/lo split; the extent limit of set_network holds
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = 0; i < n; ++i)
+        for (int c = 0; c < 3; ++c) {
+            const double v = xyz[3 * i + c];
+            if (!isfinite(v)) return arg_error("non-finite node position");
+            lo[c] = fmin(lo[c], v);
+            hi[c] = fmax(hi[c], v);
+        }
+    for (int c = 0; c < 3; ++c) {
+        if ((hi[c] - lo[c]) / ctx->mat.b > 1.0e6) return arg_error("network extent exceeds 1e6 Burgers vectors");
+        ctx->net.origin[c] = rint(ldexp(0.5 * (lo[c] + hi[c]), -ctx->len_exp));
+    }
     PTADD_CUDA(cudaMemcpyAsync(ctx->net.staging, xyz, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     aos_to_soa_scaled<<<(unsigned)((3 * n + 255) / 256), 256, 0, ctx->stream>>>(n, ctx->net.staging, 1.0 / ctx->len_unit,
                                                                                 ctx->net.pos[ctx->net.cur]);
@@ -458,6 +478,9 @@ ptadd_status ptadd_profile_reset(ptadd_ctx* ctx, int timing)
     ctx->timing = timing != 0;
     ctx->kernel_launches = ctx->pair_launches = ctx->pair_evals = 0;
     ctx->pair_ms = 0.0;
+    ctx->near_base = 0;
+    if (ctx->have_net)
+        PTADD_CUDA(cudaMemcpy(&ctx->near_base, ctx->net.near_count, sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     return PTADD_OK;
 }
 
@@ -472,6 +495,12 @@ ptadd_status ptadd_profile_read(ptadd_ctx* ctx, ptadd_profile* out)
     out->pair_launches = ctx->pair_launches;
     out->pair_evals = ctx->pair_evals;
     out->pair_ms = ctx->pair_ms;
+    out->near_point_pairs = 0;
+    if (ctx->have_net) {
+        unsigned long long nc = 0;
+        PTADD_CUDA(cudaMemcpy(&nc, ctx->net.near_count, sizeof(nc), cudaMemcpyDeviceToHost));
+        out->near_point_pairs = (int64_t)(nc - ctx->near_base);
+    }
     return PTADD_OK;
 }
 

@@ -39,6 +39,15 @@ const char* cuda_msg(cudaError_t e);
 //   [0..2] x1 (start node)   [3] L      [4..6] unit tangent t   [7] 0
 //   [8..10] Burgers vector b [11] 0     [12..14] q = b x t      [15] 0
 constexpr int SRC_STRIDE = 16;
+// FP32 record of the mixed path (16 floats):
+//   [0..2] x1_hi  [3..5] x1_lo  [6] L  [7..9] t  [10..12] b  [13..15] q
+// with x1 - origin = x1_hi + x1_lo, x1_hi integer-valued (exact in FP32 for
+// |x1 - origin| < 2^24 l), so R0 = (x_hi - x1_hi) + (x_lo - x1_lo) keeps ~1 ulp
+// relative accuracy for every pair.
+constexpr int SRC32_STRIDE = 16;
+// Near field of the mixed path: point-to-segment distance below 10 a, with a
+// 1 % margin in favour of FP64 on the FP32 estimate of that distance.
+constexpr double NEAR_FACTOR = 10.1;
 
 // Device-side state of one realisation.
 struct DevNetwork {
@@ -55,6 +64,9 @@ struct DevNetwork {
     int64_t n_tgt_burst = 0;
     int32_t* tgt_all = nullptr;    // every segment
     double* src = nullptr;         // [n*SRC_STRIDE]
+    float* src32 = nullptr;        // [n*SRC32_STRIDE] FP32 records of the mixed path
+    double origin[3] = {0, 0, 0};  // integer-valued origin of the FP32 hi/lo split
+    unsigned long long* near_count = nullptr;  // FP64 point-pairs of the mixed path
     double* fpart = nullptr;       // [max_chunks*6*n] partial nodal-force parts
     int max_chunks = 0;
     double* vel = nullptr;         // SoA [3*n]
@@ -106,6 +118,7 @@ struct ptadd_ctx {
     bool timing = false;
     int64_t kernel_launches = 0, pair_launches = 0, pair_evals = 0;
     double pair_ms = 0.0;
+    unsigned long long near_base = 0;  // near_count at the last profile reset
     std::vector<cudaEvent_t> ev_pool;     // reusable events
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_open;  // recorded, not yet read
 };

@@ -97,17 +97,36 @@ __device__ __forceinline__ void pair_constants(const T t[3], const T b[3], const
     k.w[2] = b[0] * bt[1] - b[1] * bt[0];
 }
 
-// Accumulate (sigma b') of one source at one field point, given R0 = x - x1.
+// Geometry of one (field point, source) pair from R0 = x - x1.
+template <typename T> struct PairGeom {
+    T y;             // R0 . t  (u1 = -y)
+    T Rp[3];         // perpendicular part of R0
+    T d2;            // |Rp|^2 + a^2
+    T u2;            // L - y
+    T r1s, r2s;      // rho1^2, rho2^2
+};
+
 template <typename T>
-__device__ __forceinline__ void seg_sigma_b(T R0x, T R0y, T R0z, const T t[3], T L, const T b[3],
-                                            const T q[3], const T bt[3], const PairK<T>& k, T a2, T c1,
-                                            T c2, T s[3])
+__device__ __forceinline__ void pair_geom(T R0x, T R0y, T R0z, const T t[3], T L, T a2, PairGeom<T>& g)
 {
-    const T y = R0x * t[0] + R0y * t[1] + R0z * t[2];
-    const T Rpx = fma(-y, t[0], R0x), Rpy = fma(-y, t[1], R0y), Rpz = fma(-y, t[2], R0z);
-    const T d2 = fma(Rpx, Rpx, fma(Rpy, Rpy, fma(Rpz, Rpz, a2)));
-    const T u2 = L - y;
-    const T r1s = fma(y, y, d2), r2s = fma(u2, u2, d2);
+    g.y = R0x * t[0] + R0y * t[1] + R0z * t[2];
+    g.Rp[0] = fma(-g.y, t[0], R0x);
+    g.Rp[1] = fma(-g.y, t[1], R0y);
+    g.Rp[2] = fma(-g.y, t[2], R0z);
+    g.d2 = fma(g.Rp[0], g.Rp[0], fma(g.Rp[1], g.Rp[1], fma(g.Rp[2], g.Rp[2], a2)));
+    g.u2 = L - g.y;
+    g.r1s = fma(g.y, g.y, g.d2);
+    g.r2s = fma(g.u2, g.u2, g.d2);
+}
+
+// Accumulate (sigma b') of one source at one field point from its geometry.
+template <typename T>
+__device__ __forceinline__ void seg_sigma_b_geom(const PairGeom<T>& G, const T t[3], T L, const T b[3],
+                                                 const T q[3], const T bt[3], const PairK<T>& k, T a2, T c1,
+                                                 T c2, T s[3])
+{
+    const T y = G.y, u2 = G.u2, d2 = G.d2, r1s = G.r1s, r2s = G.r2s;
+    const T Rpx = G.Rp[0], Rpy = G.Rp[1], Rpz = G.Rp[2];
     const T i1 = RMath<T>::rsqrt(r1s), i2 = RMath<T>::rsqrt(r2s);
     const T m = -y * i1, p = u2 * i2;
     const bool same = (y <= T(0)) || (y >= L);  // u1 u2 >= 0
@@ -146,6 +165,17 @@ __device__ __forceinline__ void seg_sigma_b(T R0x, T R0y, T R0z, const T t[3], T
     s[0] = fma(cRxb, Xx, fma(cq, q[0], fma(cRp, Rpx, fma(ct, t[0], fma(cb, bt[0], s[0])))));
     s[1] = fma(cRxb, Xy, fma(cq, q[1], fma(cRp, Rpy, fma(ct, t[1], fma(cb, bt[1], s[1])))));
     s[2] = fma(cRxb, Xz, fma(cq, q[2], fma(cRp, Rpz, fma(ct, t[2], fma(cb, bt[2], s[2])))));
+}
+
+// Accumulate (sigma b') of one source at one field point, given R0 = x - x1.
+template <typename T>
+__device__ __forceinline__ void seg_sigma_b(T R0x, T R0y, T R0z, const T t[3], T L, const T b[3],
+                                            const T q[3], const T bt[3], const PairK<T>& k, T a2, T c1,
+                                            T c2, T s[3])
+{
+    PairGeom<T> G;
+    pair_geom(R0x, R0y, R0z, t, L, a2, G);
+    seg_sigma_b_geom(G, t, L, b, q, bt, k, a2, c1, c2, s);
 }
 
 // Gauss-Legendre rule on [0,1]: the textbook 4-point abscissae z and

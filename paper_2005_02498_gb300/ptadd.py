@@ -42,7 +42,8 @@ class Material(ctypes.Structure):
 
 class Profile(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("pair_launches", ctypes.c_int64),
-                ("pair_evals", ctypes.c_int64), ("pair_ms", ctypes.c_double)]
+                ("pair_evals", ctypes.c_int64), ("pair_ms", ctypes.c_double),
+                ("near_point_pairs", ctypes.c_int64)]
 
 
 class Info(ctypes.Structure):
@@ -242,7 +243,7 @@ class Context:
         p = Profile()
         _check(self._lib.ptadd_profile_read(self._h, ctypes.byref(p)))
         return dict(kernel_launches=p.kernel_launches, pair_launches=p.pair_launches,
-                    pair_evals=p.pair_evals, pair_ms=p.pair_ms)
+                    pair_evals=p.pair_evals, pair_ms=p.pair_ms, near_point_pairs=p.near_point_pairs)
 
     def get_forces(self):
         out = np.zeros((self.n_nodes, 3))

@@ -1,0 +1,108 @@
+"""GPU parity of the mixed-precision burst (FP32 far field with compensated
+accumulation, FP64 for pairs nearer than 10a, FP64 forces, positions and
+averages) against the FP64 CPU oracle.
+
+Bars: nodal forces <= 1e-4 relative max-norm; averaged rates <= 1 %
+(Frobenius norm of the difference over the Frobenius norm of the oracle's).
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2005_02498_gb300 import ptadd
+from paper_2005_02498_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+MAT = W.Material().as_tuple()
+
+
+def relmax(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(b)))
+
+
+def relfro(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+
+
+def ctx_for(net, prec):
+    c = ptadd.Context(MAT, prec, 0)
+    c.set_network(net)
+    return c
+
+
+@pytest.mark.parametrize("which", ["small", "ragged_pinned", "offset_box"])
+def test_mixed_forces_match_oracle(which):
+    if which == "small":
+        net = W.small_loop_network()
+    else:
+        net = W.loop_ensemble(21, 13, 0.6e-6, np.array([20e6, -35e6, 50e6, 10e6, -5e6, 25e6]), nodes_per_loop=23)
+        if which == "ragged_pinned":
+            net.pinned[2 * 23:4 * 23] = 1
+        else:  # far from the origin: the FP32 split must not lose the geometry
+            net.xyz = net.xyz + np.array([3.0e-4, -2.0e-4, 1.0e-4])
+    with ctx_for(net, ptadd.PTADD_MIXED) as c:
+        c.profile_reset()
+        F = c.get_forces()
+        prof = c.profile_read()
+    Fo = O.nodal_forces(MAT, net)
+    assert relmax(F, Fo) <= 1e-4
+    # every target has at least its own 4 Gauss points in the near (FP64) field
+    assert prof["near_point_pairs"] >= 4 * net.n_nodes
+
+
+def test_mixed_large_workload_sampled_forces():
+    net = W.large_loop_network()
+    rng = np.random.default_rng(9)
+    sel = np.sort(rng.choice(net.n_nodes, size=48, replace=False))
+    with ctx_for(net, ptadd.PTADD_MIXED) as c:
+        F = c.get_forces()
+    Fo = O.nodal_forces_subset(MAT, net, sel)
+    assert relmax(F[sel], Fo) <= 1e-4
+
+
+def test_mixed_burst_rates_small_workload():
+    net = W.small_loop_network()
+    dt = 5e-13
+    ref = O.burst(MAT, net, 100, dt)
+    with ctx_for(net, ptadd.PTADD_MIXED) as c:
+        Lp, rho = c.advance(100, dt)
+        x = c.get_nodes()
+    assert relfro(Lp, ref["Lp_avg"]) <= 1e-2
+    assert abs(rho / ref["rho_avg"] - 1) <= 1e-6
+    assert relmax(x - net.xyz, ref["xyz"] - net.xyz) <= 1e-3
+
+
+def test_mixed_burst_rates_large_workload_against_fp64_gpu():
+    """20 steps of the 32768-segment workload at dt = 5e-13 s (well
+    conditioned): mixed vs the FP64 GPU path (itself within 1e-11 of the
+    oracle on forces)."""
+    net = W.large_loop_network()
+    dt = 5e-13
+    with ctx_for(net, ptadd.PTADD_FP64) as c:
+        Lp64, rho64 = c.advance(20, dt)
+    with ctx_for(net, ptadd.PTADD_MIXED) as c:
+        Lpm, rhom = c.advance(20, dt)
+    assert relfro(Lpm, Lp64) <= 1e-2
+    assert abs(rhom / rho64 - 1) <= 1e-4
+
+
+def test_stated_dt_amplifies_any_perturbation():
+    """At dt = 1e-11 s explicit Euler is unstable for the small loops: a 1-ulp
+    change of the initial positions alone moves the 20-step average rate of
+    the FP64 path by more than the mixed path's force error does in one step.
+    The mixed-vs-FP64 difference must stay within a few times that floor."""
+    net = W.large_loop_network()
+    dt = W.LARGE_LOOPS["dt"]
+    pert = net.copy()
+    pert.xyz = np.nextafter(pert.xyz, np.inf)
+    with ctx_for(net, ptadd.PTADD_FP64) as c:
+        Lp64, _ = c.advance(20, dt)
+    with ctx_for(pert, ptadd.PTADD_FP64) as c:
+        Lp64p, _ = c.advance(20, dt)
+    with ctx_for(net, ptadd.PTADD_MIXED) as c:
+        Lpm, _ = c.advance(20, dt)
+    floor = relfro(Lp64p, Lp64)
+    print("20-step rate change from a 1-ulp position perturbation: %.3e; mixed vs FP64: %.3e"
+          % (floor, relfro(Lpm, Lp64)))
+    assert relfro(Lpm, Lp64) <= max(1e-2, 10 * floor)
