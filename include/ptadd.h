@@ -163,6 +163,53 @@ ptadd_status ptadd_get_forces_dev(ptadd_ctx* ctx, double* F_dev);
 ptadd_status ptadd_get_state(ptadd_ctx* ctx, void* buf, size_t* bytes);
 ptadd_status ptadd_set_state(ptadd_ctx* ctx, const void* buf, size_t bytes);
 
+/* ------------------------------------------------------------------ batched */
+/* R independent realisations advanced together (the independent bursts of
+ * the blocks / material points of the paper's coupling, Sec. 4.1, which it
+ * runs "in parallel").  Realisation r owns nodes [node_off[r], node_off[r+1])
+ * of the concatenated arrays; loops use GLOBAL node indices and must not
+ * straddle realisations.  Per realisation: its applied stress sig6[6r..6r+5]
+ * (Pa) and averaging volume volume[r] (m^3).  The precision of the context
+ * applies.  The pair stage is one persistent kernel that pulls (realisation,
+ * target tile, source chunk) work items, largest first, from an atomic
+ * counter; two steps are captured once into a CUDA graph and replayed.
+ * A batch lives beside (not instead of) the single network of the context. */
+typedef struct {
+    int32_t R;
+    int64_t n_nodes, n_loops, n_targets;
+    int64_t pairs_per_step; /* sum over realisations of n_targets_r * n_nodes_r */
+    int64_t work_items;     /* tiles of the persistent pair kernel per step    */
+    int32_t tile_targets;   /* autotuned: targets per tile (threads per block)  */
+    int32_t chunk_sources;  /* autotuned: sources per work item                 */
+    int32_t tuned;          /* 1 if the configuration came from the tuner/cache */
+} ptadd_batch_info;
+
+ptadd_status ptadd_batch_set(ptadd_ctx* ctx, int32_t R, const int64_t* node_off, int64_t n_loops,
+                             const int64_t* loop_off, const double* xyz, const double* burgers,
+                             const double* normal, const uint8_t* pinned, const double* sig6,
+                             const double* volume);
+/* New applied stresses sig6[R*6] (Pa) for the loaded batch; positions kept. */
+ptadd_status ptadd_batch_set_stress(ptadd_ctx* ctx, const double* sig6);
+/* Burst of n_steps for every realisation: Lp_avg[R*9] (row-major, 1/s) and
+ * rho_avg[R] (1/m^2), the averages of Eq. 2.5; either may be NULL. */
+ptadd_status ptadd_batch_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, double* Lp_avg, double* rho_avg);
+ptadd_status ptadd_batch_get_nodes(ptadd_ctx* ctx, double* xyz);
+ptadd_status ptadd_batch_set_nodes(ptadd_ctx* ctx, const double* xyz);
+ptadd_status ptadd_batch_get_info(ptadd_ctx* ctx, ptadd_batch_info* info);
+/* Time the pair stage of the loaded batch for every candidate (tile of 64 or
+ * 128 targets x chunks of 1024/2048/4096 sources), keep the fastest, and
+ * append it to a JSON-lines cache (cache_path, else $PTADD_TUNE_CACHE, else
+ * $HOME/.cache/ptadd_tune.jsonl) keyed by GPU, library version, precision and
+ * the batch's size class.  A cached entry is reused unless force != 0.
+ * ptadd_batch_set applies a cached entry when one exists. */
+ptadd_status ptadd_batch_autotune(ptadd_ctx* ctx, const char* cache_path, int force);
+/* ptadd_batch_set followed by ptadd_batch_advance. */
+ptadd_status ptadd_batch_run(ptadd_ctx* ctx, int32_t R, const int64_t* node_off, int64_t n_loops,
+                             const int64_t* loop_off, const double* xyz, const double* burgers,
+                             const double* normal, const uint8_t* pinned, const double* sig6,
+                             const double* volume, int64_t n_steps, double dt, double* Lp_avg,
+                             double* rho_avg);
+
 /* ------------------------------------------------------------- measurement */
 /* Launch counters and CUDA-event timing of the pair-stress kernels, recorded
  * on the stream they are launched on.  Timing costs two event records per

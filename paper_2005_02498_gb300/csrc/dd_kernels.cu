@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "pair_tile.cuh"
 #include "ptadd_internal.cuh"
 #include "seg_field.cuh"
 
@@ -68,256 +69,42 @@ cudaError_t launch_seg_prep(const DevNetwork& net, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// ----------------------------------------------------------- pair_fp64
+// ------------------------------------------------------------ pair stage
 // Grid: x = target tiles of PAIR_TPB threads (one target segment each),
-//       y = source chunks.  Each block stages PAIR_TILE source records at a
-// time through shared memory; every thread walks them in the same order
-// (broadcast reads) and accumulates (sigma b') at its 4 Gauss points.
+//       y = source chunks.  Each block runs one tile (pair_tile.cuh): it
+// stages source records through shared memory; every thread walks them in the
+// same order (broadcast reads) and accumulates (sigma b') at its 4 Gauss points.
 constexpr int PAIR_TPB = 128;
 constexpr int PAIR_TILE = 128;
-
-__global__ void __launch_bounds__(PAIR_TPB) pair_fp64_kernel(
-    int64_t n, const double* __restrict__ pos, const int32_t* __restrict__ nxt,
-    const double* __restrict__ src, const int32_t* __restrict__ tgt, int64_t n_tgt, int64_t chunk_len,
-    Consts c, double s0, double s1, double s2, double s3, double s4, double s5, double* __restrict__ fpart)
-{
-    __shared__ double2 tile[PAIR_TILE * SRC_STRIDE / 2];
-    const int64_t kt = blockIdx.x * (int64_t)PAIR_TPB + threadIdx.x;
-    const int chunk = blockIdx.y;
-    const int64_t js = (int64_t)chunk * chunk_len;
-    const int64_t je = min(n, js + chunk_len);
-    const bool active = kt < n_tgt;
-    const int64_t seg = active ? tgt[kt] : 0;
-
-    // target segment: start node, chord, Burgers vector, 4 Gauss points
-    const double* tr = src + (int64_t)SRC_STRIDE * seg;
-    const int64_t sb = nxt[seg];
-    const double xa = pos[seg], ya = pos[n + seg], za = pos[2 * n + seg];
-    const double Dx = pos[sb] - xa, Dy = pos[n + sb] - ya, Dz = pos[2 * n + sb] - za;
-    const double bt[3] = {tr[8], tr[9], tr[10]};
-    double xq[4][3];
-#pragma unroll
-    for (int qp = 0; qp < 4; ++qp) {
-        // x_q = x_a + xi_q (x_b - x_a), rounded as written (no contraction)
-        const double xi = gl4_xi(qp);
-        xq[qp][0] = __dadd_rn(xa, __dmul_rn(xi, Dx));
-        xq[qp][1] = __dadd_rn(ya, __dmul_rn(xi, Dy));
-        xq[qp][2] = __dadd_rn(za, __dmul_rn(xi, Dz));
-    }
-    double acc[4][3];
-#pragma unroll
-    for (int qp = 0; qp < 4; ++qp) acc[qp][0] = acc[qp][1] = acc[qp][2] = 0.0;
-
-    for (int64_t j0 = js; j0 < je; j0 += PAIR_TILE) {
-        const int cnt = (int)min((int64_t)PAIR_TILE, je - j0);
-        __syncthreads();
-        const double2* g = reinterpret_cast<const double2*>(src + (int64_t)SRC_STRIDE * j0);
-        for (int e = threadIdx.x; e < cnt * (SRC_STRIDE / 2); e += PAIR_TPB) tile[e] = g[e];
-        __syncthreads();
-        for (int jj = 0; jj < cnt; ++jj) {
-            const double* r = reinterpret_cast<const double*>(tile + jj * (SRC_STRIDE / 2));
-            const double L = r[3];
-            if (!(L > 0.0)) continue;  // zero-length source: no field (uniform branch)
-            const double x1[3] = {r[0], r[1], r[2]};
-            const double t[3] = {r[4], r[5], r[6]};
-            const double b[3] = {r[8], r[9], r[10]};
-            const double q[3] = {r[12], r[13], r[14]};
-            PairK<double> k;
-            pair_constants(t, b, q, bt, k);
-#pragma unroll
-            for (int qp = 0; qp < 4; ++qp)
-                seg_sigma_b(xq[qp][0] - x1[0], xq[qp][1] - x1[1], xq[qp][2] - x1[2], t, L, b, q, bt, k, c.a2,
-                            c.c1, c.c2, acc[qp]);
-        }
-    }
-    if (!active) return;
-    if (chunk == 0) {  // applied stress, once per target
-        const double sb0 = s0 * bt[0] + s5 * bt[1] + s4 * bt[2];
-        const double sb1 = s5 * bt[0] + s1 * bt[1] + s3 * bt[2];
-        const double sb2 = s4 * bt[0] + s3 * bt[1] + s2 * bt[2];
-#pragma unroll
-        for (int qp = 0; qp < 4; ++qp) {
-            acc[qp][0] += sb0;
-            acc[qp][1] += sb1;
-            acc[qp][2] += sb2;
-        }
-    }
-    // F_start = sum_q w_q (1 - xi_q) (s_q x D), F_end = sum_q w_q xi_q (s_q x D)   (L t = D)
-    double Fs[3] = {0, 0, 0}, Fe[3] = {0, 0, 0};
-#pragma unroll
-    for (int qp = 0; qp < 4; ++qp) {
-        const double fx = acc[qp][1] * Dz - acc[qp][2] * Dy;
-        const double fy = acc[qp][2] * Dx - acc[qp][0] * Dz;
-        const double fz = acc[qp][0] * Dy - acc[qp][1] * Dx;
-        const double we = gl4_w(qp) * gl4_xi(qp), ws = gl4_w(qp) - we;
-        Fs[0] = fma(ws, fx, Fs[0]); Fs[1] = fma(ws, fy, Fs[1]); Fs[2] = fma(ws, fz, Fs[2]);
-        Fe[0] = fma(we, fx, Fe[0]); Fe[1] = fma(we, fy, Fe[1]); Fe[2] = fma(we, fz, Fe[2]);
-    }
-    double* fp = fpart + (int64_t)chunk * 6 * n;
-    fp[0 * n + seg] = Fs[0];
-    fp[1 * n + seg] = Fs[1];
-    fp[2 * n + seg] = Fs[2];
-    fp[3 * n + seg] = Fe[0];
-    fp[4 * n + seg] = Fe[1];
-    fp[5 * n + seg] = Fe[2];
-}
-
-// ---------------------------------------------------------- pair_mixed
-// Same decomposition as pair_fp64_kernel.  Every (Gauss point, source) pair
-// is first located in FP32 from hi/lo-split coordinates; if the point lies
-// within 10 a of the source segment the pair is evaluated in FP64 from the
-// FP64 records, otherwise in FP32.  Per Gauss point the contributions are
-// summed in FP32 with Kahan compensation (the FP64 near-field values enter as
-// hi + lo floats); the compensated sums go to FP64 before the PK force and the
-// nodal assembly.
 constexpr int MIX_TPB = 128;
 constexpr int MIX_TILE = 256;
 
-__device__ __forceinline__ void kahan_add(float& s, float& c, float v)
+__global__ void __launch_bounds__(PAIR_TPB) pair_fp64_kernel(TileArgs base, int64_t n_tgt, int64_t chunk_len,
+                                                             Consts c)
 {
-    const float y = v - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
+    __shared__ double2 tile[PAIR_TILE * SRC_STRIDE / 2];
+    TileArgs a = base;
+    a.t_begin = (int64_t)blockIdx.x * PAIR_TPB;
+    a.t_count = min((int64_t)PAIR_TPB, n_tgt - a.t_begin);
+    a.js = (int64_t)blockIdx.y * chunk_len;
+    a.je = min(a.n, a.js + chunk_len);
+    a.add_app = blockIdx.y == 0;
+    a.fp = base.fp + (int64_t)blockIdx.y * 6 * a.n;
+    pair_tile_fp64<PAIR_TILE>(a, c, tile);
 }
 
-__global__ void __launch_bounds__(MIX_TPB) pair_mixed_kernel(
-    int64_t n, const double* __restrict__ pos, const int32_t* __restrict__ nxt, const double* __restrict__ src,
-    const float* __restrict__ src32, const int32_t* __restrict__ tgt, int64_t n_tgt, int64_t chunk_len, Consts c,
-    float near2, double ox, double oy, double oz, double s0, double s1, double s2, double s3, double s4, double s5,
-    double* __restrict__ fpart, unsigned long long* __restrict__ near_count)
+__global__ void __launch_bounds__(MIX_TPB) pair_mixed_kernel(TileArgs base, int64_t n_tgt, int64_t chunk_len,
+                                                             Consts c, float near2)
 {
     __shared__ float4 tile[MIX_TILE * SRC32_STRIDE / 4];
-    const int64_t kt = blockIdx.x * (int64_t)MIX_TPB + threadIdx.x;
-    const int chunk = blockIdx.y;
-    const int64_t js = (int64_t)chunk * chunk_len;
-    const int64_t je = min(n, js + chunk_len);
-    const bool active = kt < n_tgt;
-    const int64_t seg = active ? tgt[kt] : 0;
-
-    const double* tr = src + (int64_t)SRC_STRIDE * seg;
-    const int64_t sb = nxt[seg];
-    const double xa = pos[seg], ya = pos[n + seg], za = pos[2 * n + seg];
-    const double Dx = pos[sb] - xa, Dy = pos[n + sb] - ya, Dz = pos[2 * n + sb] - za;
-    const double bt[3] = {tr[8], tr[9], tr[10]};
-    const float btf[3] = {(float)bt[0], (float)bt[1], (float)bt[2]};
-    float xh[4][3], xl[4][3];
-#pragma unroll
-    for (int qp = 0; qp < 4; ++qp) {
-        const double xi = gl4_xi(qp);
-        const double q0 = __dadd_rn(xa, __dmul_rn(xi, Dx)) - ox;
-        const double q1 = __dadd_rn(ya, __dmul_rn(xi, Dy)) - oy;
-        const double q2 = __dadd_rn(za, __dmul_rn(xi, Dz)) - oz;
-        const double h0 = rint(q0), h1 = rint(q1), h2 = rint(q2);
-        xh[qp][0] = (float)h0; xh[qp][1] = (float)h1; xh[qp][2] = (float)h2;
-        xl[qp][0] = (float)(q0 - h0); xl[qp][1] = (float)(q1 - h1); xl[qp][2] = (float)(q2 - h2);
-    }
-    float sh[4][3], sc[4][3];
-#pragma unroll
-    for (int qp = 0; qp < 4; ++qp)
-#pragma unroll
-        for (int e = 0; e < 3; ++e) sh[qp][e] = sc[qp][e] = 0.0f;
-    const float a2f = (float)c.a2, c1f = (float)c.c1, c2f = (float)c.c2;
-    unsigned near_here = 0;
-
-    for (int64_t j0 = js; j0 < je; j0 += MIX_TILE) {
-        const int cnt = (int)min((int64_t)MIX_TILE, je - j0);
-        __syncthreads();
-        const float4* g = reinterpret_cast<const float4*>(src32 + (int64_t)SRC32_STRIDE * j0);
-        for (int e = threadIdx.x; e < cnt * (SRC32_STRIDE / 4); e += MIX_TPB) tile[e] = g[e];
-        __syncthreads();
-        for (int jj = 0; jj < cnt; ++jj) {
-            const float* r = reinterpret_cast<const float*>(tile + jj * (SRC32_STRIDE / 4));
-            const float L = r[6];
-            if (!(L > 0.0f)) continue;  // zero-length source (uniform branch)
-            const float h1[3] = {r[0], r[1], r[2]}, l1[3] = {r[3], r[4], r[5]};
-            const float t[3] = {r[7], r[8], r[9]};
-            const float b[3] = {r[10], r[11], r[12]};
-            const float q[3] = {r[13], r[14], r[15]};
-            PairK<float> k;
-            pair_constants(t, b, q, btf, k);
-#pragma unroll
-            for (int qp = 0; qp < 4; ++qp) {
-                const float R0x = (xh[qp][0] - h1[0]) + (xl[qp][0] - l1[0]);
-                const float R0y = (xh[qp][1] - h1[1]) + (xl[qp][1] - l1[1]);
-                const float R0z = (xh[qp][2] - h1[2]) + (xl[qp][2] - l1[2]);
-                PairGeom<float> G;
-                pair_geom(R0x, R0y, R0z, t, L, a2f, G);
-                // squared point-to-segment distance (+ a^2)
-                const float dd = G.y < 0.0f ? G.r1s : (G.y > L ? G.r2s : G.d2);
-                float v[3] = {0.0f, 0.0f, 0.0f};
-                if (dd >= near2) {
-                    seg_sigma_b_geom(G, t, L, b, q, btf, k, a2f, c1f, c2f, v);
-                    kahan_add(sh[qp][0], sc[qp][0], v[0]);
-                    kahan_add(sh[qp][1], sc[qp][1], v[1]);
-                    kahan_add(sh[qp][2], sc[qp][2], v[2]);
-                } else {
-                    // near field: FP64 from the FP64 records
-                    ++near_here;
-                    const double* r64 = src + (int64_t)SRC_STRIDE * (j0 + jj);
-                    const double x1d[3] = {r64[0], r64[1], r64[2]};
-                    const double td[3] = {r64[4], r64[5], r64[6]};
-                    const double bd[3] = {r64[8], r64[9], r64[10]};
-                    const double qd[3] = {r64[12], r64[13], r64[14]};
-                    PairK<double> kd;
-                    pair_constants(td, bd, qd, bt, kd);
-                    const double xi = gl4_xi(qp);
-                    const double xq0 = __dadd_rn(xa, __dmul_rn(xi, Dx));
-                    const double xq1 = __dadd_rn(ya, __dmul_rn(xi, Dy));
-                    const double xq2 = __dadd_rn(za, __dmul_rn(xi, Dz));
-                    double vd[3] = {0.0, 0.0, 0.0};
-                    seg_sigma_b(xq0 - x1d[0], xq1 - x1d[1], xq2 - x1d[2], td, r64[3], bd, qd, bt, kd, c.a2, c.c1,
-                                c.c2, vd);
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        const float hi = (float)vd[e];
-                        const float lo = (float)(vd[e] - (double)hi);
-                        kahan_add(sh[qp][e], sc[qp][e], hi);
-                        kahan_add(sh[qp][e], sc[qp][e], lo);
-                    }
-                }
-            }
-        }
-    }
-    // count the FP64 point-pairs (one atomic per warp)
-    unsigned w = near_here;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
-    if ((threadIdx.x & 31) == 0 && w) atomicAdd(near_count, (unsigned long long)w);
-    if (!active) return;
-    double acc[4][3];
-#pragma unroll
-    for (int qp = 0; qp < 4; ++qp)
-#pragma unroll
-        for (int e = 0; e < 3; ++e) acc[qp][e] = (double)sh[qp][e] - (double)sc[qp][e];
-    if (chunk == 0) {
-        const double sb0 = s0 * bt[0] + s5 * bt[1] + s4 * bt[2];
-        const double sb1 = s5 * bt[0] + s1 * bt[1] + s3 * bt[2];
-        const double sb2 = s4 * bt[0] + s3 * bt[1] + s2 * bt[2];
-#pragma unroll
-        for (int qp = 0; qp < 4; ++qp) {
-            acc[qp][0] += sb0;
-            acc[qp][1] += sb1;
-            acc[qp][2] += sb2;
-        }
-    }
-    double Fs[3] = {0, 0, 0}, Fe[3] = {0, 0, 0};
-#pragma unroll
-    for (int qp = 0; qp < 4; ++qp) {
-        const double fx = acc[qp][1] * Dz - acc[qp][2] * Dy;
-        const double fy = acc[qp][2] * Dx - acc[qp][0] * Dz;
-        const double fz = acc[qp][0] * Dy - acc[qp][1] * Dx;
-        const double we = gl4_w(qp) * gl4_xi(qp), ws = gl4_w(qp) - we;
-        Fs[0] = fma(ws, fx, Fs[0]); Fs[1] = fma(ws, fy, Fs[1]); Fs[2] = fma(ws, fz, Fs[2]);
-        Fe[0] = fma(we, fx, Fe[0]); Fe[1] = fma(we, fy, Fe[1]); Fe[2] = fma(we, fz, Fe[2]);
-    }
-    double* fp = fpart + (int64_t)chunk * 6 * n;
-    fp[0 * n + seg] = Fs[0];
-    fp[1 * n + seg] = Fs[1];
-    fp[2 * n + seg] = Fs[2];
-    fp[3 * n + seg] = Fe[0];
-    fp[4 * n + seg] = Fe[1];
-    fp[5 * n + seg] = Fe[2];
+    TileArgs a = base;
+    a.t_begin = (int64_t)blockIdx.x * MIX_TPB;
+    a.t_count = min((int64_t)MIX_TPB, n_tgt - a.t_begin);
+    a.js = (int64_t)blockIdx.y * chunk_len;
+    a.je = min(a.n, a.js + chunk_len);
+    a.add_app = blockIdx.y == 0;
+    a.fp = base.fp + (int64_t)blockIdx.y * 6 * a.n;
+    pair_tile_mixed<MIX_TILE>(a, c, near2, tile);
 }
 
 int choose_chunks(int64_t n_tgt, int64_t n_src, int max_chunks)
@@ -339,18 +126,27 @@ cudaError_t launch_pair(const DevNetwork& net, const int32_t* tgt, int64_t n_tgt
     const int64_t n = net.n_nodes;
     if (n_tgt == 0 || n == 0) return cudaSuccess;
     const int64_t chunk_len = (n + chunks - 1) / chunks;
+    TileArgs a{};
+    a.pos = net.pos[net.cur];
+    a.n = n;
+    a.nxt = net.nxt;
+    a.src = net.src;
+    a.src32 = net.src32;
+    a.tgt = tgt;
+    for (int k = 0; k < 6; ++k) a.sh[k] = sh[k];
+    for (int k = 0; k < 3; ++k) a.origin[k] = net.origin[k];
+    a.fp = net.fpart;
+    a.fp_stride = n;
+    a.node_base = 0;
+    a.near_count = net.near_count;
     if (precision == (int)PTADD_MIXED) {
         dim3 grid((unsigned)((n_tgt + MIX_TPB - 1) / MIX_TPB), (unsigned)chunks);
         const float near2 = (float)((NEAR_FACTOR * NEAR_FACTOR + 1.0) * c.a2);
-        pair_mixed_kernel<<<grid, MIX_TPB, 0, st>>>(n, net.pos[net.cur], net.nxt, net.src, net.src32, tgt, n_tgt,
-                                                    chunk_len, c, near2, net.origin[0], net.origin[1],
-                                                    net.origin[2], sh[0], sh[1], sh[2], sh[3], sh[4], sh[5],
-                                                    net.fpart, net.near_count);
+        pair_mixed_kernel<<<grid, MIX_TPB, 0, st>>>(a, n_tgt, chunk_len, c, near2);
         return cudaGetLastError();
     }
     dim3 grid((unsigned)((n_tgt + PAIR_TPB - 1) / PAIR_TPB), (unsigned)chunks);
-    pair_fp64_kernel<<<grid, PAIR_TPB, 0, st>>>(n, net.pos[net.cur], net.nxt, net.src, tgt, n_tgt, chunk_len, c,
-                                                sh[0], sh[1], sh[2], sh[3], sh[4], sh[5], net.fpart);
+    pair_fp64_kernel<<<grid, PAIR_TPB, 0, st>>>(a, n_tgt, chunk_len, c);
     return cudaGetLastError();
 }
 

@@ -116,6 +116,7 @@ void ptadd_destroy(ptadd_ctx* ctx)
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     free_network(ctx->net);
+    batch_free(ctx);
     for (auto& e : ctx->ev_open) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);

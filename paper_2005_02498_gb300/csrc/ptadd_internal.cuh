@@ -17,6 +17,8 @@
 
 #include "../../include/ptadd.h"
 
+struct ptadd_ctx;
+
 namespace ptadd {
 
 // --------------------------------------------------------------- errors
@@ -101,6 +103,9 @@ int choose_chunks(int64_t n_tgt, int64_t n_src, int max_chunks);
 // peak microbenchmark
 cudaError_t launch_fma_chains(int fp64, int blocks, int threads, long iters, double* sink, cudaStream_t st);
 
+struct DevBatch;
+void batch_free(ptadd_ctx* ctx);
+
 }  // namespace ptadd
 
 struct ptadd_ctx {
@@ -113,6 +118,7 @@ struct ptadd_ctx {
     cudaStream_t stream = nullptr;
     ptadd::DevNetwork net;
     bool have_net = false;
+    ptadd::DevBatch* batch = nullptr;  // batched ensemble (ptadd_batch_*)
     double sig_app[6] = {0, 0, 0, 0, 0, 0};  // Pa
     // profiling (ptadd_profile_*)
     bool timing = false;

@@ -25,7 +25,9 @@ EXPORTS = ["ptadd_version", "ptadd_create", "ptadd_destroy", "ptadd_last_error",
            "ptadd_set_stream", "ptadd_set_network", "ptadd_set_applied_stress", "ptadd_get_info",
            "ptadd_advance", "ptadd_get_nodes", "ptadd_get_forces", "ptadd_get_forces_dev",
            "ptadd_get_state", "ptadd_set_state", "ptadd_fma_peak", "ptadd_set_nodes",
-           "ptadd_profile_reset", "ptadd_profile_read", "ptadd_forces_noalloc"]
+           "ptadd_profile_reset", "ptadd_profile_read", "ptadd_forces_noalloc",
+           "ptadd_batch_set", "ptadd_batch_set_stress", "ptadd_batch_advance", "ptadd_batch_get_nodes",
+           "ptadd_batch_set_nodes", "ptadd_batch_get_info", "ptadd_batch_autotune", "ptadd_batch_run"]
 NOALLOC_MAX_SEGMENTS = 16384
 
 
@@ -44,6 +46,12 @@ class Profile(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_int64), ("pair_launches", ctypes.c_int64),
                 ("pair_evals", ctypes.c_int64), ("pair_ms", ctypes.c_double),
                 ("near_point_pairs", ctypes.c_int64)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_int32), ("n_nodes", ctypes.c_int64), ("n_loops", ctypes.c_int64),
+                ("n_targets", ctypes.c_int64), ("pairs_per_step", ctypes.c_int64), ("work_items", ctypes.c_int64),
+                ("tile_targets", ctypes.c_int32), ("chunk_sources", ctypes.c_int32), ("tuned", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -109,6 +117,23 @@ def load(build_if_missing=True):
     lib.ptadd_profile_read.restype = st
     lib.ptadd_forces_noalloc.argtypes = [ctypes.POINTER(Material), ctypes.c_int64, _VP, _VP, _VP, _VP, _D, _VP, _VP]
     lib.ptadd_forces_noalloc.restype = st
+    lib.ptadd_batch_set.argtypes = [_VP, ctypes.c_int32, _I64, ctypes.c_int64, _I64, _D, _D, _D, _U8, _D, _D]
+    lib.ptadd_batch_set.restype = st
+    lib.ptadd_batch_set_stress.argtypes = [_VP, _D]
+    lib.ptadd_batch_set_stress.restype = st
+    lib.ptadd_batch_advance.argtypes = [_VP, ctypes.c_int64, ctypes.c_double, _D, _D]
+    lib.ptadd_batch_advance.restype = st
+    lib.ptadd_batch_get_nodes.argtypes = [_VP, _D]
+    lib.ptadd_batch_get_nodes.restype = st
+    lib.ptadd_batch_set_nodes.argtypes = [_VP, _D]
+    lib.ptadd_batch_set_nodes.restype = st
+    lib.ptadd_batch_get_info.argtypes = [_VP, ctypes.POINTER(BatchInfo)]
+    lib.ptadd_batch_get_info.restype = st
+    lib.ptadd_batch_autotune.argtypes = [_VP, ctypes.c_char_p, ctypes.c_int]
+    lib.ptadd_batch_autotune.restype = st
+    lib.ptadd_batch_run.argtypes = [_VP, ctypes.c_int32, _I64, ctypes.c_int64, _I64, _D, _D, _D, _U8, _D, _D,
+                                    ctypes.c_int64, ctypes.c_double, _D, _D]
+    lib.ptadd_batch_run.restype = st
     lib.ptadd_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]
     lib.ptadd_fma_peak.restype = st
     _lib = lib
@@ -263,3 +288,47 @@ class Context:
     def set_state(self, blob):
         buf = ctypes.create_string_buffer(blob, len(blob))
         _check(self._lib.ptadd_set_state(self._h, ctypes.cast(buf, _VP), len(blob)))
+
+    # ------------------------------------------------------------ batched
+    def batch_set(self, batch):
+        """batch: workloads.Batch (SI)."""
+        b = batch
+        self._batch_keep = [_c(b.node_off, np.int64), _c(b.loop_off, np.int64), _c(b.xyz, np.float64),
+                            _c(b.burgers, np.float64), _c(b.normal, np.float64), _c(b.pinned, np.uint8),
+                            _c(b.sig6, np.float64), _c(b.volume, np.float64)]
+        no, lo, x, bv, nv, pin, sg, vol = self._batch_keep
+        _check(self._lib.ptadd_batch_set(self._h, int(b.R), no.ctypes.data_as(_I64), lo.shape[0] - 1,
+                                         lo.ctypes.data_as(_I64), _dptr(x), _dptr(bv), _dptr(nv),
+                                         pin.ctypes.data_as(_U8), _dptr(sg), _dptr(vol)))
+        self.batch_R = int(b.R)
+        self.batch_n = int(x.shape[0])
+        self._batch_keep = None
+
+    def batch_set_stress(self, sig6):
+        s = _c(sig6, np.float64).reshape(-1)
+        _check(self._lib.ptadd_batch_set_stress(self._h, _dptr(s)))
+
+    def batch_advance(self, n_steps, dt):
+        """Returns (Lp_avg [R,3,3], rho_avg [R])."""
+        Lp = np.zeros(9 * self.batch_R)
+        rho = np.zeros(self.batch_R)
+        _check(self._lib.ptadd_batch_advance(self._h, int(n_steps), float(dt), _dptr(Lp), _dptr(rho)))
+        return Lp.reshape(-1, 3, 3), rho
+
+    def batch_get_nodes(self):
+        out = np.zeros((self.batch_n, 3))
+        _check(self._lib.ptadd_batch_get_nodes(self._h, _dptr(out)))
+        return out
+
+    def batch_set_nodes(self, xyz):
+        x = _c(xyz, np.float64)
+        _check(self._lib.ptadd_batch_set_nodes(self._h, _dptr(x)))
+
+    def batch_info(self):
+        i = BatchInfo()
+        _check(self._lib.ptadd_batch_get_info(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in BatchInfo._fields_}
+
+    def batch_autotune(self, cache_path=None, force=False):
+        _check(self._lib.ptadd_batch_autotune(self._h, cache_path.encode() if cache_path else None,
+                                              int(bool(force))))

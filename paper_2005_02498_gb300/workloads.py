@@ -256,3 +256,21 @@ def batch_ensemble(seed, R=256, n_min=1024, n_max=16384, nodes_per_loop=32,
                  np.asarray(loop_base, np.int64), np.asarray(node_off, np.int64),
                  np.ascontiguousarray(np.concatenate(bvs)), np.ascontiguousarray(np.concatenate(nvs)),
                  np.concatenate(pins), sig6, vol)
+
+
+def batch_from_networks(nets):
+    """Concatenate single-realisation Networks into a Batch."""
+    node_off = [0]
+    loop_base = [0]
+    offs = []
+    for nt in nets:
+        offs.append(np.asarray(nt.loop_off[:-1], np.int64) + node_off[-1])
+        node_off.append(node_off[-1] + nt.n_nodes)
+        loop_base.append(loop_base[-1] + nt.n_loops)
+    loop_off = np.concatenate(offs + [np.array([node_off[-1]], np.int64)])
+    return Batch(np.ascontiguousarray(np.concatenate([nt.xyz for nt in nets])), loop_off,
+                 np.asarray(loop_base, np.int64), np.asarray(node_off, np.int64),
+                 np.ascontiguousarray(np.concatenate([nt.burgers for nt in nets])),
+                 np.ascontiguousarray(np.concatenate([nt.normal for nt in nets])),
+                 np.concatenate([nt.pinned for nt in nets]).astype(np.uint8),
+                 np.stack([nt.sig_app for nt in nets]), np.array([nt.volume for nt in nets], float))
