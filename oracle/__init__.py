@@ -19,6 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ptadd_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "mlp_oracle.c")]
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
 _lib = None
@@ -33,11 +34,11 @@ def build(force=False):
     os.makedirs(_LIBDIR, exist_ok=True)
     hdr = os.path.join(_HERE, "ptadd_oracle.h")
     if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= max(os.path.getmtime(_SRC), os.path.getmtime(hdr))):
+            and os.path.getmtime(_LIB) >= max([os.path.getmtime(f) for f in _SRCS] + [os.path.getmtime(hdr)])):
         return _LIB
     tmp = _LIB + ".tmp.%d" % os.getpid()
     cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off",
-           "-std=c11", "-o", tmp, _SRC, "-lm"]
+           "-std=c11", "-o", tmp, *_SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
@@ -67,6 +68,17 @@ def _load():
                                   _D, _D, _D, _D, _D]
         lib.orc_burst.restype = ctypes.c_int
         lib.orc_num_threads.restype = ctypes.c_int
+        lib.orc_gelu.argtypes = [ctypes.c_double]
+        lib.orc_gelu.restype = ctypes.c_double
+        lib.orc_gelu_grad.argtypes = [ctypes.c_double]
+        lib.orc_gelu_grad.restype = ctypes.c_double
+        lib.orc_mlp_param_count.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        lib.orc_mlp_param_count.restype = ctypes.c_int64
+        lib.orc_mlp_forward.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D, ctypes.c_int64, _D, _D]
+        lib.orc_mlp_loss_grad.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _D, ctypes.c_int64, _D, _D, _D]
+        lib.orc_mlp_loss_grad.restype = ctypes.c_double
+        lib.orc_adam_step.argtypes = [ctypes.c_int64, _D, _D, _D, _D, ctypes.c_int64, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_double, ctypes.c_double]
         _lib = lib
     return _lib
 
@@ -233,3 +245,50 @@ def burst(mat, net, n_steps, dt, interactions=True, trace=False):
         out["Lp_trace"] = tL[:n_steps].reshape(-1, 3, 3)
         out["rho_trace"] = tr[:n_steps]
     return out
+
+
+# ------------------------------------------------------------------ MLP
+def _dims(dims):
+    arr = (ctypes.c_int * len(dims))(*[int(d) for d in dims])
+    return len(dims) - 1, arr
+
+
+def gelu(z):
+    return _load().orc_gelu(float(z))
+
+
+def gelu_grad(z):
+    return _load().orc_gelu_grad(float(z))
+
+
+def mlp_param_count(dims):
+    L, arr = _dims(dims)
+    return int(_load().orc_mlp_param_count(L, arr))
+
+
+def mlp_forward(dims, params, X):
+    L, arr = _dims(dims)
+    p, pp = _d(params)
+    x, px = _d(np.asarray(X).reshape(-1, dims[0]))
+    Y = np.zeros((x.shape[0], dims[-1]))
+    _load().orc_mlp_forward(L, arr, pp, x.shape[0], px, Y.ctypes.data_as(_D))
+    return Y
+
+
+def mlp_loss_grad(dims, params, X, T):
+    L, arr = _dims(dims)
+    p, pp = _d(params)
+    x, px = _d(np.asarray(X).reshape(-1, dims[0]))
+    t, pt = _d(np.asarray(T).reshape(-1, dims[-1]))
+    g = np.zeros_like(p)
+    loss = _load().orc_mlp_loss_grad(L, arr, pp, x.shape[0], px, pt, g.ctypes.data_as(_D))
+    return loss, g
+
+
+def adam_step(p, g, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In place on float64 arrays p, m, v."""
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    gg, pg = _d(g)
+    _load().orc_adam_step(p.size, p.ctypes.data_as(_D), pg, m.ctypes.data_as(_D), v.ctypes.data_as(_D),
+                          int(t), float(lr), float(b1), float(b2), float(eps))

@@ -95,6 +95,18 @@ int orc_burst(const double mat[5], int64_t n_nodes, const double* xyz,
               double* xyz_out, double Lp_avg[9], double* rho_avg,
               double* Lp_trace, double* rho_trace);
 
+/* ---- MLP (mlp_oracle.c): dims[0] -> ... -> dims[L], GELU on hidden layers,
+ * linear output, parameters packed per layer as W (dims[l+1] x dims[l],
+ * row-major) then b; loss = mean (y - t)^2 over batch and outputs. */
+double orc_gelu(double z);
+double orc_gelu_grad(double z);
+int64_t orc_mlp_param_count(int L, const int* dims);
+void orc_mlp_forward(int L, const int* dims, const double* params, int64_t B, const double* X, double* Y);
+double orc_mlp_loss_grad(int L, const int* dims, const double* params, int64_t B, const double* X,
+                         const double* T, double* grad);
+void orc_adam_step(int64_t n, double* p, const double* g, double* m, double* v, int64_t t, double lr,
+                   double b1, double b2, double eps);
+
 /* Number of OpenMP threads the oracle uses (for reporting). */
 int orc_num_threads(void);
 
