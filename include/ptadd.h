@@ -210,6 +210,16 @@ ptadd_status ptadd_batch_run(ptadd_ctx* ctx, int32_t R, const int64_t* node_off,
                              const double* volume, int64_t n_steps, double dt, double* Lp_avg,
                              double* rho_avg);
 
+/* ---------------------------------------------------------- tensor cores */
+/* C[M x N] = A[M x K] * B[N x K]^T on the tensor cores (tcgen05.mma, FP32
+ * accumulation in tensor memory).  Host arrays: A and B hold BF16 bit
+ * patterns (uint16), K contiguous; C is FP32 row-major.  N a multiple of 16
+ * in [16, 256], K a multiple of 16.  Allocates its own device buffers; the
+ * surrogate's kernels use the same GEMM tile.  Returns PTADD_ERR_TIMEOUT if a
+ * bounded wait for the tensor core gave up. */
+ptadd_status ptadd_gemm_bf16(int device, int64_t M, int32_t N, int32_t K, const uint16_t* A, const uint16_t* B,
+                             float* C);
+
 /* ------------------------------------------------------------- measurement */
 /* Launch counters and CUDA-event timing of the pair-stress kernels, recorded
  * on the stream they are launched on.  Timing costs two event records per

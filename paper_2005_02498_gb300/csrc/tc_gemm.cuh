@@ -1,0 +1,271 @@
+// tc_gemm.cuh -- BF16 x BF16 -> FP32 GEMM tile on the 5th-generation tensor
+// cores (tcgen05.mma, accumulator in tensor memory), with fused epilogues for
+// the surrogate MLP.
+//
+//   C[M x N] = A[M x K] * B[N x K]^T     (A and B K-contiguous, "TN")
+//
+// One CTA of 128 threads owns a 128-row tile of C and all N <= 256 columns.
+// Per K-chunk of 64 the threads copy the A and B chunks from global memory
+// into shared memory in the canonical no-swizzle K-major layout of the
+// tensor core (8-row x 16-byte core matrices; core matrices adjacent in K are
+// 128 B apart (leading byte offset), 8-row groups are 1024 B apart (stride
+// byte offset)), fence them into the async proxy, and one elected thread
+// issues four 128xNx16 MMAs into the TMEM accumulator and commits them to an
+// mbarrier that every thread waits on (with an iteration limit) before the
+// chunk buffers are reused.  The epilogue reads the accumulator back with
+// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = rows of the tile).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ptadd {
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols));
+}
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false if the phase did not complete within `cycles` SM clocks.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, long long cycles)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(mbar, parity))
+        if (clock64() - t0 > cycles) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tc_mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, no swizzle, K-major canonical layout.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo_bytes, uint32_t sbo_bytes)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo_bytes >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of this tensor-core generation
+    return d;                // base offset 0, swizzle mode 0 (none)
+}
+// Instruction descriptor: D FP32, A/B BF16, both K-major, M = 128, N.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ---------------------------------------------------------------- GEMM
+enum GemmEpi : int {
+    EPI_STORE = 0,      // C -> out_f32 (row-major)
+    EPI_BIAS = 1,       // C + bias -> out_f32
+    EPI_BIAS_GELU = 2,  // z = C + bias -> out_f32 (z), GELU(z) -> out_bf16 (+ transposed)
+    EPI_DGELU = 3,      // C * GELU'(zin) -> out_bf16 (+ transposed)
+    EPI_STORE_T = 4,    // C -> out_f32 transposed: out[c * ld_out + r]
+};
+
+struct GemmArgs {
+    const __nv_bfloat16* A;
+    int64_t lda;
+    const __nv_bfloat16* B;
+    int64_t ldb;
+    int64_t M;
+    int N;  // multiple of 16, <= 256
+    int K;  // multiple of 16
+    int epi;
+    const float* bias;
+    float* out_f32;
+    int64_t ld_out;
+    __nv_bfloat16* out_bf16;
+    int64_t ld_bf16;
+    __nv_bfloat16* out_bf16_t;  // element (r, c) at [c * ld_t + r]
+    int64_t ld_t;
+    const float* zin;
+    int64_t ld_z;
+    int* err;  // set to 1 if an MMA wait gave up
+};
+
+constexpr int GEMM_THREADS = 128;
+constexpr int GEMM_KC = 64;                   // K per chunk
+constexpr int GEMM_A_BYTES = 128 * GEMM_KC * 2;  // 16 KB
+constexpr int GEMM_B_BYTES = 256 * GEMM_KC * 2;  // 32 KB (N <= 256)
+// a guard region after the operand buffers keeps every address a descriptor can
+// reach inside this CTA's shared memory
+constexpr int GEMM_GUARD = 64 * 1024;
+constexpr int GEMM_SMEM = GEMM_A_BYTES + GEMM_B_BYTES + GEMM_GUARD + 1024;  // + alignment slack
+constexpr long long MBAR_WAIT_LIMIT = 4000000000LL;  // ~2 s of SM clocks
+
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z)
+{
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+// Copy a [rows x 64] K-chunk (columns k0..k0+63 of a K-contiguous matrix) into
+// the canonical layout at dst; rows >= row_lim or columns >= K read as zero.
+__device__ __forceinline__ void load_chunk(uint8_t* dst, const __nv_bfloat16* src, int64_t ld, int64_t row0,
+                                           int rows, int64_t row_lim, int k0, int K)
+{
+    for (int v = threadIdx.x; v < rows * 8; v += GEMM_THREADS) {
+        const int r = v >> 3, kk = v & 7;
+        const int64_t gr = row0 + r;
+        const int gk = k0 + 8 * kk;
+        uint4 val = make_uint4(0u, 0u, 0u, 0u);
+        if (gr < row_lim && gk < K) val = *reinterpret_cast<const uint4*>(src + gr * ld + gk);
+        *reinterpret_cast<uint4*>(dst + (r >> 3) * 1024 + kk * 128 + (r & 7) * 16) = val;
+    }
+}
+
+__global__ void __launch_bounds__(GEMM_THREADS, 1) tc_gemm_kernel(GemmArgs g)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sA = base;
+    uint8_t* sB = base + GEMM_A_BYTES;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row0 = (int64_t)blockIdx.x * 128;
+    const int N = g.N;
+    const uint32_t ncols = N <= 32 ? 32u : N <= 64 ? 64u : N <= 128 ? 128u : 256u;
+    const uint32_t mb = smem_u32(&mbar);
+
+    if (warp == 0) {
+        tmem_alloc(smem_u32(&tmem_base), ncols);
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 0) mbar_init(mb, 1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = idesc_bf16_f32(128, N);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int k0 = 0; k0 < g.K; k0 += GEMM_KC) {
+        const int kc = min(GEMM_KC, g.K - k0);
+        load_chunk(sA, g.A, g.lda, row0, 128, g.M, k0, g.K);
+        load_chunk(sB, g.B, g.ldb, 0, N, N, k0, g.K);
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            for (int s = 0; s < kc / 16; ++s) {
+                const uint64_t ad = smem_desc(a0 + s * 256, 128, 1024);
+                const uint64_t bd = smem_desc(b0 + s * 256, 128, 1024);
+                tc_mma_bf16(tmem, ad, bd, idesc, (k0 > 0 || s > 0) ? 1u : 0u);
+            }
+            tc_commit(mb);
+        }
+        // every thread waits for the MMAs before the chunk buffers are reused
+        if (!mbar_wait_bounded(mb, phase, MBAR_WAIT_LIMIT)) ok = false;
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+    }
+    tc_fence_after();
+
+    if (ok) {
+        const int64_t r = row0 + warp * 32 + lane;
+        const bool live = r < g.M;
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (!live) continue;
+            if (g.epi == EPI_STORE || g.epi == EPI_BIAS) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) g.out_f32[r * g.ld_out + c0 + i] = v[i] + (g.epi == EPI_BIAS ? g.bias[c0 + i] : 0.f);
+            } else if (g.epi == EPI_STORE_T) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) g.out_f32[(int64_t)(c0 + i) * g.ld_out + r] = v[i];
+            } else if (g.epi == EPI_BIAS_GELU) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float z = v[i] + g.bias[c0 + i];
+                    if (g.out_f32) g.out_f32[r * g.ld_out + c0 + i] = z;
+                    const __nv_bfloat16 h = __float2bfloat16_rn(gelu_f(z));
+                    if (g.out_bf16) g.out_bf16[r * g.ld_bf16 + c0 + i] = h;
+                    if (g.out_bf16_t) g.out_bf16_t[(int64_t)(c0 + i) * g.ld_t + r] = h;
+                }
+            } else {  // EPI_DGELU
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float dz = v[i] * gelu_grad_f(g.zin[r * g.ld_z + c0 + i]);
+                    const __nv_bfloat16 h = __float2bfloat16_rn(dz);
+                    if (g.out_bf16) g.out_bf16[r * g.ld_bf16 + c0 + i] = h;
+                    if (g.out_bf16_t) g.out_bf16_t[(int64_t)(c0 + i) * g.ld_t + r] = h;
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(g.err, 1);
+        // give the tensor core a last bounded chance to finish before TMEM is freed
+        mbar_wait_bounded(mb, phase ^ 1u, MBAR_WAIT_LIMIT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+}  // namespace ptadd

@@ -27,7 +27,8 @@ EXPORTS = ["ptadd_version", "ptadd_create", "ptadd_destroy", "ptadd_last_error",
            "ptadd_get_state", "ptadd_set_state", "ptadd_fma_peak", "ptadd_set_nodes",
            "ptadd_profile_reset", "ptadd_profile_read", "ptadd_forces_noalloc",
            "ptadd_batch_set", "ptadd_batch_set_stress", "ptadd_batch_advance", "ptadd_batch_get_nodes",
-           "ptadd_batch_set_nodes", "ptadd_batch_get_info", "ptadd_batch_autotune", "ptadd_batch_run"]
+           "ptadd_batch_set_nodes", "ptadd_batch_get_info", "ptadd_batch_autotune", "ptadd_batch_run",
+           "ptadd_gemm_bf16"]
 NOALLOC_MAX_SEGMENTS = 16384
 
 
@@ -134,6 +135,8 @@ def load(build_if_missing=True):
     lib.ptadd_batch_run.argtypes = [_VP, ctypes.c_int32, _I64, ctypes.c_int64, _I64, _D, _D, _D, _U8, _D, _D,
                                     ctypes.c_int64, ctypes.c_double, _D, _D]
     lib.ptadd_batch_run.restype = st
+    lib.ptadd_gemm_bf16.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]
+    lib.ptadd_gemm_bf16.restype = st
     lib.ptadd_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]
     lib.ptadd_fma_peak.restype = st
     _lib = lib
@@ -176,6 +179,29 @@ def forces_noalloc(material, n_nodes, xyz_ptr, nxt_ptr, prv_ptr, burgers_ptr, si
     s = _c(sig_app, np.float64)
     _check(lib.ptadd_forces_noalloc(ctypes.byref(m), int(n_nodes), _VP(xyz_ptr), _VP(nxt_ptr), _VP(prv_ptr),
                                     _VP(burgers_ptr), _dptr(s), _VP(F_ptr), _VP(stream) if stream else None))
+
+
+def gemm_bf16(A_bits, B_bits, device=0):
+    """C = A B^T on the tensor cores; A [M,K], B [N,K] as uint16 BF16 bit patterns."""
+    lib = load()
+    A = np.ascontiguousarray(A_bits, dtype=np.uint16)
+    B = np.ascontiguousarray(B_bits, dtype=np.uint16)
+    M, K = A.shape
+    N = B.shape[0]
+    C = np.zeros((M, N), dtype=np.float32)
+    _check(lib.ptadd_gemm_bf16(int(device), M, N, K, A.ctypes.data, B.ctypes.data, C.ctypes.data))
+    return C
+
+
+def to_bf16_bits(x):
+    """Round-to-nearest-even FP32 -> BF16 bit patterns (uint16)."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u >> 16) & 1) + 0x7FFF
+    return ((u + r) >> 16).astype(np.uint16)
+
+
+def from_bf16_bits(b):
+    return (np.asarray(b, dtype=np.uint32) << 16).view(np.float32)
 
 
 class Context:
