@@ -220,6 +220,47 @@ ptadd_status ptadd_batch_run(ptadd_ctx* ctx, int32_t R, const int64_t* node_off,
 ptadd_status ptadd_gemm_bf16(int device, int64_t M, int32_t N, int32_t K, const uint16_t* A, const uint16_t* B,
                              float* C);
 
+/* -------------------------------------------------------------- surrogate */
+/* A learned stand-in for the PTA closure (not in the paper): an MLP
+ * 30 -> 256 -> 256 -> 256 -> 6 with GELU hidden layers, BF16 weights and
+ * activations and FP32 accumulation on the tensor cores, FP32 master weights,
+ * trained with Adam (beta 0.9/0.999, eps 1e-8) on the mean-square error.
+ * Parameters are exchanged packed per layer as W (out x in, row-major) then b,
+ * FP32, ptadd_mlp_param_count() values in all. */
+int64_t ptadd_mlp_param_count(void);
+/* Glorot-uniform weights from a splitmix64 stream of `seed`, zero biases. */
+ptadd_status ptadd_mlp_init(ptadd_ctx* ctx, uint64_t seed);
+ptadd_status ptadd_mlp_set_params(ptadd_ctx* ctx, const float* params, int64_t count);
+ptadd_status ptadd_mlp_get_params(ptadd_ctx* ctx, float* params, int64_t count);
+/* Loss and gradient (packed like the parameters) of one forward/backward pass
+ * over n normalised samples (host xn[n*30], yn[n*6]); no update. */
+ptadd_status ptadd_mlp_loss_grad(ptadd_ctx* ctx, int64_t n, const float* xn, const float* yn, float* grad,
+                                 float* loss);
+/* Adam training on normalised samples: `epochs` passes over a seeded
+ * shuffle, full batches of `batch` (a multiple of 16) only.  loss_per_epoch
+ * (or NULL) receives the mean batch loss of each epoch. */
+ptadd_status ptadd_mlp_train(ptadd_ctx* ctx, int64_t n, const float* xn, const float* yn, int epochs, int batch,
+                             float lr, uint64_t seed, float* loss_per_epoch);
+/* Forward pass on normalised inputs (host arrays xn[n*30] -> yn[n*6]). */
+ptadd_status ptadd_mlp_forward(ptadd_ctx* ctx, int64_t n, const float* xn, float* yn);
+
+/* Closure level.  Raw features per point, feat[n*30]: the 6 applied-stress
+ * components (Pa, Voigt order), the 12 mobile then the 12 sessile line
+ * densities per FCC slip system (1/m^2); labels lp6[n*6]: sym(Lp) in Voigt
+ * order (1/s).  Inputs are mapped to [sigma/200 MPa, log10(rho + 1e10)] and
+ * standardised, labels standardised, with the training set's moments.  The
+ * trust region of a point: inside the per-feature [min, max] box of the
+ * training inputs, and a Mahalanobis distance (training covariance) within the
+ * training set's 99th percentile.  fit (re)trains from the
+ * current weights (initialised from `seed` if none). */
+ptadd_status ptadd_surrogate_fit(ptadd_ctx* ctx, int64_t n, const double* feat, const double* lp6, int epochs,
+                                 int batch, float lr, uint64_t seed, float* loss_per_epoch);
+/* Host arrays; in_region (or NULL) receives 1 inside the trust region. */
+ptadd_status ptadd_surrogate_predict(ptadd_ctx* ctx, int64_t n, const double* feat, double* lp6, uint8_t* in_region);
+/* Device arrays, enqueued on the context's stream without synchronising. */
+ptadd_status ptadd_surrogate_predict_dev(ptadd_ctx* ctx, int64_t n, const double* feat_dev, double* lp6_dev,
+                                         uint8_t* in_region_dev);
+
 /* ------------------------------------------------------------- measurement */
 /* Launch counters and CUDA-event timing of the pair-stress kernels, recorded
  * on the stream they are launched on.  Timing costs two event records per

@@ -117,6 +117,7 @@ void ptadd_destroy(ptadd_ctx* ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     free_network(ctx->net);
     batch_free(ctx);
+    mlp_free(ctx);
     for (auto& e : ctx->ev_open) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);

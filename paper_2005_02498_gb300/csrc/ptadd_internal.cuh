@@ -105,6 +105,8 @@ cudaError_t launch_fma_chains(int fp64, int blocks, int threads, long iters, dou
 
 struct DevBatch;
 void batch_free(ptadd_ctx* ctx);
+struct MlpDev;
+void mlp_free(ptadd_ctx* ctx);
 
 }  // namespace ptadd
 
@@ -119,6 +121,7 @@ struct ptadd_ctx {
     ptadd::DevNetwork net;
     bool have_net = false;
     ptadd::DevBatch* batch = nullptr;  // batched ensemble (ptadd_batch_*)
+    ptadd::MlpDev* mlp = nullptr;      // surrogate (ptadd_mlp_* / ptadd_surrogate_*)
     double sig_app[6] = {0, 0, 0, 0, 0, 0};  // Pa
     // profiling (ptadd_profile_*)
     bool timing = false;

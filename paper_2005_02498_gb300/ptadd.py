@@ -28,7 +28,9 @@ EXPORTS = ["ptadd_version", "ptadd_create", "ptadd_destroy", "ptadd_last_error",
            "ptadd_profile_reset", "ptadd_profile_read", "ptadd_forces_noalloc",
            "ptadd_batch_set", "ptadd_batch_set_stress", "ptadd_batch_advance", "ptadd_batch_get_nodes",
            "ptadd_batch_set_nodes", "ptadd_batch_get_info", "ptadd_batch_autotune", "ptadd_batch_run",
-           "ptadd_gemm_bf16"]
+           "ptadd_gemm_bf16", "ptadd_mlp_param_count", "ptadd_mlp_init", "ptadd_mlp_set_params",
+           "ptadd_mlp_get_params", "ptadd_mlp_loss_grad", "ptadd_mlp_train", "ptadd_mlp_forward",
+           "ptadd_surrogate_fit", "ptadd_surrogate_predict", "ptadd_surrogate_predict_dev"]
 NOALLOC_MAX_SEGMENTS = 16384
 
 
@@ -137,6 +139,28 @@ def load(build_if_missing=True):
     lib.ptadd_batch_run.restype = st
     lib.ptadd_gemm_bf16.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]
     lib.ptadd_gemm_bf16.restype = st
+    _F = ctypes.POINTER(ctypes.c_float)
+    lib.ptadd_mlp_param_count.restype = ctypes.c_int64
+    lib.ptadd_mlp_init.argtypes = [_VP, ctypes.c_uint64]
+    lib.ptadd_mlp_init.restype = st
+    lib.ptadd_mlp_set_params.argtypes = [_VP, _F, ctypes.c_int64]
+    lib.ptadd_mlp_set_params.restype = st
+    lib.ptadd_mlp_get_params.argtypes = [_VP, _F, ctypes.c_int64]
+    lib.ptadd_mlp_get_params.restype = st
+    lib.ptadd_mlp_loss_grad.argtypes = [_VP, ctypes.c_int64, _F, _F, _F, _F]
+    lib.ptadd_mlp_loss_grad.restype = st
+    lib.ptadd_mlp_train.argtypes = [_VP, ctypes.c_int64, _F, _F, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                    ctypes.c_uint64, _F]
+    lib.ptadd_mlp_train.restype = st
+    lib.ptadd_mlp_forward.argtypes = [_VP, ctypes.c_int64, _F, _F]
+    lib.ptadd_mlp_forward.restype = st
+    lib.ptadd_surrogate_fit.argtypes = [_VP, ctypes.c_int64, _D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                        ctypes.c_uint64, _F]
+    lib.ptadd_surrogate_fit.restype = st
+    lib.ptadd_surrogate_predict.argtypes = [_VP, ctypes.c_int64, _D, _D, _U8]
+    lib.ptadd_surrogate_predict.restype = st
+    lib.ptadd_surrogate_predict_dev.argtypes = [_VP, ctypes.c_int64, _VP, _VP, _VP]
+    lib.ptadd_surrogate_predict_dev.restype = st
     lib.ptadd_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]
     lib.ptadd_fma_peak.restype = st
     _lib = lib
@@ -179,6 +203,14 @@ def forces_noalloc(material, n_nodes, xyz_ptr, nxt_ptr, prv_ptr, burgers_ptr, si
     s = _c(sig_app, np.float64)
     _check(lib.ptadd_forces_noalloc(ctypes.byref(m), int(n_nodes), _VP(xyz_ptr), _VP(nxt_ptr), _VP(prv_ptr),
                                     _VP(burgers_ptr), _dptr(s), _VP(F_ptr), _VP(stream) if stream else None))
+
+
+def mlp_param_count():
+    return int(load().ptadd_mlp_param_count())
+
+
+def _fptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
 
 
 def gemm_bf16(A_bits, B_bits, device=0):
@@ -358,3 +390,59 @@ class Context:
     def batch_autotune(self, cache_path=None, force=False):
         _check(self._lib.ptadd_batch_autotune(self._h, cache_path.encode() if cache_path else None,
                                               int(bool(force))))
+
+    # ---------------------------------------------------------- surrogate
+    def mlp_init(self, seed=0):
+        _check(self._lib.ptadd_mlp_init(self._h, int(seed)))
+
+    def mlp_set_params(self, params):
+        p = _c(params, np.float32)
+        _check(self._lib.ptadd_mlp_set_params(self._h, _fptr(p), p.size))
+
+    def mlp_get_params(self):
+        p = np.zeros(mlp_param_count(), np.float32)
+        _check(self._lib.ptadd_mlp_get_params(self._h, _fptr(p), p.size))
+        return p
+
+    def mlp_loss_grad(self, xn, yn):
+        x = _c(xn, np.float32)
+        y = _c(yn, np.float32)
+        g = np.zeros(mlp_param_count(), np.float32)
+        loss = ctypes.c_float(0.0)
+        _check(self._lib.ptadd_mlp_loss_grad(self._h, x.shape[0], _fptr(x), _fptr(y), _fptr(g), ctypes.byref(loss)))
+        return loss.value, g
+
+    def mlp_train(self, xn, yn, epochs, batch=512, lr=1e-3, seed=0):
+        x = _c(xn, np.float32)
+        y = _c(yn, np.float32)
+        losses = np.zeros(max(1, epochs), np.float32)
+        _check(self._lib.ptadd_mlp_train(self._h, x.shape[0], _fptr(x), _fptr(y), int(epochs), int(batch),
+                                         float(lr), int(seed), _fptr(losses)))
+        return losses[:epochs]
+
+    def mlp_forward(self, xn):
+        x = _c(xn, np.float32)
+        y = np.zeros((x.shape[0], 6), np.float32)
+        _check(self._lib.ptadd_mlp_forward(self._h, x.shape[0], _fptr(x), _fptr(y)))
+        return y
+
+    def surrogate_fit(self, feat, lp6, epochs, batch=512, lr=1e-3, seed=0):
+        f = _c(feat, np.float64)
+        y = _c(lp6, np.float64)
+        losses = np.zeros(max(1, epochs), np.float32)
+        _check(self._lib.ptadd_surrogate_fit(self._h, f.shape[0], _dptr(f), _dptr(y), int(epochs), int(batch),
+                                             float(lr), int(seed), _fptr(losses)))
+        return losses[:epochs]
+
+    def surrogate_predict(self, feat):
+        """Returns (lp6 [n,6], in_region [n] bool)."""
+        f = _c(feat, np.float64)
+        y = np.zeros((f.shape[0], 6))
+        r = np.zeros(f.shape[0], np.uint8)
+        _check(self._lib.ptadd_surrogate_predict(self._h, f.shape[0], _dptr(f), _dptr(y),
+                                                 r.ctypes.data_as(_U8)))
+        return y, r.astype(bool)
+
+    def surrogate_predict_dev(self, n, feat_ptr, lp6_ptr, region_ptr=None):
+        _check(self._lib.ptadd_surrogate_predict_dev(self._h, int(n), _VP(feat_ptr), _VP(lp6_ptr),
+                                                     _VP(region_ptr) if region_ptr else None))

@@ -1,0 +1,138 @@
+"""GPU parity of the tensor-core surrogate MLP against the FP64 MLP oracle.
+
+The GPU multiplies BF16 operands (weights, inputs, hidden activations and
+back-propagated gradients are rounded to BF16) and accumulates in FP32.  The
+oracle runs in FP64 on the same BF16-rounded weights and inputs, so the
+remaining difference is the BF16 rounding of the hidden activations and
+gradients: the bar is 2e-2 relative (Frobenius norm per tensor) on gradients
+and outputs, and 3 % on the training-loss curve of 100 full-batch Adam steps.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2005_02498_gb300 import ptadd
+
+pytestmark = pytest.mark.gpu
+DIMS = (30, 256, 256, 256, 6)
+MAT = (48e9, 0.34, 2.556e-10, 2.556e-10, 1e-4)
+
+
+def bf16(x):
+    return ptadd.from_bf16_bits(ptadd.to_bf16_bits(np.asarray(x, np.float32))).astype(np.float64)
+
+
+def split(p):
+    """Packed parameters -> list of (W, b) per layer."""
+    out, off = [], 0
+    for din, dout in zip(DIMS[:-1], DIMS[1:]):
+        W = p[off:off + din * dout].reshape(dout, din)
+        off += din * dout
+        b = p[off:off + dout]
+        off += dout
+        out.append((W, b))
+    return out
+
+
+def weights_bf16(p):
+    """BF16-round the weights (the GPU keeps biases in FP32)."""
+    q = np.asarray(p, np.float64).copy()
+    off = 0
+    for din, dout in zip(DIMS[:-1], DIMS[1:]):
+        q[off:off + din * dout] = bf16(q[off:off + din * dout])
+        off += din * dout + dout
+    return q
+
+
+def relfro(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def target_fn(x):
+    rng = np.random.default_rng(123)
+    A = rng.normal(size=(30, 6)) / np.sqrt(30)
+    return np.tanh(x @ A) + 0.1 * (x[:, :6] ** 2)
+
+
+def test_forward_and_gradient_match_oracle():
+    rng = np.random.default_rng(1)
+    n = 100  # not a multiple of 16: padded rows must not leak into loss or gradients
+    x = rng.normal(size=(n, 30)).astype(np.float32)
+    y = target_fn(x.astype(np.float64)).astype(np.float32)
+    with ptadd.Context(MAT, ptadd.PTADD_FP64, 0) as c:
+        c.mlp_init(seed=7)
+        p = c.mlp_get_params().astype(np.float64)
+        yhat = c.mlp_forward(x)
+        loss, g = c.mlp_loss_grad(x, y)
+    pq = weights_bf16(p)
+    xq = bf16(x)
+    yo = O.mlp_forward(DIMS, pq, xq)
+    assert relfro(yhat, yo) <= 2e-2
+    lo, go = O.mlp_loss_grad(DIMS, pq, xq, y.astype(np.float64))
+    assert abs(loss / lo - 1) <= 2e-2
+    for (Wg, bg), (Wo, bo) in zip(split(g), split(go)):
+        assert relfro(Wg, Wo) <= 2e-2
+        assert relfro(bg, bo) <= 2e-2
+
+
+def test_params_roundtrip_and_padding_stays_zero():
+    with ptadd.Context(MAT, ptadd.PTADD_FP64, 0) as c:
+        c.mlp_init(seed=3)
+        p = c.mlp_get_params()
+        assert p.size == ptadd.mlp_param_count() == 141062
+        c.mlp_set_params(p * 0.5)
+        assert np.array_equal(c.mlp_get_params(), (p * 0.5).astype(np.float32))
+        x = np.random.default_rng(2).normal(size=(64, 30)).astype(np.float32)
+        c.mlp_train(x, target_fn(x.astype(np.float64)).astype(np.float32), epochs=3, batch=32)
+        q = c.mlp_get_params()
+    assert np.all(np.isfinite(q)) and not np.array_equal(q, p * 0.5)
+
+
+def test_training_curve_matches_oracle_adam():
+    rng = np.random.default_rng(5)
+    n = 1024
+    x = rng.normal(size=(n, 30)).astype(np.float32)
+    y = target_fn(x.astype(np.float64)).astype(np.float32)
+    steps = 100
+    with ptadd.Context(MAT, ptadd.PTADD_FP64, 0) as c:
+        c.mlp_init(seed=11)
+        p0 = c.mlp_get_params().astype(np.float64)
+        gpu_losses = c.mlp_train(x, y, epochs=steps, batch=n, lr=1e-3, seed=1)
+    # oracle: full-batch Adam in FP64 from the same (BF16-rounded) start
+    p = weights_bf16(p0)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    xq = bf16(x)
+    ora = []
+    for t in range(1, steps + 1):
+        loss, g = O.mlp_loss_grad(DIMS, p, xq, y.astype(np.float64))
+        ora.append(loss)
+        O.adam_step(p, g, m, v, t, lr=1e-3)
+    ora = np.array(ora)
+    assert ora[-1] < 0.5 * ora[0]  # it learns
+    dev = np.abs(gpu_losses - ora) / ora
+    print("max relative deviation of the GPU loss curve from the oracle: %.3e" % dev.max())
+    assert dev.max() <= 3e-2
+
+
+def test_surrogate_fit_predict_and_trust_region():
+    rng = np.random.default_rng(8)
+    n = 4096
+    sig = rng.uniform(-200e6, 200e6, size=(n, 6))
+    rho = 10 ** rng.uniform(11, 13, size=(n, 24))
+    feat = np.hstack([sig, rho])
+    # a smooth synthetic closure: resolved-stress-like response times density
+    lp = np.tanh(sig / 1e8) * (np.log10(rho[:, :6]) - 10.0) * 50.0
+    with ptadd.Context(MAT, ptadd.PTADD_FP64, 0) as c:
+        losses = c.surrogate_fit(feat[:3584], lp[:3584], epochs=60, batch=256, lr=2e-3, seed=3)
+        pred, inr = c.surrogate_predict(feat[3584:])
+        far = feat[:4].copy()
+        far[:, 0] = 5e9  # 25x the training stress range
+        _, inr_far = c.surrogate_predict(far)
+    assert losses[-1] < 0.1 * losses[0]
+    err = np.linalg.norm(pred - lp[3584:]) / np.linalg.norm(lp[3584:])
+    print("hold-out relative error of the synthetic closure: %.3e, in region %.2f" % (err, inr.mean()))
+    assert err < 0.1
+    assert inr.mean() > 0.9  # in-distribution points: box of the training set, 99th percentile
+    assert not inr_far.any()
