@@ -221,7 +221,8 @@ def run_ours(args):
     mat = W.Material()
     net = W.large_loop_network(seed=W.LARGE_LOOPS["seed"] + rank)
     dt = W.LARGE_LOOPS["dt"]
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()  # a real stream shared by the library and the timing events
+    torch.cuda.set_stream(stream)
     ctx = ptadd.Context(mat.as_tuple(), prec, local)
     ctx.set_stream(stream.cuda_stream)
     ctx.set_network(net)

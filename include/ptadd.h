@@ -261,6 +261,11 @@ ptadd_status ptadd_surrogate_predict(ptadd_ctx* ctx, int64_t n, const double* fe
 ptadd_status ptadd_surrogate_predict_dev(ptadd_ctx* ctx, int64_t n, const double* feat_dev, double* lp6_dev,
                                          uint8_t* in_region_dev);
 
+/* Save / restore a fitted surrogate (weights, input/output maps, trust
+ * region) as one blob; buf = NULL asks for the size. */
+ptadd_status ptadd_surrogate_get_state(ptadd_ctx* ctx, void* buf, size_t* bytes);
+ptadd_status ptadd_surrogate_set_state(ptadd_ctx* ctx, const void* buf, size_t bytes);
+
 /* ------------------------------------------------------------- measurement */
 /* Launch counters and CUDA-event timing of the pair-stress kernels, recorded
  * on the stream they are launched on.  Timing costs two event records per

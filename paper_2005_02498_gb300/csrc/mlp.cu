@@ -59,7 +59,7 @@ struct MlpDev {
     double box_lo[NIN], box_hi[NIN];
     double chol[NIN * NIN];  // lower Cholesky factor of the training covariance (standardised x)
     double d2_thr = 0.0;
-    double* d_norm = nullptr;  // device copy: xm, xs, ym, ys, box_lo, box_hi, chol, d2_thr
+    float* d_norm = nullptr;  // device copy (FP32): xm, xs, ym, ys, box_lo, box_hi, chol, d2_thr
 };
 
 namespace {
@@ -283,25 +283,26 @@ struct NormView {
     double d2_thr;
 };
 
-__device__ __forceinline__ double feature(const double* raw, int c)
+__device__ __forceinline__ float feature(const double* raw, int c)
 {
-    return c < 6 ? raw[c] / SIG_SCALE : log10(raw[c] + RHO_FLOOR);
+    return c < 6 ? (float)(raw[c] * (1.0 / SIG_SCALE)) : log10f((float)raw[c] + (float)RHO_FLOOR);
 }
 
-// raw features [n x 30] -> standardised BF16 X [rows x 32] (and X^T), and the
-// trust-region flag of every point.
-__global__ void surr_inputs(int64_t n, int64_t rows, const double* __restrict__ raw, const double* __restrict__ nv,
+// raw features [n x 30] -> standardised BF16 X [rows x 32], and the
+// trust-region flag of every point.  FP32 throughout: the values feed BF16
+// operands, and FP64 runs at 1/64 of the FP32 rate on this GPU.
+__global__ void surr_inputs(int64_t n, int64_t rows, const double* __restrict__ raw, const float* __restrict__ nv,
                             __nv_bfloat16* __restrict__ X, uint8_t* __restrict__ in_region)
 {
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r >= rows) return;
-    const double* xm = nv;
-    const double* xs = nv + NIN;
-    const double* lo = nv + 2 * NIN + 2 * NOUT;
-    const double* hi = lo + NIN;
-    const double* L = hi + NIN;
-    const double d2_thr = L[NIN * NIN];
-    double z[NIN];
+    const float* xm = nv;
+    const float* xs = nv + NIN;
+    const float* lo = nv + 2 * NIN + 2 * NOUT;
+    const float* hi = lo + NIN;
+    const float* L = hi + NIN;
+    const float d2_thr = L[NIN * NIN];
+    float z[NIN];
     bool inbox = true;
     if (r < n) {
         for (int c = 0; c < NIN; ++c) {
@@ -309,14 +310,14 @@ __global__ void surr_inputs(int64_t n, int64_t rows, const double* __restrict__ 
             inbox = inbox && z[c] >= lo[c] && z[c] <= hi[c];
         }
     } else {
-        for (int c = 0; c < NIN; ++c) z[c] = 0.0;
+        for (int c = 0; c < NIN; ++c) z[c] = 0.0f;
     }
-    for (int c = 0; c < 32; ++c) X[r * 32 + c] = __float2bfloat16_rn(c < NIN ? (float)z[c] : 0.0f);
+    for (int c = 0; c < 32; ++c) X[r * 32 + c] = __float2bfloat16_rn(c < NIN ? z[c] : 0.0f);
     if (r < n && in_region) {
         // Mahalanobis distance^2 = |L^{-1} z|^2 (forward substitution)
-        double w[NIN], d2 = 0.0;
+        float w[NIN], d2 = 0.0f;
         for (int i = 0; i < NIN; ++i) {
-            double s = z[i];
+            float s = z[i];
             for (int j = 0; j < i; ++j) s -= L[i * NIN + j] * w[j];
             w[i] = s / L[i * NIN + i];
             d2 += w[i] * w[i];
@@ -325,15 +326,15 @@ __global__ void surr_inputs(int64_t n, int64_t rows, const double* __restrict__ 
     }
 }
 
-__global__ void surr_outputs(int64_t n, const float* __restrict__ Y, const double* __restrict__ nv,
+__global__ void surr_outputs(int64_t n, const float* __restrict__ Y, const float* __restrict__ nv,
                              double* __restrict__ lp6)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n * NOUT) return;
-    const double* ym = nv + 2 * NIN;
-    const double* ys = ym + NOUT;
+    const float* ym = nv + 2 * NIN;
+    const float* ys = ym + NOUT;
     const int c = (int)(i % NOUT);
-    lp6[i] = (double)Y[(i / NOUT) * 16 + c] * ys[c] + ym[c];
+    lp6[i] = (double)(Y[(i / NOUT) * 16 + c] * ys[c] + ym[c]);
 }
 
 // ------------------------------------------------------------ passes
@@ -769,7 +770,7 @@ ptadd_status ptadd_mlp_forward(ptadd_ctx* ctx, int64_t n, const float* xn, float
 // ----------------------------------------------------------- closures
 static double host_feature(const double* raw, int c)
 {
-    return c < 6 ? raw[c] / SIG_SCALE : log10(raw[c] + RHO_FLOOR);
+    return c < 6 ? (double)(float)(raw[c] * (1.0 / SIG_SCALE)) : (double)log10f((float)raw[c] + (float)RHO_FLOOR);
 }
 
 ptadd_status ptadd_surrogate_fit(ptadd_ctx* ctx, int64_t n, const double* feat, const double* lp6, int epochs,
@@ -864,7 +865,10 @@ ptadd_status ptadd_surrogate_fit(ptadd_ctx* ctx, int64_t n, const double* feat, 
     memcpy(&nv[3 * NIN + 2 * NOUT], m.box_hi, sizeof(m.box_hi));
     memcpy(&nv[4 * NIN + 2 * NOUT], m.chol, sizeof(m.chol));
     nv[4 * NIN + 2 * NOUT + NIN * NIN] = m.d2_thr;
-    PTADD_CUDA(cudaMemcpy(m.d_norm, nv.data(), nv.size() * sizeof(double), cudaMemcpyHostToDevice));
+    {
+        std::vector<float> nvf(nv.begin(), nv.end());
+        PTADD_CUDA(cudaMemcpy(m.d_norm, nvf.data(), nvf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
     // normalised training arrays
     std::vector<float> xn((size_t)n * NIN), yn((size_t)n * NOUT);
     for (int64_t i = 0; i < n * NIN; ++i) xn[i] = (float)z[i];
@@ -939,6 +943,85 @@ ptadd_status ptadd_surrogate_predict(ptadd_ctx* ctx, int64_t n, const double* fe
         set_error("a tensor-core wait gave up");
         return PTADD_ERR_TIMEOUT;
     }
+    return PTADD_OK;
+}
+
+
+// state blob: magic, param count, params (FP32), then the input/output maps
+static const uint64_t SURR_MAGIC = 0x50544144534d4c31ull;  // "PTADSML1"
+
+static size_t surr_state_bytes()
+{
+    return 2 * sizeof(uint64_t) + (size_t)packed_count() * sizeof(float) +
+           (size_t)(4 * NIN + 2 * NOUT + NIN * NIN + 1) * sizeof(double);
+}
+
+ptadd_status ptadd_surrogate_get_state(ptadd_ctx* ctx, void* buf, size_t* bytes)
+{
+    ptadd_status st = need_mlp(ctx);
+    if (st != PTADD_OK) return st;
+    if (!bytes) return marg("bytes is NULL");
+    MlpDev& m = *ctx->mlp;
+    if (!m.have_norm) {
+        set_error("surrogate has no input/output maps to save");
+        return PTADD_ERR_STATE;
+    }
+    const size_t need = surr_state_bytes();
+    if (!buf) {
+        *bytes = need;
+        return PTADD_OK;
+    }
+    if (*bytes < need) return marg("state buffer too small");
+    char* p = (char*)buf;
+    const uint64_t hdr[2] = {SURR_MAGIC, (uint64_t)packed_count()};
+    memcpy(p, hdr, sizeof(hdr));
+    p += sizeof(hdr);
+    st = ptadd_mlp_get_params(ctx, (float*)p, packed_count());
+    if (st != PTADD_OK) return st;
+    p += (size_t)packed_count() * sizeof(float);
+    double* d = (double*)p;
+    memcpy(d, m.xm, sizeof(m.xm));
+    memcpy(d + NIN, m.xs, sizeof(m.xs));
+    memcpy(d + 2 * NIN, m.ym, sizeof(m.ym));
+    memcpy(d + 2 * NIN + NOUT, m.ys, sizeof(m.ys));
+    memcpy(d + 2 * NIN + 2 * NOUT, m.box_lo, sizeof(m.box_lo));
+    memcpy(d + 3 * NIN + 2 * NOUT, m.box_hi, sizeof(m.box_hi));
+    memcpy(d + 4 * NIN + 2 * NOUT, m.chol, sizeof(m.chol));
+    d[4 * NIN + 2 * NOUT + NIN * NIN] = m.d2_thr;
+    *bytes = need;
+    return PTADD_OK;
+}
+
+ptadd_status ptadd_surrogate_set_state(ptadd_ctx* ctx, const void* buf, size_t bytes)
+{
+    if (!ctx) return marg("null context");
+    if (!buf || bytes != surr_state_bytes()) return marg("state blob has the wrong size");
+    const char* p = (const char*)buf;
+    uint64_t hdr[2];
+    memcpy(hdr, p, sizeof(hdr));
+    if (hdr[0] != SURR_MAGIC || hdr[1] != (uint64_t)packed_count()) return marg("not a surrogate state blob");
+    p += sizeof(hdr);
+    std::vector<float> params((size_t)packed_count());
+    memcpy(params.data(), p, params.size() * sizeof(float));
+    ptadd_status st = ptadd_mlp_set_params(ctx, params.data(), packed_count());
+    if (st != PTADD_OK) return st;
+    p += params.size() * sizeof(float);
+    MlpDev& m = *ctx->mlp;
+    std::vector<double> nv(4 * NIN + 2 * NOUT + NIN * NIN + 1);
+    memcpy(nv.data(), p, nv.size() * sizeof(double));
+    memcpy(m.xm, &nv[0], sizeof(m.xm));
+    memcpy(m.xs, &nv[NIN], sizeof(m.xs));
+    memcpy(m.ym, &nv[2 * NIN], sizeof(m.ym));
+    memcpy(m.ys, &nv[2 * NIN + NOUT], sizeof(m.ys));
+    memcpy(m.box_lo, &nv[2 * NIN + 2 * NOUT], sizeof(m.box_lo));
+    memcpy(m.box_hi, &nv[3 * NIN + 2 * NOUT], sizeof(m.box_hi));
+    memcpy(m.chol, &nv[4 * NIN + 2 * NOUT], sizeof(m.chol));
+    m.d2_thr = nv[4 * NIN + 2 * NOUT + NIN * NIN];
+    {
+        std::vector<float> nvf(nv.begin(), nv.end());
+        PTADD_CUDA(cudaMemcpy(m.d_norm, nvf.data(), nvf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    m.have_norm = true;
     return PTADD_OK;
 }
 

@@ -30,7 +30,8 @@ EXPORTS = ["ptadd_version", "ptadd_create", "ptadd_destroy", "ptadd_last_error",
            "ptadd_batch_set_nodes", "ptadd_batch_get_info", "ptadd_batch_autotune", "ptadd_batch_run",
            "ptadd_gemm_bf16", "ptadd_mlp_param_count", "ptadd_mlp_init", "ptadd_mlp_set_params",
            "ptadd_mlp_get_params", "ptadd_mlp_loss_grad", "ptadd_mlp_train", "ptadd_mlp_forward",
-           "ptadd_surrogate_fit", "ptadd_surrogate_predict", "ptadd_surrogate_predict_dev"]
+           "ptadd_surrogate_fit", "ptadd_surrogate_predict", "ptadd_surrogate_predict_dev",
+           "ptadd_surrogate_get_state", "ptadd_surrogate_set_state"]
 NOALLOC_MAX_SEGMENTS = 16384
 
 
@@ -161,6 +162,10 @@ def load(build_if_missing=True):
     lib.ptadd_surrogate_predict.restype = st
     lib.ptadd_surrogate_predict_dev.argtypes = [_VP, ctypes.c_int64, _VP, _VP, _VP]
     lib.ptadd_surrogate_predict_dev.restype = st
+    lib.ptadd_surrogate_get_state.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_size_t)]
+    lib.ptadd_surrogate_get_state.restype = st
+    lib.ptadd_surrogate_set_state.argtypes = [_VP, _VP, ctypes.c_size_t]
+    lib.ptadd_surrogate_set_state.restype = st
     lib.ptadd_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, _D]
     lib.ptadd_fma_peak.restype = st
     _lib = lib
@@ -446,3 +451,14 @@ class Context:
     def surrogate_predict_dev(self, n, feat_ptr, lp6_ptr, region_ptr=None):
         _check(self._lib.ptadd_surrogate_predict_dev(self._h, int(n), _VP(feat_ptr), _VP(lp6_ptr),
                                                      _VP(region_ptr) if region_ptr else None))
+
+    def surrogate_get_state(self):
+        n = ctypes.c_size_t(0)
+        _check(self._lib.ptadd_surrogate_get_state(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self._lib.ptadd_surrogate_get_state(self._h, ctypes.cast(buf, _VP), ctypes.byref(n)))
+        return bytes(buf.raw[:n.value])
+
+    def surrogate_set_state(self, blob):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(self._lib.ptadd_surrogate_set_state(self._h, ctypes.cast(buf, _VP), len(blob)))

@@ -1,0 +1,200 @@
+"""Surrogate closure: generate DD-labelled samples, train, evaluate, time.
+
+    python -m paper_2005_02498_gb300.surrogate --samples 20000 --epochs 200
+
+A closure input is (sigma, mobile and sessile line density per slip
+system); a DD closure at that input is the burst-averaged plastic distortion
+rate sym(R^Lp) (Voigt order) of a realisation of `--loops` glide loops drawn
+to follow those densities (`workloads.realisation_for_densities`), computed
+by batched mixed-precision DD bursts (`--dt`, `--steps`).  Realisations with
+the same input differ, so a single closure is noisy: the network is trained
+on one realisation per training point (it regresses to the conditional
+mean) and judged on hold-out points against the mean of `--members`
+realisations; the spread of single realisations around those means is
+reported as the noise floor.  A subset is relabelled with plain FP64 DD.
+Inference is timed on `--infer` points resampled from the training
+features, device-resident, and compared with the DD closures/s of the same
+closure definition.  Prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import ptadd
+from . import workloads as W
+
+
+def sym_voigt(Lp):
+    """[R,3,3] -> [R,6] sym(Lp) in the order xx, yy, zz, yz, xz, xy."""
+    S = 0.5 * (Lp + np.transpose(Lp, (0, 2, 1)))
+    return np.stack([S[:, 0, 0], S[:, 1, 1], S[:, 2, 2], S[:, 1, 2], S[:, 0, 2], S[:, 0, 1]], axis=1)
+
+
+def label(ctx, batch, steps, dt):
+    """DD closures of every realisation of a batch: sym(R^Lp) [R, 6]."""
+    ctx.batch_set(batch)
+    Lp, _ = ctx.batch_advance(steps, dt)
+    return sym_voigt(Lp)
+
+
+def feature_points(rng, n, rho_min=2e12, rho_max=2e13, stress_max=200e6):
+    """Closure inputs: stress ~ U(-200, 200) MPa per component; total mobile and
+    sessile densities log-uniform in [rho_min, rho_max]; per-system shares
+    ~ Dirichlet(1, ..., 1) for each population.  [n, 30]."""
+    f = np.zeros((n, 30))
+    f[:, :6] = rng.uniform(-stress_max, stress_max, size=(n, 6))
+    for col in (6, 18):
+        tot = 10 ** rng.uniform(np.log10(rho_min), np.log10(rho_max), size=n)
+        f[:, col:col + 12] = rng.dirichlet(np.ones(12), size=n) * tot[:, None]
+    return f
+
+
+def generate(ctx, feats, members, seed, steps, dt, n_loops=48, chunk=1024):
+    """DD closures at the given feature points: the mean of sym(R^Lp) over
+    `members` realisations drawn for each point (realisation_for_densities)."""
+    rng = np.random.default_rng(seed)
+    n = feats.shape[0]
+    jobs = [(i, m) for i in range(n) for m in range(members)]
+    acc = np.zeros((n, 6))
+    t0 = time.perf_counter()
+    pairs = 0
+    for s0 in range(0, len(jobs), chunk):
+        part = jobs[s0:s0 + chunk]
+        nets = [W.realisation_for_densities(rng, feats[i, :6], feats[i, 6:18], feats[i, 18:], n_loops=n_loops)
+                for i, _ in part]
+        lab = label(ctx, W.batch_from_networks(nets), steps, dt)
+        pairs += ctx.batch_info()["pairs_per_step"] * steps
+        for (i, _), y in zip(part, lab):
+            acc[i] += y
+    return acc / members, time.perf_counter() - t0, pairs
+
+
+def relerr(pred, ref):
+    return float(np.linalg.norm(pred - ref) / np.linalg.norm(ref))
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--samples", type=int, default=20000)
+    p.add_argument("--holdout", type=float, default=0.1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--dt", type=float, default=5e-13)
+    p.add_argument("--seed", type=int, default=1004)
+    p.add_argument("--epochs", type=int, default=200, help="maximum epochs")
+    p.add_argument("--round-epochs", type=int, default=5)
+    p.add_argument("--patience", type=int, default=4)
+    p.add_argument("--val-frac", type=float, default=0.1)
+    p.add_argument("--save-data", default=None, help="write the features and labels (npz)")
+    p.add_argument("--batch", type=int, default=512)
+    p.add_argument("--lr", type=float, default=1e-3)
+    p.add_argument("--fp64-check", type=int, default=128, help="hold-out points relabelled with FP64 DD")
+    p.add_argument("--members", type=int, default=16, help="realisations per hold-out ensemble mean")
+    p.add_argument("--loops", type=int, default=48, help="loops per realisation")
+    p.add_argument("--infer", type=int, default=1 << 20)
+    p.add_argument("--device", type=int, default=0)
+    p.add_argument("--save", default=None, help="write the fitted surrogate state to this file")
+    a = p.parse_args(argv)
+
+    mat = W.Material().as_tuple()
+    out = {"samples": a.samples, "steps": a.steps, "dt": a.dt, "seed": a.seed, "loops_per_realisation": a.loops,
+           "holdout_members": a.members}
+    rng = np.random.default_rng(a.seed)
+    ntr = int(round(a.samples * (1 - a.holdout)))
+    X = feature_points(rng, a.samples)
+    with ptadd.Context(mat, ptadd.PTADD_MIXED, a.device) as ctx:
+        # training labels: one realisation per point; hold-out labels: ensemble means
+        Ytr, t_gen, pairs = generate(ctx, X[:ntr], 1, a.seed + 1, a.steps, a.dt, a.loops)
+        Yho, t_ho, _ = generate(ctx, X[ntr:], a.members, a.seed + 2, a.steps, a.dt, a.loops)
+        out.update({"dd_label_s": t_gen, "dd_closures_per_s": ntr / t_gen, "dd_pair_evals_per_s": pairs / t_gen,
+                    "holdout_label_s": t_ho})
+        # noise floor: single-realisation labels around the hold-out ensemble means
+        Y1, _, _ = generate(ctx, X[ntr:], 1, a.seed + 3, a.steps, a.dt, a.loops)
+        # early stopping: the labels are single noisy realisations, so the
+        # network is trained in rounds and the round with the lowest error on
+        # a validation split (also single realisations) is kept
+        nval = max(64, int(a.val_frac * ntr))
+        nfit = ntr - nval
+        t0 = time.perf_counter()
+        best, best_err, curve, bad = None, np.inf, [], 0
+        for rnd in range(max(1, a.epochs // a.round_epochs)):
+            losses = ctx.surrogate_fit(X[:nfit], Ytr[:nfit], epochs=a.round_epochs, batch=a.batch, lr=a.lr,
+                                       seed=a.seed + rnd)
+            pv, _ = ctx.surrogate_predict(X[nfit:ntr])
+            e = relerr(pv, Ytr[nfit:ntr])
+            curve.append([(rnd + 1) * a.round_epochs, float(losses[-1]), e])
+            if e < best_err - 1e-4:
+                best, best_err, bad = ctx.surrogate_get_state(), e, 0
+            else:
+                bad += 1
+                if bad >= a.patience:
+                    break
+        ctx.surrogate_set_state(best)
+        out["train_s"] = time.perf_counter() - t0
+        out["training_curve_epoch_loss_valerr"] = curve
+        out["best_val_rel_err"] = best_err
+        pred, inr = ctx.surrogate_predict(X[ntr:])
+        out["holdout"] = {
+            "n": int(Yho.shape[0]),
+            "rel_err_vs_ensemble_mean": relerr(pred, Yho),
+            "rel_err_in_region": relerr(pred[inr], Yho[inr]) if inr.any() else None,
+            "in_region_frac": float(inr.mean()),
+            "single_realisation_rel_err_vs_ensemble_mean": relerr(Y1, Yho),
+            "ensemble_mean_noise_floor": relerr(Y1, Yho) / np.sqrt(a.members),
+            "mean_predictor_rel_err": relerr(np.broadcast_to(Ytr.mean(0), Yho.shape), Yho),
+            "label_norm_median": float(np.median(np.linalg.norm(Yho, axis=1))),
+        }
+        train_pred, _ = ctx.surrogate_predict(X[:nfit])
+        out["train_rel_err_vs_single_labels"] = relerr(train_pred, Ytr[:nfit])
+        if a.save_data:
+            np.savez_compressed(a.save_data, X=X, Ytr=Ytr, Yho=Yho, Y1=Y1)
+        if a.save:
+            with open(a.save, "wb") as fh:
+                fh.write(ctx.surrogate_get_state())
+
+        # surrogate inference on device-resident points resampled from the training features
+        try:
+            import torch
+            feats = X[rng.integers(0, ntr, size=a.infer)]
+            fd = torch.from_numpy(feats).cuda(a.device)
+            yd = torch.empty((a.infer, 6), dtype=torch.float64, device=fd.device)
+            rd = torch.empty(a.infer, dtype=torch.uint8, device=fd.device)
+            st = torch.cuda.Stream(device=fd.device)  # a real (non-default) stream shared with the library
+            torch.cuda.synchronize()
+            ctx.set_stream(st.cuda_stream)
+            ctx.surrogate_predict_dev(a.infer, fd.data_ptr(), yd.data_ptr(), rd.data_ptr())  # warm-up
+            st.synchronize()
+            reps = 10
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                ctx.surrogate_predict_dev(a.infer, fd.data_ptr(), yd.data_ptr(), rd.data_ptr())
+            e1.record(st)
+            st.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            ctx.set_stream(None)
+            flops = 2.0 * (30 * 256 + 256 * 256 * 2 + 256 * 6) * a.infer
+            out["inference"] = {"points": a.infer, "ms": ms, "closures_per_s": a.infer / (ms * 1e-3),
+                                "tflops_algorithmic": flops / (ms * 1e-3) / 1e12,
+                                "in_region_frac": float(rd.float().mean().item()),
+                                "gain_vs_dd_closures": (a.infer / (ms * 1e-3)) / out["dd_closures_per_s"]}
+        except ImportError:
+            out["inference"] = None
+
+    if a.fp64_check > 0:
+        k = min(a.fp64_check, a.samples - ntr)
+        with ptadd.Context(mat, ptadd.PTADD_FP64, a.device) as ctx64:
+            y64, t64, _ = generate(ctx64, X[ntr:ntr + k], 1, a.seed + 3, a.steps, a.dt, a.loops)
+        out["fp64_check"] = {"n": k, "mixed_vs_fp64_rel_err": relerr(Y1[:k], y64),
+                             "fp64_dd_closures_per_s": k / t64}
+    print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

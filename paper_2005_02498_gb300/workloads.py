@@ -274,3 +274,110 @@ def batch_from_networks(nets):
                  np.ascontiguousarray(np.concatenate([nt.normal for nt in nets])),
                  np.concatenate([nt.pinned for nt in nets]).astype(np.uint8),
                  np.stack([nt.sig_app for nt in nets]), np.array([nt.volume for nt in nets], float))
+
+
+# --------------------------------------------------------------------------
+# Closure samples for the surrogate: realisations whose per-slip-system line
+# densities vary, and the 30 closure features of each realisation.
+# --------------------------------------------------------------------------
+def slip_system_index(burgers, normal):
+    """Index (0..11) of the FCC slip system of each loop, matching +-b_hat and +-n."""
+    bh, nh = fcc_slip_systems()
+    b = burgers / np.linalg.norm(burgers, axis=1, keepdims=True)
+    sb = np.abs(b @ bh.T)
+    sn = np.abs(normal @ nh.T)
+    idx = np.argmax(sb * sn, axis=1)
+    return idx
+
+
+def closure_features(batch):
+    """[R, 30]: applied stress (6, Pa), mobile (12) and sessile (12) line
+    densities per FCC slip system (1/m^2) of every realisation."""
+    sys_idx = slip_system_index(batch.burgers, batch.normal)
+    feats = np.zeros((batch.R, 30))
+    feats[:, :6] = batch.sig6
+    for r in range(batch.R):
+        l0, l1 = int(batch.loop_base[r]), int(batch.loop_base[r + 1])
+        for k in range(l0, l1):
+            a, b = int(batch.loop_off[k]), int(batch.loop_off[k + 1])
+            x = batch.xyz[a:b]
+            per = np.sum(np.linalg.norm(np.roll(x, -1, axis=0) - x, axis=1))
+            col = 18 if batch.pinned[a] else 6
+            feats[r, col + sys_idx[k]] += per / batch.volume[r]
+    return feats
+
+
+def closure_ensemble(seed, R, loops_min=16, loops_max=64, density_min=8.0, density_max=32.0,
+                     stress_max=200e6, sessile_min=0.1, sessile_max=0.9, nodes_per_loop=32):
+    """R independent realisations for closure samples.
+
+    Per realisation: loop count ~ U{loops_min..loops_max}; loop density
+    ~ U(density_min, density_max) per um^3 (sets the cube); slip-system
+    weights ~ Dirichlet(1, ..., 1) and each loop's system drawn from them;
+    radius ~ U(0.05, 0.2) um; every stress component ~ U(-stress_max,
+    stress_max); whole loops pinned in random order until the pinned line
+    fraction reaches f ~ U(sessile_min, sessile_max).
+    Returns (Batch, features [R, 30]).
+    """
+    rng = np.random.default_rng(seed)
+    nets = []
+    for _ in range(R):
+        nl = int(rng.integers(loops_min, loops_max + 1))
+        dens = rng.uniform(density_min, density_max)
+        edge = (nl / dens) ** (1.0 / 3.0) * MICRON
+        w = rng.dirichlet(np.ones(12))
+        systems = rng.choice(12, size=nl, p=w)
+        xyz, off, bv, nv = _loops_with_systems(rng, systems, edge, nodes_per_loop)
+        frac = rng.uniform(sessile_min, sessile_max)
+        seg = np.roll(xyz.reshape(nl, nodes_per_loop, 3), -1, axis=1) - xyz.reshape(nl, nodes_per_loop, 3)
+        loop_len = np.sqrt((seg ** 2).sum(-1)).sum(-1)
+        pinned_loop = np.zeros(nl, bool)
+        acc, tot = 0.0, loop_len.sum()
+        for k in rng.permutation(nl):
+            if acc >= frac * tot:
+                break
+            pinned_loop[k] = True
+            acc += loop_len[k]
+        pin = np.repeat(pinned_loop, nodes_per_loop).astype(np.uint8)
+        nets.append(Network(xyz, off, bv, nv, pin, edge ** 3, rng.uniform(-stress_max, stress_max, size=6)))
+    batch = batch_from_networks(nets)
+    return batch, closure_features(batch)
+
+
+def _loops_with_systems(rng, systems, edge, nodes_per_loop, r_min=0.05 * MICRON, r_max=0.2 * MICRON):
+    bh, nh = fcc_slip_systems()
+    n = len(systems)
+    radius = rng.uniform(r_min, r_max, size=n)
+    centre = rng.uniform(0.0, edge, size=(n, 3))
+    phi0 = rng.uniform(0.0, 2.0 * math.pi, size=n)
+    sense = rng.choice(np.array([-1.0, 1.0]), size=n)
+    e1 = bh[systems]
+    nrm = nh[systems]
+    e2 = np.cross(nrm, e1)
+    k = np.arange(nodes_per_loop, dtype=np.float64)
+    phi = phi0[:, None] + sense[:, None] * (2.0 * math.pi / nodes_per_loop) * k[None, :]
+    xyz = (centre[:, None, :] + radius[:, None, None] * (np.cos(phi)[:, :, None] * e1[:, None, :]
+                                                         + np.sin(phi)[:, :, None] * e2[:, None, :]))
+    off = np.arange(n + 1, dtype=np.int64) * nodes_per_loop
+    return (np.ascontiguousarray(xyz.reshape(-1, 3)), off, np.ascontiguousarray(BURGERS * e1),
+            np.ascontiguousarray(nrm))
+
+
+def realisation_for_densities(rng, sig6, rho_m, rho_s, n_loops=32, nodes_per_loop=32,
+                              r_min=0.05 * MICRON, r_max=0.2 * MICRON):
+    """One realisation whose mobile/sessile line densities per slip system
+    follow rho_m[12], rho_s[12] (1/m^2) on average: n_loops loops split over
+    the 24 (system, mobile/sessile) classes in proportion to their density,
+    the cube volume set so that the total density matches."""
+    dens = np.concatenate([np.asarray(rho_m, float), np.asarray(rho_s, float)])
+    tot = dens.sum()
+    p = dens / tot if tot > 0 else np.full(24, 1.0 / 24)
+    cls = rng.choice(24, size=n_loops, p=p)
+    systems = cls % 12
+    xyz_tmp_edge = 1.0 * MICRON
+    mean_perim = nodes_per_loop * 2 * (0.5 * (r_min + r_max)) * math.sin(math.pi / nodes_per_loop)
+    volume = n_loops * mean_perim / tot if tot > 0 else xyz_tmp_edge ** 3
+    edge = volume ** (1.0 / 3.0)
+    xyz, off, bv, nv = _loops_with_systems(rng, systems, edge, nodes_per_loop, r_min, r_max)
+    pin = np.repeat((cls >= 12).astype(np.uint8), nodes_per_loop)
+    return Network(xyz, off, bv, nv, pin, edge ** 3, np.asarray(sig6, float).copy())
