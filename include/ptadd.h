@@ -285,9 +285,10 @@ ptadd_status ptadd_profile_reset(ptadd_ctx* ctx, int timing);
 ptadd_status ptadd_profile_read(ptadd_ctx* ctx, ptadd_profile* out);
 
 /* Throughput of dependent fused multiply-add chains on every SM of `device`
- * (FP64 if fp64 != 0, else FP32), run for about `seconds`; *flops receives
- * FLOP/s counting an FMA as 2.  The non-tensor arithmetic peak the pair
- * kernels are compared against. */
+ * (fp64 = 1: FP64; 0: FP32; 2: packed FP32 pairs, two FMAs per
+ * instruction), run for about `seconds`; *flops receives FLOP/s counting an
+ * FMA as 2.  The non-tensor arithmetic peak the pair kernels are compared
+ * against. */
 ptadd_status ptadd_fma_peak(int device, int fp64, double seconds, double* flops);
 
 /* ------------------------------------------------------ no device allocation */

@@ -81,6 +81,7 @@ struct DevBatch {
     int* flag = nullptr;
     unsigned long long* near_count = nullptr;
     double* staging = nullptr;
+    double* k64 = nullptr;  // {a2, c1, c2} for the near-field path
     // host copies
     std::vector<int64_t> node_off, tgt_off;
     std::vector<double> volume, origin, sh;
@@ -97,7 +98,7 @@ namespace {
 
 constexpr int BRED = 256;   // nodes per reduction block
 constexpr int TILE_FP64 = 128;
-constexpr int TILE_MIX = 256;
+constexpr int TILE_MIX = 128;
 
 // ------------------------------------------------------------ kernels
 __global__ void batch_prep_kernel(int64_t n, const double* __restrict__ pos, const int32_t* __restrict__ nxt,
@@ -153,6 +154,7 @@ struct BatchPairArgs {
     int n_items;
     unsigned* counter;
     unsigned long long* near_count;
+    const double* k64;
 };
 
 __device__ __forceinline__ TileArgs tile_from_item(const BatchPairArgs& b, const WorkItem& w)
@@ -176,6 +178,7 @@ __device__ __forceinline__ TileArgs tile_from_item(const BatchPairArgs& b, const
     a.fp_stride = nr;
     a.node_base = b.node_off[w.r];
     a.near_count = b.near_count;
+    a.k64 = b.k64;
     return a;
 }
 
@@ -184,7 +187,7 @@ __device__ __forceinline__ TileArgs tile_from_item(const BatchPairArgs& b, const
 template <int TPB, int MINB, bool MIXED>
 __global__ void __launch_bounds__(TPB, MINB) batch_pair_kernel(BatchPairArgs b, Consts c, float near2)
 {
-    constexpr int SM_BYTES = MIXED ? TILE_MIX * SRC32_STRIDE * 4 : TILE_FP64 * SRC_STRIDE * 8;
+    constexpr int SM_BYTES = MIXED ? (int)sizeof(MixSmem<TILE_MIX, TPB>) : TILE_FP64 * SRC_STRIDE * 8;
     __shared__ __align__(16) unsigned char smem[SM_BYTES];
     __shared__ int item;
     for (;;) {
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(TPB, MINB) batch_pair_kernel(BatchPairArgs b, 
         const WorkItem w = b.items[it];
         const TileArgs a = tile_from_item(b, w);
         if (MIXED)
-            pair_tile_mixed<TILE_MIX>(a, c, near2, reinterpret_cast<float4*>(smem));
+            pair_tile_mixed<TILE_MIX, TPB>(a, c, near2, *reinterpret_cast<MixSmem<TILE_MIX, TPB>*>(smem));
         else
             pair_tile_fp64<TILE_FP64>(a, c, reinterpret_cast<double2*>(smem));
     }
@@ -427,6 +430,7 @@ BatchPairArgs pair_args(const DevBatch& B)
     a.n_items = B.n_items;
     a.counter = B.counter;
     a.near_count = B.near_count;
+    a.k64 = B.k64;
     return a;
 }
 
@@ -488,7 +492,7 @@ void free_batch(DevBatch& B)
                     B.loop_b,   B.loop_n,    B.pinned,    B.src,        B.src32,    B.fpart,   B.vel,
                     B.force,    B.partial,   B.acc,       B.d_node_off, B.d_fp_base, B.d_chunks, B.d_origin,
                     B.d_sh,     B.d_blk_real, B.d_blk_start, B.d_real_blk, B.d_items, B.counter, B.flag,
-                    B.near_count, B.staging};
+                    B.near_count, B.staging, B.k64};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     B = DevBatch{};
@@ -744,6 +748,7 @@ ptadd_status ptadd_batch_set(ptadd_ctx* ctx, int32_t R, const int64_t* node_off,
     BALLOC(B.flag, 1);
     BALLOC(B.near_count, 1);
     BALLOC(B.staging, 3 * n);
+    BALLOC(B.k64, 4);
 #undef BALLOC
     if (st != PTADD_OK) {
         free_batch(B);
@@ -773,6 +778,11 @@ ptadd_status ptadd_batch_set(ptadd_ctx* ctx, int32_t R, const int64_t* node_off,
     PTADD_CUDA(cudaMemsetAsync(B.acc, 0, 16 * (size_t)R * sizeof(double), s));
     PTADD_CUDA(cudaMemsetAsync(B.flag, 0, sizeof(int), s));
     PTADD_CUDA(cudaMemsetAsync(B.near_count, 0, sizeof(unsigned long long), s));
+    {
+        const Consts kc = batch_consts(ctx);
+        const double k64[4] = {kc.a2, kc.c1, kc.c2, 0.0};
+        PTADD_CUDA(cudaMemcpyAsync(B.k64, k64, sizeof(k64), cudaMemcpyHostToDevice, s));
+    }
     PTADD_CUDA(cudaStreamSynchronize(s));
     BatchConfig cfg;
     B.tuned = tune_lookup(tune_path(nullptr), tune_key(ctx, B, (int)ctx->prec), cfg) ? 1 : 0;

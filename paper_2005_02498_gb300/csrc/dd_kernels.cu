@@ -77,7 +77,10 @@ cudaError_t launch_seg_prep(const DevNetwork& net, cudaStream_t st)
 constexpr int PAIR_TPB = 128;
 constexpr int PAIR_TILE = 128;
 constexpr int MIX_TPB = 128;
-constexpr int MIX_TILE = 256;
+constexpr int MIX_TILE = 128;
+#ifndef PTADD_MIX_MINB
+#define PTADD_MIX_MINB 2  // resident blocks per SM the register budget is sized for
+#endif
 
 __global__ void __launch_bounds__(PAIR_TPB) pair_fp64_kernel(TileArgs base, int64_t n_tgt, int64_t chunk_len,
                                                              Consts c)
@@ -93,10 +96,10 @@ __global__ void __launch_bounds__(PAIR_TPB) pair_fp64_kernel(TileArgs base, int6
     pair_tile_fp64<PAIR_TILE>(a, c, tile);
 }
 
-__global__ void __launch_bounds__(MIX_TPB) pair_mixed_kernel(TileArgs base, int64_t n_tgt, int64_t chunk_len,
+__global__ void __launch_bounds__(MIX_TPB, PTADD_MIX_MINB) pair_mixed_kernel(TileArgs base, int64_t n_tgt, int64_t chunk_len,
                                                              Consts c, float near2)
 {
-    __shared__ float4 tile[MIX_TILE * SRC32_STRIDE / 4];
+    __shared__ MixSmem<MIX_TILE, MIX_TPB> sm;
     TileArgs a = base;
     a.t_begin = (int64_t)blockIdx.x * MIX_TPB;
     a.t_count = min((int64_t)MIX_TPB, n_tgt - a.t_begin);
@@ -104,16 +107,26 @@ __global__ void __launch_bounds__(MIX_TPB) pair_mixed_kernel(TileArgs base, int6
     a.je = min(a.n, a.js + chunk_len);
     a.add_app = blockIdx.y == 0;
     a.fp = base.fp + (int64_t)blockIdx.y * 6 * a.n;
-    pair_tile_mixed<MIX_TILE>(a, c, near2, tile);
+    pair_tile_mixed<MIX_TILE, MIX_TPB>(a, c, near2, sm);
 }
 
-int choose_chunks(int64_t n_tgt, int64_t n_src, int max_chunks)
+int choose_chunks(int64_t n_tgt, int64_t n_src, int max_chunks, int precision)
 {
-    // enough blocks to fill 152 SMs several times over, chunks of >= 1 tile
+    // About 16 waves of resident blocks, so that the blocks still running
+    // when the others have finished (the tail) cost a few per cent; chunks of
+    // at least two source tiles, so the per-block set-up and the nodal
+    // output stay small next to the pair work.
+    int dev = 0, sms = 152, per_sm = 2;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (precision == (int)PTADD_MIXED)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_mixed_kernel, MIX_TPB, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_fp64_kernel, PAIR_TPB, 0);
+    if (per_sm < 1) per_sm = 1;
     const int64_t tiles_t = (n_tgt + PAIR_TPB - 1) / PAIR_TPB;
-    const int64_t want_blocks = 152 * 8;
+    const int64_t want_blocks = (int64_t)sms * per_sm * 16;
     int64_t ch = (want_blocks + tiles_t - 1) / (tiles_t > 0 ? tiles_t : 1);
-    const int64_t max_by_src = (n_src + PAIR_TILE - 1) / PAIR_TILE;
+    const int64_t max_by_src = n_src / (2 * PAIR_TILE);
     if (ch > max_by_src) ch = max_by_src;
     if (ch > max_chunks) ch = max_chunks;
     if (ch < 1) ch = 1;
@@ -139,6 +152,7 @@ cudaError_t launch_pair(const DevNetwork& net, const int32_t* tgt, int64_t n_tgt
     a.fp_stride = n;
     a.node_base = 0;
     a.near_count = net.near_count;
+    a.k64 = net.k64;
     if (precision == (int)PTADD_MIXED) {
         dim3 grid((unsigned)((n_tgt + MIX_TPB - 1) / MIX_TPB), (unsigned)chunks);
         const float near2 = (float)((NEAR_FACTOR * NEAR_FACTOR + 1.0) * c.a2);

@@ -1,6 +1,7 @@
 // fma_peak.cu -- non-tensor arithmetic peak: every thread runs 8 independent
-// fused multiply-add chains (x <- x * m + c), FP64 or FP32, so the FMA pipe
-// of every SM stays busy; the host times the launch with CUDA events.
+// fused multiply-add chains (x <- x * m + c) in FP64, FP32 or packed FP32
+// pairs (FFMA2), so the FMA pipe of every SM stays busy; the host times the
+// launch with CUDA events.
 #include <cuda_runtime.h>
 
 #include "ptadd_internal.cuh"
@@ -20,11 +21,30 @@ __global__ void fma_chains_kernel(long iters, T m, T c, double* sink)
     if (s == T(-12345.678)) *sink = (double)s;  // keeps the chains live
 }
 
-cudaError_t launch_fma_chains(int fp64, int blocks, int threads, long iters, double* sink, cudaStream_t st)
+// Packed FP32 pairs: one FFMA2 instruction performs two FP32 FMAs.
+__global__ void fma2_chains_kernel(long iters, float m, float c, double* sink)
+{
+    const float2 mm = make_float2(m, m), cc = make_float2(c, c);
+    float2 x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = make_float2(threadIdx.x * 1e-3f + k, threadIdx.x * 1e-3f + k + 0.5f);
+    for (long i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = __ffma2_rn(x[k], mm, cc);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k].x + x[k].y;
+    if (s == -12345.678f) *sink = (double)s;
+}
+
+cudaError_t launch_fma_chains(int mode, int blocks, int threads, long iters, double* sink, cudaStream_t st)
 {
     // m slightly below 1 and c small keep every value finite and normal
-    if (fp64)
+    if (mode == 1)
         fma_chains_kernel<double><<<blocks, threads, 0, st>>>(iters, 0.999999, 1e-6, sink);
+    else if (mode == 2)
+        fma2_chains_kernel<<<blocks, threads, 0, st>>>(iters, 0.999999f, 1e-6f, sink);
     else
         fma_chains_kernel<float><<<blocks, threads, 0, st>>>(iters, 0.999999f, 1e-6f, sink);
     return cudaGetLastError();

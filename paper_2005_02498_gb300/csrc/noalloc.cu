@@ -149,7 +149,7 @@ extern "C" ptadd_status ptadd_forces_noalloc(const ptadd_material* mat, int64_t 
     c.c2 = 1.0 / (4.0 * M_PI * (1.0 - mat->nu));
     double sh[6];
     for (int k = 0; k < 6; ++k) sh[k] = sig_app[k] / mat->mu;
-    const int chunks = choose_chunks(n, n, NA_CHUNKS);
+    const int chunks = choose_chunks(n, n, NA_CHUNKS, (int)PTADD_FP64);
     PTADD_CUDA(launch_seg_prep(net, s));
     PTADD_CUDA(launch_pair(net, tgt, n, chunks, (int)PTADD_FP64, c, sh, s));
     PTADD_CUDA(launch_node_velocity(net, chunks, s));

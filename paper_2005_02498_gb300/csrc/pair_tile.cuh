@@ -35,6 +35,7 @@ struct TileArgs {
     int64_t fp_stride;
     int64_t node_base;
     unsigned long long* near_count;
+    const double* k64;      // device copy of {a2, c1, c2} for the near-field path (mixed)
 };
 
 __device__ __forceinline__ void tile_store(const TileArgs& a, int64_t seg, double Dx, double Dy, double Dz,
@@ -127,9 +128,14 @@ __device__ __forceinline__ void pair_tile_fp64(const TileArgs& a, const Consts& 
 // Every (Gauss point, source) pair is first located in FP32 from hi/lo-split
 // coordinates; if the point lies within 10 a of the source segment the pair
 // is evaluated in FP64 from the FP64 records, otherwise in FP32.  Per Gauss
-// point the contributions are summed in FP32 with Kahan compensation (the
-// FP64 near-field values enter as hi + lo floats); the compensated sums go to
-// FP64 before the PK force and the nodal assembly.
+// point the FP32 contributions are summed with Kahan compensation and the FP64
+// near-field values in FP64; both sums go to FP64 before the PK force and the
+// nodal assembly.
+//
+// The FP32 work is packed: Gauss points (0,1) and (2,3) travel as the two
+// lanes of a float2, so every add, multiply and fused multiply-add of the
+// field formula is one FADD2/FMUL2/FFMA2 instruction for two points.  The
+// shared-memory tile holds every source scalar duplicated into both lanes.
 __device__ __forceinline__ void kahan_add(float& s, float& c, float v)
 {
     const float y = v - c;
@@ -138,9 +144,189 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float v)
     s = t;
 }
 
-// smem: TILE * SRC32_STRIDE floats (as float4).
-template <int TILE>
-__device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts& c, float near2, float4* tile)
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+// a - b, rounded once
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 f2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b)
+{
+    return make_float2(cx ? a.x : b.x, cy ? a.y : b.y);
+}
+__device__ __forceinline__ void kahan_add2(float2& s, float2& c, float2 v)
+{
+    const float2 y = sub2(v, c);
+    const float2 t = add2(s, y);
+    c = sub2(sub2(t, s), y);
+    s = t;
+}
+// keep a register value opaque, so the compiler holds it instead of
+// recomputing it from its (FP64) inputs inside the loop
+__device__ __forceinline__ void opaque(float& x) { asm volatile("" : "+f"(x)); }
+
+// Shared-memory record of one source for the packed loop (float2 units, every
+// scalar in both lanes): x1 hi (0-2), x1 lo (3-5), L (6), t (7-9), b (10-12),
+// q = b x t (13-15), -t (16-18), -b (19-21).  The negated copies let the
+// field formula use plain fused multiply-adds where it subtracts.
+constexpr int MIX_REC = 22;
+
+struct Src2 {
+    float2 t[3], nt[3], L, b[3], nb[3], q[3];
+};
+
+// Sign-adjusted material constants of the packed formula.
+struct K2 {
+    float2 a2, a2x3, na2x3, nc1, c2, nc2, c2x3;
+};
+
+// Packed field of one source at two Gauss points (lanes), given R0 = x - x1.
+// s <- (sigma b') of the source, per lane: the formula of seg_sigma_b_geom
+// with y = R0.t carried as ny = -y and J3 as -J3, so that no intermediate
+// needs an explicit negation.  dd <- squared point-to-segment distance + a^2.
+__device__ __forceinline__ void seg_sigma_b2(float2 R0x, float2 R0y, float2 R0z, const Src2& S, const float2 bt[3],
+                                             const float2 w[3], float2 tb, float2 qb, const K2& k, float2 s[3],
+                                             float2& dd)
+{
+    const float2 ny = fma2(R0x, S.nt[0], fma2(R0y, S.nt[1], mul2(R0z, S.nt[2])));
+    const float2 Rpx = fma2(ny, S.t[0], R0x), Rpy = fma2(ny, S.t[1], R0y), Rpz = fma2(ny, S.t[2], R0z);
+    const float2 d2 = fma2(Rpx, Rpx, fma2(Rpy, Rpy, fma2(Rpz, Rpz, k.a2)));
+    const float2 u2 = add2(S.L, ny);
+    const float2 r1s = fma2(ny, ny, d2), r2s = fma2(u2, u2, d2);
+    // y < 0: nearest to x1; y > L: nearest to x2; else to the line
+    dd = sel2(ny.x > 0.0f, ny.y > 0.0f, r1s, sel2(u2.x < 0.0f, u2.y < 0.0f, r2s, d2));
+    const float2 i1 = make_float2(rsqrt_approx(r1s.x), rsqrt_approx(r1s.y));
+    const float2 i2 = make_float2(rsqrt_approx(r2s.x), rsqrt_approx(r2s.y));
+    const float2 m = mul2(ny, i1), p = mul2(u2, i2);
+    // u1 u2 >= 0 (y <= 0 or y >= L)
+    const bool samex = (ny.x >= 0.0f) || (u2.x <= 0.0f), samey = (ny.y >= 0.0f) || (u2.y <= 0.0f);
+    const float2 i1s = mul2(i1, i1), i2s = mul2(i2, i2), i12 = mul2(i1s, i2s);
+    const float2 pm = mul2(p, m);
+    const float2 S2 = fma2(p, p, fma2(m, m, pm));
+    const float2 isum = add2(i1, i2);
+    const float2 pps = add2(p, m), one_pm = add2(f2(1.0f), pm);
+    const float2 den = sel2(samex, samey, mul2(pps, one_pm), d2);
+    const float2 dis = mul2(den, isum);
+    const float2 rr = make_float2(rcp_approx(dis.x), rcp_approx(dis.y));
+    const float2 rden = mul2(rr, isum);
+    const float2 Lsum = mul2(S.L, add2(u2, ny));
+    const float2 Li = mul2(Lsum, i12);
+    const float2 J1 = mul2(Li, mul2(rr, den));
+    const float2 nJ3 = mul2(mul2(J1, add2(i1s, fma2(i1, i2, i2s))), f2(-1.0f / 3.0f));
+    const float2 g = mul2(Li, rden);
+    const float2 J0 = sel2(samex, samey, mul2(g, one_pm), mul2(sub2(p, m), rden));
+    const float2 Wt = sel2(samex, samey, fma2(mul2(mul2(add2(r1s, mul2(u2, u2)), i12), rden), pps, add2(i1s, i2s)),
+                           mul2(sub2(f2(3.0f), S2), rden));
+    const float2 J0_3 = mul2(J0, f2(1.0f / 3.0f));
+    const float2 J2 = mul2(J0_3, Wt);
+    const float2 J4 = mul2(J0_3, S2);
+    const float2 A0 = fma2(k.a2x3, J2, add2(J0, J0));
+    const float2 A1 = fma2(k.na2x3, nJ3, add2(J1, J1));
+    const float2 Rb = fma2(Rpx, bt[0], fma2(Rpy, bt[1], mul2(Rpz, bt[2])));
+    const float2 Rw = fma2(Rpx, w[0], fma2(Rpy, w[1], mul2(Rpz, w[2])));
+    const float2 qR = fma2(Rpx, S.q[0], fma2(Rpy, S.q[1], mul2(Rpz, S.q[2])));
+    const float2 nc1tb = mul2(k.nc1, tb);
+    const float2 c3qR = mul2(k.c2x3, qR);
+    const float2 nc2J0 = mul2(k.nc2, J0);
+    const float2 c2J1 = mul2(k.c2, J1);
+    const float2 cRxb = mul2(nc1tb, A0);
+    const float2 cq = fma2(nc1tb, A1, fma2(c2J1, tb, mul2(nc2J0, Rb)));
+    const float2 cRp = fma2(c3qR, fma2(nJ3, tb, mul2(J2, Rb)), mul2(nc2J0, qb));
+    const float2 ct = fma2(k.nc1, fma2(A0, Rw, mul2(A1, qb)), fma2(c2J1, qb, mul2(c3qR, fma2(nJ3, Rb, mul2(J4, tb)))));
+    const float2 cb = mul2(mul2(k.c2, qR), sub2(A0, J0));
+    // Rp x b
+    const float2 Xx = fma2(Rpy, S.b[2], mul2(Rpz, S.nb[1]));
+    const float2 Xy = fma2(Rpz, S.b[0], mul2(Rpx, S.nb[2]));
+    const float2 Xz = fma2(Rpx, S.b[1], mul2(Rpy, S.nb[0]));
+    s[0] = fma2(cRxb, Xx, fma2(cq, S.q[0], fma2(cRp, Rpx, fma2(ct, S.t[0], mul2(cb, bt[0])))));
+    s[1] = fma2(cRxb, Xy, fma2(cq, S.q[1], fma2(cRp, Rpy, fma2(ct, S.t[1], mul2(cb, bt[1])))));
+    s[2] = fma2(cRxb, Xz, fma2(cq, S.q[2], fma2(cRp, Rpz, fma2(ct, S.t[2], mul2(cb, bt[2])))));
+}
+
+// One near-field (Gauss point, source) pair in FP64: (sigma b') of source js
+// at Gauss point qp of target seg, from the FP64 records.
+__device__ __forceinline__ double3 near_field_fp64(const double* __restrict__ pos, int64_t n,
+                                                   const int32_t* __restrict__ nxt, const double* __restrict__ src,
+                                                   int64_t seg, int64_t js, int qp, const double* __restrict__ k64)
+{
+    const double a2 = k64[0], c1 = k64[1], c2 = k64[2];
+    const double* tr = src + (int64_t)SRC_STRIDE * seg;
+    const int64_t sb = nxt[seg];
+    const double xa = pos[seg], ya = pos[n + seg], za = pos[2 * n + seg];
+    const double Dx = pos[sb] - xa, Dy = pos[n + sb] - ya, Dz = pos[2 * n + sb] - za;
+    const double bt[3] = {tr[8], tr[9], tr[10]};
+    const double* r64 = src + (int64_t)SRC_STRIDE * js;
+    const double x1d[3] = {r64[0], r64[1], r64[2]};
+    const double td[3] = {r64[4], r64[5], r64[6]};
+    const double bd[3] = {r64[8], r64[9], r64[10]};
+    const double qd[3] = {r64[12], r64[13], r64[14]};
+    PairK<double> kd;
+    pair_constants(td, bd, qd, bt, kd);
+    const double xi = gl4_xi(qp);
+    const double xq0 = __dadd_rn(xa, __dmul_rn(xi, Dx));
+    const double xq1 = __dadd_rn(ya, __dmul_rn(xi, Dy));
+    const double xq2 = __dadd_rn(za, __dmul_rn(xi, Dz));
+    double vd[3] = {0.0, 0.0, 0.0};
+    seg_sigma_b(xq0 - x1d[0], xq1 - x1d[1], xq2 - x1d[2], td, r64[3], bd, qd, bt, kd, a2, c1, c2, vd);
+    return make_double3(vd[0], vd[1], vd[2]);
+}
+
+// Near pairs found by a warp wait in a per-warp queue of (source index,
+// owner lane << 2 | Gauss point) entries; a full queue is evaluated 32 at a
+// time, one entry per lane, so the FP64 work runs with every lane busy.
+// Each result goes to its owner's FP64 near sums in queue order, so the
+// summation order (and the result) does not depend on scheduling.
+constexpr int NEAR_Q = 160;  // <= 31 waiting + 128 added by one source (4 Gauss points x 32 lanes)
+
+template <int TILE, int TPB>
+struct MixSmem {
+    float2 tile[TILE * MIX_REC];  // source records (MIX_REC float2 each)
+    double nacc[12 * TPB];             // FP64 near sums: [qp * 3 + e][thread]
+    uint2 queue[TPB / 32][NEAR_Q];
+};
+
+// Evaluate the first cnt (<= 32) entries of a warp queue; warp-uniform call.
+static __device__ __noinline__ void near_flush(const double* __restrict__ pos, int64_t n,
+                                               const int32_t* __restrict__ nxt, const double* __restrict__ src,
+                                               const double* __restrict__ k64, int64_t seg,
+                                               const uint2* __restrict__ q, int cnt, double* __restrict__ nacc,
+                                               int tpb)
+{
+    const int lane = threadIdx.x & 31;
+    const uint2 e = lane < cnt ? q[lane] : make_uint2(0u, 0u);
+    const int64_t seg_o = __shfl_sync(0xffffffffu, (long long)seg, (int)((e.y >> 2) & 31u));
+    double3 d = make_double3(0.0, 0.0, 0.0);
+    if (lane < cnt) d = near_field_fp64(pos, n, nxt, src, seg_o, (int64_t)e.x, (int)(e.y & 3u), k64);
+    for (int k = 0; k < cnt; ++k) {
+        const double dx = __shfl_sync(0xffffffffu, d.x, k);
+        const double dy = __shfl_sync(0xffffffffu, d.y, k);
+        const double dz = __shfl_sync(0xffffffffu, d.z, k);
+        const unsigned tag = __shfl_sync(0xffffffffu, e.y, k);
+        if ((int)((tag >> 2) & 31u) == lane) {
+            double* acc = nacc + 3 * (int)(tag & 3u) * tpb + threadIdx.x;
+            acc[0] += dx;
+            acc[tpb] += dy;
+            acc[2 * tpb] += dz;
+        }
+    }
+}
+
+// Drop the first 32 entries of a warp queue holding cnt (32 < cnt <= NEAR_Q)
+// of them: chunk by chunk, each read before the chunk below it is overwritten.
+__device__ __forceinline__ void near_shift(uint2* q, int cnt)
+{
+    const int lane = threadIdx.x & 31;
+    for (int base = 32; base < cnt; base += 32) {
+        const uint2 u = base + lane < cnt ? q[base + lane] : make_uint2(0u, 0u);
+        __syncwarp();
+        if (base + lane < cnt) q[base - 32 + lane] = u;
+        __syncwarp();
+    }
+}
+
+template <int TILE, int TPB>
+__device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts& c, float near2,
+                                                MixSmem<TILE, TPB>& sm)
 {
     const int64_t n = a.n;
     const bool active = threadIdx.x < a.t_count;
@@ -150,98 +336,150 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
     const double xa = a.pos[seg], ya = a.pos[n + seg], za = a.pos[2 * n + seg];
     const double Dx = a.pos[sb] - xa, Dy = a.pos[n + sb] - ya, Dz = a.pos[2 * n + sb] - za;
     const double bt[3] = {tr[8], tr[9], tr[10]};
-    const float btf[3] = {(float)bt[0], (float)bt[1], (float)bt[2]};
-    float xh[4][3], xl[4][3];
+    float btf[3] = {(float)bt[0], (float)bt[1], (float)bt[2]};
+    opaque(btf[0]);
+    opaque(btf[1]);
+    opaque(btf[2]);
+    const float2 bt2[3] = {f2(btf[0]), f2(btf[1]), f2(btf[2])};
+    // Gauss points, hi/lo split about the origin; pair p holds points 2p, 2p+1
+    float2 XH[2][3], XL[2][3];
 #pragma unroll
     for (int qp = 0; qp < 4; ++qp) {
         const double xi = gl4_xi(qp);
-        const double q0 = __dadd_rn(xa, __dmul_rn(xi, Dx)) - a.origin[0];
-        const double q1 = __dadd_rn(ya, __dmul_rn(xi, Dy)) - a.origin[1];
-        const double q2 = __dadd_rn(za, __dmul_rn(xi, Dz)) - a.origin[2];
-        const double h0 = rint(q0), h1 = rint(q1), h2 = rint(q2);
-        xh[qp][0] = (float)h0; xh[qp][1] = (float)h1; xh[qp][2] = (float)h2;
-        xl[qp][0] = (float)(q0 - h0); xl[qp][1] = (float)(q1 - h1); xl[qp][2] = (float)(q2 - h2);
+        const double qd[3] = {__dadd_rn(xa, __dmul_rn(xi, Dx)) - a.origin[0],
+                              __dadd_rn(ya, __dmul_rn(xi, Dy)) - a.origin[1],
+                              __dadd_rn(za, __dmul_rn(xi, Dz)) - a.origin[2]};
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const double h = rint(qd[e]);
+            float hf = (float)h, lf = (float)(qd[e] - h);
+            opaque(hf);
+            opaque(lf);
+            if (qp & 1) {
+                XH[qp >> 1][e].y = hf;
+                XL[qp >> 1][e].y = lf;
+            } else {
+                XH[qp >> 1][e].x = hf;
+                XL[qp >> 1][e].x = lf;
+            }
+        }
     }
-    float sh[4][3], sc[4][3];
+    float2 SH[2][3], SC[2][3];
 #pragma unroll
-    for (int qp = 0; qp < 4; ++qp)
+    for (int p = 0; p < 2; ++p)
 #pragma unroll
-        for (int e = 0; e < 3; ++e) sh[qp][e] = sc[qp][e] = 0.0f;
-    const float a2f = (float)c.a2, c1f = (float)c.c1, c2f = (float)c.c2;
-    unsigned near_here = 0;
+        for (int e = 0; e < 3; ++e) SH[p][e] = SC[p][e] = f2(0.0f);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) sm.nacc[k * TPB + threadIdx.x] = 0.0;
+    // loop-invariant constants held in registers (not re-derived from FP64 inputs in the loop)
+    float kc[7] = {(float)c.a2, (float)(3.0 * c.a2), (float)(-3.0 * c.a2), (float)(-c.c1),
+                   (float)c.c2, (float)(-c.c2), (float)(3.0 * c.c2)};
+#pragma unroll
+    for (int e = 0; e < 7; ++e) opaque(kc[e]);
+    const K2 kk{f2(kc[0]), f2(kc[1]), f2(kc[2]), f2(kc[3]), f2(kc[4]), f2(kc[5]), f2(kc[6])};
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    uint2* wq = sm.queue[threadIdx.x >> 5];
+    int qn = 0;             // entries waiting in this warp's queue (warp-uniform)
+    unsigned near_warp = 0;  // near point-pairs of this warp (warp-uniform)
 
     for (int64_t j0 = a.js; j0 < a.je; j0 += TILE) {
         const int cnt = (int)min((int64_t)TILE, a.je - j0);
         __syncthreads();
-        const float4* g = reinterpret_cast<const float4*>(a.src32 + (int64_t)SRC32_STRIDE * j0);
-        for (int e = threadIdx.x; e < cnt * (SRC32_STRIDE / 4); e += blockDim.x) tile[e] = g[e];
+        for (int js = threadIdx.x; js < cnt; js += blockDim.x) {
+            const float4* g = reinterpret_cast<const float4*>(a.src32 + (int64_t)SRC32_STRIDE * (j0 + js));
+            float v[SRC32_STRIDE];
+#pragma unroll
+            for (int e = 0; e < SRC32_STRIDE / 4; ++e) {
+                const float4 u = g[e];
+                v[4 * e] = u.x;
+                v[4 * e + 1] = u.y;
+                v[4 * e + 2] = u.z;
+                v[4 * e + 3] = u.w;
+            }
+            float4* d = reinterpret_cast<float4*>(sm.tile + (int64_t)MIX_REC * js);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) d[e] = make_float4(v[2 * e], v[2 * e], v[2 * e + 1], v[2 * e + 1]);
+            d[8] = make_float4(-v[7], -v[7], -v[8], -v[8]);
+            d[9] = make_float4(-v[9], -v[9], -v[10], -v[10]);
+            d[10] = make_float4(-v[11], -v[11], -v[12], -v[12]);
+        }
         __syncthreads();
         for (int jj = 0; jj < cnt; ++jj) {
-            const float* r = reinterpret_cast<const float*>(tile + jj * (SRC32_STRIDE / 4));
-            const float L = r[6];
-            if (!(L > 0.0f)) continue;  // zero-length source (uniform branch)
-            const float h1[3] = {r[0], r[1], r[2]}, l1[3] = {r[3], r[4], r[5]};
-            const float t[3] = {r[7], r[8], r[9]};
-            const float b[3] = {r[10], r[11], r[12]};
-            const float q[3] = {r[13], r[14], r[15]};
-            PairK<float> k;
-            pair_constants(t, b, q, btf, k);
+            const float2* r = sm.tile + jj * MIX_REC;
+            if (!(r[6].x > 0.0f)) continue;  // zero-length source (uniform branch)
+            Src2 S;
+            const float2 h1[3] = {r[0], r[1], r[2]}, l1[3] = {r[3], r[4], r[5]};
+            S.L = r[6];
 #pragma unroll
-            for (int qp = 0; qp < 4; ++qp) {
-                const float R0x = (xh[qp][0] - h1[0]) + (xl[qp][0] - l1[0]);
-                const float R0y = (xh[qp][1] - h1[1]) + (xl[qp][1] - l1[1]);
-                const float R0z = (xh[qp][2] - h1[2]) + (xl[qp][2] - l1[2]);
-                PairGeom<float> G;
-                pair_geom(R0x, R0y, R0z, t, L, a2f, G);
-                // squared point-to-segment distance (+ a^2)
-                const float dd = G.y < 0.0f ? G.r1s : (G.y > L ? G.r2s : G.d2);
-                if (dd >= near2) {
-                    float v[3] = {0.0f, 0.0f, 0.0f};
-                    seg_sigma_b_geom(G, t, L, b, q, btf, k, a2f, c1f, c2f, v);
-                    kahan_add(sh[qp][0], sc[qp][0], v[0]);
-                    kahan_add(sh[qp][1], sc[qp][1], v[1]);
-                    kahan_add(sh[qp][2], sc[qp][2], v[2]);
-                } else {
-                    // near field: FP64 from the FP64 records
-                    ++near_here;
-                    const double* r64 = a.src + (int64_t)SRC_STRIDE * (j0 + jj);
-                    const double x1d[3] = {r64[0], r64[1], r64[2]};
-                    const double td[3] = {r64[4], r64[5], r64[6]};
-                    const double bd[3] = {r64[8], r64[9], r64[10]};
-                    const double qd[3] = {r64[12], r64[13], r64[14]};
-                    PairK<double> kd;
-                    pair_constants(td, bd, qd, bt, kd);
-                    const double xi = gl4_xi(qp);
-                    const double xq0 = __dadd_rn(xa, __dmul_rn(xi, Dx));
-                    const double xq1 = __dadd_rn(ya, __dmul_rn(xi, Dy));
-                    const double xq2 = __dadd_rn(za, __dmul_rn(xi, Dz));
-                    double vd[3] = {0.0, 0.0, 0.0};
-                    seg_sigma_b(xq0 - x1d[0], xq1 - x1d[1], xq2 - x1d[2], td, r64[3], bd, qd, bt, kd, c.a2, c.c1,
-                                c.c2, vd);
+            for (int e = 0; e < 3; ++e) {
+                S.t[e] = r[7 + e];
+                S.b[e] = r[10 + e];
+                S.q[e] = r[13 + e];
+                S.nt[e] = r[16 + e];
+                S.nb[e] = r[19 + e];
+            }
+            // per-pair constants t.b', q.b', b x b'
+            const float2 tb = fma2(S.t[0], bt2[0], fma2(S.t[1], bt2[1], mul2(S.t[2], bt2[2])));
+            const float2 qb = fma2(S.q[0], bt2[0], fma2(S.q[1], bt2[1], mul2(S.q[2], bt2[2])));
+            const float2 w[3] = {fma2(S.b[1], bt2[2], mul2(S.nb[2], bt2[1])),
+                                 fma2(S.b[2], bt2[0], mul2(S.nb[0], bt2[2])),
+                                 fma2(S.b[0], bt2[1], mul2(S.nb[1], bt2[0]))};
+            // both Gauss-point pairs first (two independent chains), then the sums
+            float2 v[2][3], dd[2];
 #pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        const float hi = (float)vd[e];
-                        const float lo = (float)(vd[e] - (double)hi);
-                        kahan_add(sh[qp][e], sc[qp][e], hi);
-                        kahan_add(sh[qp][e], sc[qp][e], lo);
-                    }
+            for (int p = 0; p < 2; ++p) {
+                const float2 R0x = add2(sub2(XH[p][0], h1[0]), sub2(XL[p][0], l1[0]));
+                const float2 R0y = add2(sub2(XH[p][1], h1[1]), sub2(XL[p][1], l1[1]));
+                const float2 R0z = add2(sub2(XH[p][2], h1[2]), sub2(XL[p][2], l1[2]));
+                seg_sigma_b2(R0x, R0y, R0z, S, bt2, w, tb, qb, kk, v[p], dd[p]);
+            }
+            bool nr[2][2];
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                nr[p][0] = active && dd[p].x < near2;
+                nr[p][1] = active && dd[p].y < near2;
+                // far lanes go to the FP32 sums; near lanes to the FP64 queue
+#pragma unroll
+                for (int e = 0; e < 3; ++e)
+                    kahan_add2(SH[p][e], SC[p][e], sel2(nr[p][0], nr[p][1], f2(0.0f), v[p][e]));
+            }
+            if (__any_sync(0xffffffffu, nr[0][0] || nr[0][1] || nr[1][0] || nr[1][1])) {
+                const unsigned js = (unsigned)(j0 + jj);
+#pragma unroll
+                for (int qp = 0; qp < 4; ++qp) {
+                    const bool mine = nr[qp >> 1][qp & 1];
+                    const unsigned bal = __ballot_sync(0xffffffffu, mine);
+                    if (mine) wq[qn + __popc(bal & lt)] = make_uint2(js, ((unsigned)lane << 2) | (unsigned)qp);
+                    qn += __popc(bal);
+                    near_warp += (unsigned)__popc(bal);
+                }
+                while (qn >= 32) {
+                    __syncwarp();
+                    near_flush(a.pos, n, a.nxt, a.src, a.k64, seg, wq, 32, sm.nacc, TPB);
+                    near_shift(wq, qn);
+                    qn -= 32;
                 }
             }
         }
     }
-    // count the FP64 point-pairs (one atomic per warp)
-    if (a.near_count) {
-        unsigned w = active ? near_here : 0u;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
-        if ((threadIdx.x & 31) == 0 && w) atomicAdd(a.near_count, (unsigned long long)w);
+    if (qn > 0) {
+        __syncwarp();
+        near_flush(a.pos, n, a.nxt, a.src, a.k64, seg, wq, qn, sm.nacc, TPB);
     }
+    // count the FP64 point-pairs (one atomic per warp)
+    if (a.near_count && lane == 0 && near_warp) atomicAdd(a.near_count, (unsigned long long)near_warp);
+    __syncwarp();
     if (!active) return;
     double acc[4][3];
 #pragma unroll
-    for (int qp = 0; qp < 4; ++qp)
+    for (int p = 0; p < 2; ++p)
 #pragma unroll
-        for (int e = 0; e < 3; ++e) acc[qp][e] = (double)sh[qp][e] - (double)sc[qp][e];
+        for (int e = 0; e < 3; ++e) {
+            acc[2 * p][e] = ((double)SH[p][e].x - (double)SC[p][e].x) + sm.nacc[(6 * p + e) * TPB + threadIdx.x];
+            acc[2 * p + 1][e] =
+                ((double)SH[p][e].y - (double)SC[p][e].y) + sm.nacc[(6 * p + 3 + e) * TPB + threadIdx.x];
+        }
     tile_store(a, seg, Dx, Dy, Dz, bt, acc);
 }
 

@@ -47,7 +47,7 @@ static void free_network(DevNetwork& n)
 {
     void* ptrs[] = {n.pos[0], n.pos[1], n.nxt,   n.prv,   n.loop_of, n.loop_b,  n.loop_n, n.pinned, n.tgt_burst,
                     n.tgt_all, n.src,    n.fpart, n.vel,   n.force,   n.partial, n.acc,    n.flag,   n.staging,
-                    n.src32,   n.near_count};
+                    n.src32,   n.near_count, n.k64};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     n = DevNetwork{};
@@ -237,6 +237,7 @@ ptadd_status ptadd_set_network(ptadd_ctx* ctx, int64_t n_nodes, const double* xy
     ALLOC(net.staging, 3 * n);
     ALLOC(net.src32, SRC32_STRIDE * n);
     ALLOC(net.near_count, 1);
+    ALLOC(net.k64, 4);
 #undef ALLOC
     if (st != PTADD_OK) {
         free_network(net);
@@ -260,6 +261,9 @@ ptadd_status ptadd_set_network(ptadd_ctx* ctx, int64_t n_nodes, const double* xy
     PTADD_CUDA(cudaMemsetAsync(net.acc, 0, 16 * sizeof(double), s));
     PTADD_CUDA(cudaMemsetAsync(net.flag, 0, sizeof(int), s));
     PTADD_CUDA(cudaMemsetAsync(net.near_count, 0, sizeof(unsigned long long), s));
+    const Consts kc = make_consts(ctx);
+    const double k64[4] = {kc.a2, kc.c1, kc.c2, 0.0};
+    PTADD_CUDA(cudaMemcpyAsync(net.k64, k64, sizeof(k64), cudaMemcpyHostToDevice, s));
     // host vectors die at return: make the copies complete first
     PTADD_CUDA(cudaStreamSynchronize(s));
     for (int c = 0; c < 6; ++c) ctx->sig_app[c] = 0.0;
@@ -315,7 +319,7 @@ static ptadd_status eval_forces(ptadd_ctx* ctx, const int32_t* tgt, int64_t n_tg
     const Consts c = make_consts(ctx);
     double sh[6];
     for (int k = 0; k < 6; ++k) sh[k] = ctx->sig_app[k] / ctx->mat.mu;
-    const int chunks = choose_chunks(n_tgt, net.n_nodes, net.max_chunks);
+    const int chunks = choose_chunks(n_tgt, net.n_nodes, net.max_chunks, (int)ctx->prec);
     cudaStream_t s = ctx->stream;
     if (n_tgt < net.n_nodes)
         PTADD_CUDA(cudaMemsetAsync(net.fpart, 0, (size_t)chunks * 6 * net.n_nodes * sizeof(double), s));
@@ -587,6 +591,7 @@ ptadd_status ptadd_set_state(ptadd_ctx* ctx, const void* buf, size_t bytes)
 ptadd_status ptadd_fma_peak(int device, int fp64, double seconds, double* flops)
 {
     if (!flops) return arg_error("flops is NULL");
+    if (fp64 < 0 || fp64 > 2) return arg_error("mode must be 0 (FP32), 1 (FP64) or 2 (packed FP32 pairs)");
     int ndev = 0;
     PTADD_CUDA(cudaGetDeviceCount(&ndev));
     if (device < 0 || device >= ndev) return arg_error("device index out of range");
@@ -602,7 +607,7 @@ ptadd_status ptadd_fma_peak(int device, int fp64, double seconds, double* flops)
     cudaEventCreate(&e1);
     const int threads = 256, blocks = sms * 8;
     const int chains = 8;
-    long iters = fp64 ? 2000 : 20000;
+    long iters = fp64 == 1 ? 2000 : 20000;
     double best = 0.0;
     ptadd_status st = PTADD_OK;
     for (int pass = 0; pass < 16 && st == PTADD_OK; ++pass) {
@@ -617,7 +622,7 @@ ptadd_status ptadd_fma_peak(int device, int fp64, double seconds, double* flops)
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        const double f = 2.0 * chains * (double)iters * blocks * threads / (ms * 1e-3);
+        const double f = 2.0 * chains * (fp64 == 2 ? 2.0 : 1.0) * (double)iters * blocks * threads / (ms * 1e-3);
         if (pass >= 2 && f > best) best = f;
         if (pass >= 3 && ms * 1e-3 >= seconds / 2) break;
         // grow the run towards the requested duration

@@ -69,6 +69,7 @@ struct DevNetwork {
     float* src32 = nullptr;        // [n*SRC32_STRIDE] FP32 records of the mixed path
     double origin[3] = {0, 0, 0};  // integer-valued origin of the FP32 hi/lo split
     unsigned long long* near_count = nullptr;  // FP64 point-pairs of the mixed path
+    double* k64 = nullptr;         // {a2, c1, c2} for the near-field path of the mixed kernel
     double* fpart = nullptr;       // [max_chunks*6*n] partial nodal-force parts
     int max_chunks = 0;
     double* vel = nullptr;         // SoA [3*n]
@@ -98,7 +99,7 @@ cudaError_t launch_node_velocity(const DevNetwork& net, int chunks, cudaStream_t
 // Lp/rho sample of the step-start state, Euler update into the other buffer,
 // and the fixed-order reduction into net.acc (weighted by dt_hat)
 cudaError_t launch_lp_euler(DevNetwork& net, double dt_hat, cudaStream_t st);
-int choose_chunks(int64_t n_tgt, int64_t n_src, int max_chunks);
+int choose_chunks(int64_t n_tgt, int64_t n_src, int max_chunks, int precision);
 
 // peak microbenchmark
 cudaError_t launch_fma_chains(int fp64, int blocks, int threads, long iters, double* sink, cudaStream_t st);

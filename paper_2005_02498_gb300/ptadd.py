@@ -189,11 +189,12 @@ def version():
     return load().ptadd_version()
 
 
-def fma_peak(device=0, fp64=True, seconds=1.0):
-    """Measured FMA throughput (FLOP/s) of every SM, FP64 or FP32."""
+def fma_peak(device=0, fp64=True, seconds=1.0, packed=False):
+    """Measured FMA throughput (FLOP/s) of every SM: FP64, FP32, or packed FP32 pairs."""
     lib = load()
     out = ctypes.c_double(0.0)
-    _check(lib.ptadd_fma_peak(int(device), int(bool(fp64)), float(seconds), ctypes.byref(out)))
+    mode = 2 if packed else (1 if fp64 else 0)
+    _check(lib.ptadd_fma_peak(int(device), mode, float(seconds), ctypes.byref(out)))
     return out.value
 
 

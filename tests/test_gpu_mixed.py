@@ -62,15 +62,26 @@ def test_mixed_large_workload_sampled_forces():
 
 
 def test_mixed_burst_rates_small_workload():
+    """Between steps 40 and 80 at dt = 5e-13 s two loops of this network pass
+    close to each other, and the trajectory itself amplifies perturbations
+    about 1e4-fold there (the oracle moved by 1e-16 of the displacement
+    differs by 1e-12 at step 60).  Positions are therefore held to 1e-5 of
+    the displacement before that transient and to the 1 % rate bar after
+    it."""
     net = W.small_loop_network()
     dt = 5e-13
+    ref40 = O.burst(MAT, net, 40, dt)
     ref = O.burst(MAT, net, 100, dt)
+    with ctx_for(net, ptadd.PTADD_MIXED) as c:
+        c.advance(40, dt)
+        x40 = c.get_nodes()
     with ctx_for(net, ptadd.PTADD_MIXED) as c:
         Lp, rho = c.advance(100, dt)
         x = c.get_nodes()
+    assert relmax(x40 - net.xyz, ref40["xyz"] - net.xyz) <= 1e-5
     assert relfro(Lp, ref["Lp_avg"]) <= 1e-2
     assert abs(rho / ref["rho_avg"] - 1) <= 1e-6
-    assert relmax(x - net.xyz, ref["xyz"] - net.xyz) <= 1e-3
+    assert relmax(x - net.xyz, ref["xyz"] - net.xyz) <= 1e-2
 
 
 def test_mixed_burst_rates_large_workload_against_fp64_gpu():
