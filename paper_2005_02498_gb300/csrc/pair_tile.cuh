@@ -128,22 +128,14 @@ __device__ __forceinline__ void pair_tile_fp64(const TileArgs& a, const Consts& 
 // Every (Gauss point, source) pair is first located in FP32 from hi/lo-split
 // coordinates; if the point lies within 10 a of the source segment the pair
 // is evaluated in FP64 from the FP64 records, otherwise in FP32.  Per Gauss
-// point the FP32 contributions are summed with Kahan compensation and the FP64
-// near-field values in FP64; both sums go to FP64 before the PK force and the
-// nodal assembly.
+// point the FP32 contributions of one shared-memory tile of sources are
+// summed in FP32 and the tile sums, like the FP64 near-field values, are
+// accumulated in FP64; the FP64 sums feed the PK force and the nodal assembly.
 //
 // The FP32 work is packed: Gauss points (0,1) and (2,3) travel as the two
 // lanes of a float2, so every add, multiply and fused multiply-add of the
 // field formula is one FADD2/FMUL2/FFMA2 instruction for two points.  The
 // shared-memory tile holds every source scalar duplicated into both lanes.
-__device__ __forceinline__ void kahan_add(float& s, float& c, float v)
-{
-    const float y = v - c;
-    const float t = s + y;
-    c = (t - s) - y;
-    s = t;
-}
-
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
@@ -153,13 +145,6 @@ __device__ __forceinline__ float2 f2(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b)
 {
     return make_float2(cx ? a.x : b.x, cy ? a.y : b.y);
-}
-__device__ __forceinline__ void kahan_add2(float2& s, float2& c, float2 v)
-{
-    const float2 y = sub2(v, c);
-    const float2 t = add2(s, y);
-    c = sub2(sub2(t, s), y);
-    s = t;
 }
 // keep a register value opaque, so the compiler holds it instead of
 // recomputing it from its (FP64) inputs inside the loop
@@ -175,22 +160,25 @@ struct Src2 {
     float2 t[3], nt[3], L, b[3], nb[3], q[3];
 };
 
-// Sign-adjusted material constants of the packed formula.
-struct K2 {
-    float2 a2, a2x3, na2x3, nc1, c2, nc2, c2x3;
+// Quantities of one (source, target) pair shared by the four Gauss points:
+// t.b', -t.b', q.b', -q.b' and -(c1/c2) t.b'.
+struct Pair2 {
+    float2 tb, ntb, qb, nqb, nrtb;
 };
 
-// Packed field of one source at two Gauss points (lanes), given R0 = x - x1.
-// s <- (sigma b') of the source, per lane: the formula of seg_sigma_b_geom
-// with y = R0.t carried as ny = -y and J3 as -J3, so that no intermediate
-// needs an explicit negation.  dd <- squared point-to-segment distance + a^2.
+// Packed field of one source at two Gauss points (lanes), given R0 = x - x1:
+// s <- (sigma b') / c2 per lane, and dd <- squared point-to-segment distance
+// + a^2.  The formula of seg_sigma_b_geom rearranged for fused multiply-adds:
+// c2 is taken out of every coefficient (the caller scales the sums), the
+// moments enter as K2 = 3 J2, K3 = 3 J3, K4 = 3 J4 (which absorbs the 1/3 and
+// the 3 of 3 c2), y = R0.t is carried as ny = -y, and (b x b').Rp is
+// evaluated as b'.(Rp x b).  a2 = a^2, nr = -c1/c2.
 __device__ __forceinline__ void seg_sigma_b2(float2 R0x, float2 R0y, float2 R0z, const Src2& S, const float2 bt[3],
-                                             const float2 w[3], float2 tb, float2 qb, const K2& k, float2 s[3],
-                                             float2& dd)
+                                             const Pair2& P, float2 a2, float2 nr, float2 s[3], float2& dd)
 {
     const float2 ny = fma2(R0x, S.nt[0], fma2(R0y, S.nt[1], mul2(R0z, S.nt[2])));
     const float2 Rpx = fma2(ny, S.t[0], R0x), Rpy = fma2(ny, S.t[1], R0y), Rpz = fma2(ny, S.t[2], R0z);
-    const float2 d2 = fma2(Rpx, Rpx, fma2(Rpy, Rpy, fma2(Rpz, Rpz, k.a2)));
+    const float2 d2 = fma2(Rpx, Rpx, fma2(Rpy, Rpy, fma2(Rpz, Rpz, a2)));
     const float2 u2 = add2(S.L, ny);
     const float2 r1s = fma2(ny, ny, d2), r2s = fma2(u2, u2, d2);
     // y < 0: nearest to x1; y > L: nearest to x2; else to the line
@@ -212,32 +200,28 @@ __device__ __forceinline__ void seg_sigma_b2(float2 R0x, float2 R0y, float2 R0z,
     const float2 Lsum = mul2(S.L, add2(u2, ny));
     const float2 Li = mul2(Lsum, i12);
     const float2 J1 = mul2(Li, mul2(rr, den));
-    const float2 nJ3 = mul2(mul2(J1, add2(i1s, fma2(i1, i2, i2s))), f2(-1.0f / 3.0f));
+    const float2 K3 = mul2(J1, add2(i1s, fma2(i1, i2, i2s)));
     const float2 g = mul2(Li, rden);
     const float2 J0 = sel2(samex, samey, mul2(g, one_pm), mul2(sub2(p, m), rden));
     const float2 Wt = sel2(samex, samey, fma2(mul2(mul2(add2(r1s, mul2(u2, u2)), i12), rden), pps, add2(i1s, i2s)),
                            mul2(sub2(f2(3.0f), S2), rden));
-    const float2 J0_3 = mul2(J0, f2(1.0f / 3.0f));
-    const float2 J2 = mul2(J0_3, Wt);
-    const float2 J4 = mul2(J0_3, S2);
-    const float2 A0 = fma2(k.a2x3, J2, add2(J0, J0));
-    const float2 A1 = fma2(k.na2x3, nJ3, add2(J1, J1));
-    const float2 Rb = fma2(Rpx, bt[0], fma2(Rpy, bt[1], mul2(Rpz, bt[2])));
-    const float2 Rw = fma2(Rpx, w[0], fma2(Rpy, w[1], mul2(Rpz, w[2])));
-    const float2 qR = fma2(Rpx, S.q[0], fma2(Rpy, S.q[1], mul2(Rpz, S.q[2])));
-    const float2 nc1tb = mul2(k.nc1, tb);
-    const float2 c3qR = mul2(k.c2x3, qR);
-    const float2 nc2J0 = mul2(k.nc2, J0);
-    const float2 c2J1 = mul2(k.c2, J1);
-    const float2 cRxb = mul2(nc1tb, A0);
-    const float2 cq = fma2(nc1tb, A1, fma2(c2J1, tb, mul2(nc2J0, Rb)));
-    const float2 cRp = fma2(c3qR, fma2(nJ3, tb, mul2(J2, Rb)), mul2(nc2J0, qb));
-    const float2 ct = fma2(k.nc1, fma2(A0, Rw, mul2(A1, qb)), fma2(c2J1, qb, mul2(c3qR, fma2(nJ3, Rb, mul2(J4, tb)))));
-    const float2 cb = mul2(mul2(k.c2, qR), sub2(A0, J0));
+    const float2 K2 = mul2(J0, Wt);
+    const float2 K4 = mul2(J0, S2);
+    const float2 A0 = fma2(a2, K2, add2(J0, J0));
+    const float2 A1 = fma2(a2, K3, add2(J1, J1));
     // Rp x b
     const float2 Xx = fma2(Rpy, S.b[2], mul2(Rpz, S.nb[1]));
     const float2 Xy = fma2(Rpz, S.b[0], mul2(Rpx, S.nb[2]));
     const float2 Xz = fma2(Rpx, S.b[1], mul2(Rpy, S.nb[0]));
+    const float2 Rb = fma2(Rpx, bt[0], fma2(Rpy, bt[1], mul2(Rpz, bt[2])));
+    const float2 nRb = mul2(Rb, f2(-1.0f));
+    const float2 Rw = fma2(Xx, bt[0], fma2(Xy, bt[1], mul2(Xz, bt[2])));
+    const float2 qR = fma2(Rpx, S.q[0], fma2(Rpy, S.q[1], mul2(Rpz, S.q[2])));
+    const float2 cRxb = mul2(P.nrtb, A0);
+    const float2 cq = fma2(P.nrtb, A1, fma2(J1, P.tb, mul2(J0, nRb)));
+    const float2 cRp = fma2(qR, fma2(K3, P.ntb, mul2(K2, Rb)), mul2(J0, P.nqb));
+    const float2 ct = fma2(nr, fma2(A0, Rw, mul2(A1, P.qb)), fma2(J1, P.qb, mul2(qR, fma2(K3, nRb, mul2(K4, P.tb)))));
+    const float2 cb = mul2(qR, sub2(A0, J0));
     s[0] = fma2(cRxb, Xx, fma2(cq, S.q[0], fma2(cRp, Rpx, fma2(ct, S.t[0], mul2(cb, bt[0])))));
     s[1] = fma2(cRxb, Xy, fma2(cq, S.q[1], fma2(cRp, Rpy, fma2(ct, S.t[1], mul2(cb, bt[1])))));
     s[2] = fma2(cRxb, Xz, fma2(cq, S.q[2], fma2(cRp, Rpz, fma2(ct, S.t[2], mul2(cb, bt[2])))));
@@ -364,19 +348,14 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
             }
         }
     }
-    float2 SH[2][3], SC[2][3];
-#pragma unroll
-    for (int p = 0; p < 2; ++p)
-#pragma unroll
-        for (int e = 0; e < 3; ++e) SH[p][e] = SC[p][e] = f2(0.0f);
+    // FP64 sums per Gauss point (far-field tile sums and near-field values)
 #pragma unroll
     for (int k = 0; k < 12; ++k) sm.nacc[k * TPB + threadIdx.x] = 0.0;
     // loop-invariant constants held in registers (not re-derived from FP64 inputs in the loop)
-    float kc[7] = {(float)c.a2, (float)(3.0 * c.a2), (float)(-3.0 * c.a2), (float)(-c.c1),
-                   (float)c.c2, (float)(-c.c2), (float)(3.0 * c.c2)};
-#pragma unroll
-    for (int e = 0; e < 7; ++e) opaque(kc[e]);
-    const K2 kk{f2(kc[0]), f2(kc[1]), f2(kc[2]), f2(kc[3]), f2(kc[4]), f2(kc[5]), f2(kc[6])};
+    float kc[2] = {(float)c.a2, (float)(-c.c1 / c.c2)};
+    opaque(kc[0]);
+    opaque(kc[1]);
+    const float2 a2 = f2(kc[0]), nr = f2(kc[1]);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     uint2* wq = sm.queue[threadIdx.x >> 5];
@@ -405,6 +384,11 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
             d[10] = make_float4(-v[11], -v[11], -v[12], -v[12]);
         }
         __syncthreads();
+        float2 SP[2][3];  // FP32 sums of this tile, / c2
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int e = 0; e < 3; ++e) SP[p][e] = f2(0.0f);
         for (int jj = 0; jj < cnt; ++jj) {
             const float2* r = sm.tile + jj * MIX_REC;
             if (!(r[6].x > 0.0f)) continue;  // zero-length source (uniform branch)
@@ -419,12 +403,12 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
                 S.nt[e] = r[16 + e];
                 S.nb[e] = r[19 + e];
             }
-            // per-pair constants t.b', q.b', b x b'
-            const float2 tb = fma2(S.t[0], bt2[0], fma2(S.t[1], bt2[1], mul2(S.t[2], bt2[2])));
-            const float2 qb = fma2(S.q[0], bt2[0], fma2(S.q[1], bt2[1], mul2(S.q[2], bt2[2])));
-            const float2 w[3] = {fma2(S.b[1], bt2[2], mul2(S.nb[2], bt2[1])),
-                                 fma2(S.b[2], bt2[0], mul2(S.nb[0], bt2[2])),
-                                 fma2(S.b[0], bt2[1], mul2(S.nb[1], bt2[0]))};
+            Pair2 P;
+            P.tb = fma2(S.t[0], bt2[0], fma2(S.t[1], bt2[1], mul2(S.t[2], bt2[2])));
+            P.qb = fma2(S.q[0], bt2[0], fma2(S.q[1], bt2[1], mul2(S.q[2], bt2[2])));
+            P.ntb = mul2(P.tb, f2(-1.0f));
+            P.nqb = mul2(P.qb, f2(-1.0f));
+            P.nrtb = mul2(nr, P.tb);
             // both Gauss-point pairs first (two independent chains), then the sums
             float2 v[2][3], dd[2];
 #pragma unroll
@@ -432,23 +416,22 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
                 const float2 R0x = add2(sub2(XH[p][0], h1[0]), sub2(XL[p][0], l1[0]));
                 const float2 R0y = add2(sub2(XH[p][1], h1[1]), sub2(XL[p][1], l1[1]));
                 const float2 R0z = add2(sub2(XH[p][2], h1[2]), sub2(XL[p][2], l1[2]));
-                seg_sigma_b2(R0x, R0y, R0z, S, bt2, w, tb, qb, kk, v[p], dd[p]);
+                seg_sigma_b2(R0x, R0y, R0z, S, bt2, P, a2, nr, v[p], dd[p]);
             }
-            bool nr[2][2];
+            bool nrq[2][2];
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
-                nr[p][0] = active && dd[p].x < near2;
-                nr[p][1] = active && dd[p].y < near2;
+                nrq[p][0] = active && dd[p].x < near2;
+                nrq[p][1] = active && dd[p].y < near2;
                 // far lanes go to the FP32 sums; near lanes to the FP64 queue
 #pragma unroll
-                for (int e = 0; e < 3; ++e)
-                    kahan_add2(SH[p][e], SC[p][e], sel2(nr[p][0], nr[p][1], f2(0.0f), v[p][e]));
+                for (int e = 0; e < 3; ++e) SP[p][e] = add2(SP[p][e], sel2(nrq[p][0], nrq[p][1], f2(0.0f), v[p][e]));
             }
-            if (__any_sync(0xffffffffu, nr[0][0] || nr[0][1] || nr[1][0] || nr[1][1])) {
+            if (__any_sync(0xffffffffu, nrq[0][0] || nrq[0][1] || nrq[1][0] || nrq[1][1])) {
                 const unsigned js = (unsigned)(j0 + jj);
 #pragma unroll
                 for (int qp = 0; qp < 4; ++qp) {
-                    const bool mine = nr[qp >> 1][qp & 1];
+                    const bool mine = nrq[qp >> 1][qp & 1];
                     const unsigned bal = __ballot_sync(0xffffffffu, mine);
                     if (mine) wq[qn + __popc(bal & lt)] = make_uint2(js, ((unsigned)lane << 2) | (unsigned)qp);
                     qn += __popc(bal);
@@ -462,6 +445,16 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
                 }
             }
         }
+        // tile sums to FP64, restoring the factor c2
+        __syncwarp();
+#pragma unroll
+        for (int p = 0; p < 2; ++p)
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {
+                double* acc = sm.nacc + (6 * p + e) * TPB + threadIdx.x;
+                acc[0] = fma(c.c2, (double)SP[p][e].x, acc[0]);
+                acc[3 * TPB] = fma(c.c2, (double)SP[p][e].y, acc[3 * TPB]);
+            }
     }
     if (qn > 0) {
         __syncwarp();
@@ -473,13 +466,9 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
     if (!active) return;
     double acc[4][3];
 #pragma unroll
-    for (int p = 0; p < 2; ++p)
+    for (int qp = 0; qp < 4; ++qp)
 #pragma unroll
-        for (int e = 0; e < 3; ++e) {
-            acc[2 * p][e] = ((double)SH[p][e].x - (double)SC[p][e].x) + sm.nacc[(6 * p + e) * TPB + threadIdx.x];
-            acc[2 * p + 1][e] =
-                ((double)SH[p][e].y - (double)SC[p][e].y) + sm.nacc[(6 * p + 3 + e) * TPB + threadIdx.x];
-        }
+        for (int e = 0; e < 3; ++e) acc[qp][e] = sm.nacc[(3 * qp + e) * TPB + threadIdx.x];
     tile_store(a, seg, Dx, Dy, Dz, bt, acc);
 }
 
