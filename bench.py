@@ -13,8 +13,11 @@ mobility, Lp/rho averaging, explicit Euler -- over `--dd-steps` DD steps.
   e2e     : the same metric through the C ABI with host buffers: per step
             positions copied in from pinned host memory (ptadd_set_nodes),
             the burst, positions and averages copied back;
-  roofline: the pair-stress kernel, algorithmic FP64/FP32 FLOPs per launch
-            over its CUDA-event time, against the measured FMA peak;
+  roofline: the pair-stress kernel, algorithmic FLOPs per launch over its
+            CUDA-event time, against the FMA peak of its arithmetic type from
+            the unit counts and the maximum SM clock (FP32: 128 FMA lanes per
+            SM; FP64: 2 per SM), with the FMA-chain peaks measured in the
+            same run beside it;
   cpu_baseline: the FP64 CPU oracle on a bounded sample of the same workload.
 
 Multi-GPU (torchrun): every rank runs its own realisation (seed + rank);
@@ -53,7 +56,7 @@ WORKLOAD = ("1024 circular FCC glide loops x 32 segments = 32768 segments, 5 um 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
@@ -92,7 +95,7 @@ class ClockSampler:
             os.close(fd)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -132,7 +135,7 @@ class ClockSampler:
 # ---------------------------------------------------------------- helpers
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("seg_field.cuh", "dd_kernels.cu"):
+    for f in ("seg_field.cuh", "pair_tile.cuh", "dd_kernels.cu"):
         h.update(open(os.path.join(ROOT, "paper_2005_02498_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -229,8 +232,10 @@ def run_ours(args):
     info = ctx.info()
     pairs_per_bench_step = info["pairs_per_step"] * args.dd_steps
 
-    peak_fp64 = ptadd.fma_peak(local, fp64=True, seconds=2.0)
-    peak_fp32 = ptadd.fma_peak(local, fp64=False, seconds=2.0)
+    meas_fp64 = ptadd.fma_peak(local, fp64=True, seconds=2.0)
+    meas_fp32 = ptadd.fma_peak(local, fp64=False, seconds=2.0)
+    meas_fp32x2 = ptadd.fma_peak(local, fp64=False, packed=True, seconds=2.0)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
@@ -287,8 +292,7 @@ def run_ours(args):
         v64 = world * pairs_per_bench_step * args.fp64_steps / (ms64 * 1e-3)
         fp64_cmp = {"value": v64, "unit": "pair-evals/s", "steps": args.fp64_steps,
                     "ms_per_step": ms64 / args.fp64_steps, "speedup_of_mixed": value / v64,
-                    "pair_kernel_frac_of_fp64_peak":
-                        FLOPS_PER_PAIR * p64["pair_evals"] / (p64["pair_ms"] * 1e-3) / peak_fp64}
+                    "pair_kernel_tflops": FLOPS_PER_PAIR * p64["pair_evals"] / (p64["pair_ms"] * 1e-3) / 1e12}
         ctx.set_precision(prec)
 
     # ---- end to end through the C ABI with pinned host buffers
@@ -320,15 +324,22 @@ def run_ours(args):
     avg_ms = prof["pair_ms"] / max(1, prof["pair_launches"])
     evals_per_launch = prof["pair_evals"] / max(1, prof["pair_launches"])
     achieved = FLOPS_PER_PAIR * evals_per_launch / (avg_ms * 1e-3)
-    peak = peak_fp64 if args.precision == "fp64" else peak_fp32
+    max_mhz = clk.get("sm_max_mhz") if clk and clk.get("sm_max_mhz") == clk.get("sm_max_mhz") else None
+    max_mhz = max_mhz or 2070.0
+    lanes = 2 if args.precision == "fp64" else 128  # FMA lanes per SM per clock
+    peak = sms * lanes * 2 * max_mhz * 1e6
+    if fp64_cmp:
+        fp64_cmp["pair_kernel_frac_of_fp64_peak"] = fp64_cmp["pair_kernel_tflops"] * 1e12 / (sms * 2 * 2 * max_mhz * 1e6)
     roof = {"kernel": "pair_fp64_kernel" if args.precision == "fp64" else "pair_mixed_kernel",
             "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": recorded_traffic(args.precision),
             "flops_per_pair": FLOPS_PER_PAIR, "pair_evals_per_launch": evals_per_launch,
             "avg_launch_ms": avg_ms,
-            "peak_source": "measured in this run: ptadd_fma_peak, %s FMA chains on every SM for ~2 s "
-                           "(no FP64/FP32 figure in MEASURED_PEAKS.json)" % ("FP64" if args.precision == "fp64" else "FP32"),
-            "peak_fp64_tflops": peak_fp64 / 1e12, "peak_fp32_tflops": peak_fp32 / 1e12}
+            "peak_source": "%s FMA peak from unit counts: %d SMs x %d FMA lanes x 2 FLOP x %.0f MHz (maximum SM "
+                           "clock); MEASURED_PEAKS.json has no FP32/FP64 figure"
+                           % ("FP64" if args.precision == "fp64" else "FP32", sms, lanes, max_mhz),
+            "measured_fma_chain_tflops": {"fp64": meas_fp64 / 1e12, "fp32": meas_fp32 / 1e12,
+                                          "fp32_packed_pairs": meas_fp32x2 / 1e12}}
 
     out = {"metric": "segment-pair evals/s", "value": value, "unit": "pair-evals/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
