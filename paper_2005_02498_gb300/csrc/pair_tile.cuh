@@ -128,9 +128,10 @@ __device__ __forceinline__ void pair_tile_fp64(const TileArgs& a, const Consts& 
 // Every (Gauss point, source) pair is first located in FP32 from hi/lo-split
 // coordinates; if the point lies within 10 a of the source segment the pair
 // is evaluated in FP64 from the FP64 records, otherwise in FP32.  Per Gauss
-// point the FP32 contributions of one shared-memory tile of sources are
-// summed in FP32 and the tile sums, like the FP64 near-field values, are
-// accumulated in FP64; the FP64 sums feed the PK force and the nodal assembly.
+// point the FP32 contributions are summed in three levels: plainly over
+// groups of SUM_GROUP sources, with Kahan compensation over the groups of one
+// shared-memory tile, and in FP64 over the tiles (where the FP64 near-field
+// values also go); the FP64 sums feed the PK force and the nodal assembly.
 //
 // The FP32 work is packed: Gauss points (0,1) and (2,3) travel as the two
 // lanes of a float2, so every add, multiply and fused multiply-add of the
@@ -146,6 +147,16 @@ __device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b)
 {
     return make_float2(cx ? a.x : b.x, cy ? a.y : b.y);
 }
+// s + v with Kahan compensation c (s - c is the compensated sum)
+__device__ __forceinline__ void kahan_add2(float2& s, float2& c, float2 v)
+{
+    const float2 y = sub2(v, c);
+    const float2 t = add2(s, y);
+    c = sub2(sub2(t, s), y);
+    s = t;
+}
+// sources summed plainly before a compensated add
+constexpr int SUM_GROUP = 16;
 // keep a register value opaque, so the compiler holds it instead of
 // recomputing it from its (FP64) inputs inside the loop
 __device__ __forceinline__ void opaque(float& x) { asm volatile("" : "+f"(x)); }
@@ -265,7 +276,8 @@ constexpr int NEAR_Q = 160;  // <= 31 waiting + 128 added by one source (4 Gauss
 template <int TILE, int TPB>
 struct MixSmem {
     float2 tile[TILE * MIX_REC];  // source records (MIX_REC float2 each)
-    double nacc[12 * TPB];             // FP64 near sums: [qp * 3 + e][thread]
+    double nacc[12 * TPB];             // FP64 sums: [qp * 3 + e][thread]
+    float2 ksum[12 * TPB];             // Kahan sums of a tile: [p * 3 + e][thread], then compensations
     uint2 queue[TPB / 32][NEAR_Q];
 };
 
@@ -384,76 +396,93 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
             d[10] = make_float4(-v[11], -v[11], -v[12], -v[12]);
         }
         __syncthreads();
-        float2 SP[2][3];  // FP32 sums of this tile, / c2
+        // plain sums of the current group of SUM_GROUP sources (/ c2); the
+        // Kahan sums of the tile and their compensations wait in shared memory
+        float2 SG[2][3];
 #pragma unroll
-        for (int p = 0; p < 2; ++p)
+        for (int k = 0; k < 12; ++k) sm.ksum[k * TPB + threadIdx.x] = f2(0.0f);
+        for (int g0 = 0; g0 < cnt; g0 += SUM_GROUP) {
+            const int g1 = min(cnt, g0 + SUM_GROUP);
 #pragma unroll
-            for (int e = 0; e < 3; ++e) SP[p][e] = f2(0.0f);
-        for (int jj = 0; jj < cnt; ++jj) {
-            const float2* r = sm.tile + jj * MIX_REC;
-            if (!(r[6].x > 0.0f)) continue;  // zero-length source (uniform branch)
-            Src2 S;
-            const float2 h1[3] = {r[0], r[1], r[2]}, l1[3] = {r[3], r[4], r[5]};
-            S.L = r[6];
+            for (int p = 0; p < 2; ++p)
 #pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                S.t[e] = r[7 + e];
-                S.b[e] = r[10 + e];
-                S.q[e] = r[13 + e];
-                S.nt[e] = r[16 + e];
-                S.nb[e] = r[19 + e];
-            }
-            Pair2 P;
-            P.tb = fma2(S.t[0], bt2[0], fma2(S.t[1], bt2[1], mul2(S.t[2], bt2[2])));
-            P.qb = fma2(S.q[0], bt2[0], fma2(S.q[1], bt2[1], mul2(S.q[2], bt2[2])));
-            P.ntb = mul2(P.tb, f2(-1.0f));
-            P.nqb = mul2(P.qb, f2(-1.0f));
-            P.nrtb = mul2(nr, P.tb);
-            // both Gauss-point pairs first (two independent chains), then the sums
-            float2 v[2][3], dd[2];
+                for (int e = 0; e < 3; ++e) SG[p][e] = f2(0.0f);
+            for (int jj = g0; jj < g1; ++jj) {
+                const float2* r = sm.tile + jj * MIX_REC;
+                if (!(r[6].x > 0.0f)) continue;  // zero-length source (uniform branch)
+                Src2 S;
+                const float2 h1[3] = {r[0], r[1], r[2]}, l1[3] = {r[3], r[4], r[5]};
+                S.L = r[6];
 #pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const float2 R0x = add2(sub2(XH[p][0], h1[0]), sub2(XL[p][0], l1[0]));
-                const float2 R0y = add2(sub2(XH[p][1], h1[1]), sub2(XL[p][1], l1[1]));
-                const float2 R0z = add2(sub2(XH[p][2], h1[2]), sub2(XL[p][2], l1[2]));
-                seg_sigma_b2(R0x, R0y, R0z, S, bt2, P, a2, nr, v[p], dd[p]);
-            }
-            bool nrq[2][2];
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                nrq[p][0] = active && dd[p].x < near2;
-                nrq[p][1] = active && dd[p].y < near2;
-                // far lanes go to the FP32 sums; near lanes to the FP64 queue
-#pragma unroll
-                for (int e = 0; e < 3; ++e) SP[p][e] = add2(SP[p][e], sel2(nrq[p][0], nrq[p][1], f2(0.0f), v[p][e]));
-            }
-            if (__any_sync(0xffffffffu, nrq[0][0] || nrq[0][1] || nrq[1][0] || nrq[1][1])) {
-                const unsigned js = (unsigned)(j0 + jj);
-#pragma unroll
-                for (int qp = 0; qp < 4; ++qp) {
-                    const bool mine = nrq[qp >> 1][qp & 1];
-                    const unsigned bal = __ballot_sync(0xffffffffu, mine);
-                    if (mine) wq[qn + __popc(bal & lt)] = make_uint2(js, ((unsigned)lane << 2) | (unsigned)qp);
-                    qn += __popc(bal);
-                    near_warp += (unsigned)__popc(bal);
+                for (int e = 0; e < 3; ++e) {
+                    S.t[e] = r[7 + e];
+                    S.b[e] = r[10 + e];
+                    S.q[e] = r[13 + e];
+                    S.nt[e] = r[16 + e];
+                    S.nb[e] = r[19 + e];
                 }
-                while (qn >= 32) {
-                    __syncwarp();
-                    near_flush(a.pos, n, a.nxt, a.src, a.k64, seg, wq, 32, sm.nacc, TPB);
-                    near_shift(wq, qn);
-                    qn -= 32;
+                Pair2 P;
+                P.tb = fma2(S.t[0], bt2[0], fma2(S.t[1], bt2[1], mul2(S.t[2], bt2[2])));
+                P.qb = fma2(S.q[0], bt2[0], fma2(S.q[1], bt2[1], mul2(S.q[2], bt2[2])));
+                P.ntb = mul2(P.tb, f2(-1.0f));
+                P.nqb = mul2(P.qb, f2(-1.0f));
+                P.nrtb = mul2(nr, P.tb);
+                // both Gauss-point pairs first (two independent chains), then the sums
+                float2 v[2][3], dd[2];
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    const float2 R0x = add2(sub2(XH[p][0], h1[0]), sub2(XL[p][0], l1[0]));
+                    const float2 R0y = add2(sub2(XH[p][1], h1[1]), sub2(XL[p][1], l1[1]));
+                    const float2 R0z = add2(sub2(XH[p][2], h1[2]), sub2(XL[p][2], l1[2]));
+                    seg_sigma_b2(R0x, R0y, R0z, S, bt2, P, a2, nr, v[p], dd[p]);
                 }
+                bool nrq[2][2];
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    nrq[p][0] = active && dd[p].x < near2;
+                    nrq[p][1] = active && dd[p].y < near2;
+                    // far lanes go to the FP32 group sums; near lanes to the FP64 queue
+#pragma unroll
+                    for (int e = 0; e < 3; ++e)
+                        SG[p][e] = add2(SG[p][e], sel2(nrq[p][0], nrq[p][1], f2(0.0f), v[p][e]));
+                }
+                if (__any_sync(0xffffffffu, nrq[0][0] || nrq[0][1] || nrq[1][0] || nrq[1][1])) {
+                    const unsigned js = (unsigned)(j0 + jj);
+#pragma unroll
+                    for (int qp = 0; qp < 4; ++qp) {
+                        const bool mine = nrq[qp >> 1][qp & 1];
+                        const unsigned bal = __ballot_sync(0xffffffffu, mine);
+                        if (mine) wq[qn + __popc(bal & lt)] = make_uint2(js, ((unsigned)lane << 2) | (unsigned)qp);
+                        qn += __popc(bal);
+                        near_warp += (unsigned)__popc(bal);
+                    }
+                    while (qn >= 32) {
+                        __syncwarp();
+                        near_flush(a.pos, n, a.nxt, a.src, a.k64, seg, wq, 32, sm.nacc, TPB);
+                        near_shift(wq, qn);
+                        qn -= 32;
+                    }
+                }
+            }
+            // close the group
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                float2 sk = sm.ksum[k * TPB + threadIdx.x], ck = sm.ksum[(6 + k) * TPB + threadIdx.x];
+                kahan_add2(sk, ck, SG[k / 3][k % 3]);
+                sm.ksum[k * TPB + threadIdx.x] = sk;
+                sm.ksum[(6 + k) * TPB + threadIdx.x] = ck;
             }
         }
-        // tile sums to FP64, restoring the factor c2
-        __syncwarp();
+        // compensated tile sums to FP64, restoring the factor c2
 #pragma unroll
         for (int p = 0; p < 2; ++p)
 #pragma unroll
             for (int e = 0; e < 3; ++e) {
+                const float2 sk = sm.ksum[(3 * p + e) * TPB + threadIdx.x];
+                const float2 ck = sm.ksum[(6 + 3 * p + e) * TPB + threadIdx.x];
                 double* acc = sm.nacc + (6 * p + e) * TPB + threadIdx.x;
-                acc[0] = fma(c.c2, (double)SP[p][e].x, acc[0]);
-                acc[3 * TPB] = fma(c.c2, (double)SP[p][e].y, acc[3 * TPB]);
+                acc[0] = fma(c.c2, (double)sk.x - (double)ck.x, acc[0]);
+                acc[3 * TPB] = fma(c.c2, (double)sk.y - (double)ck.y, acc[3 * TPB]);
             }
     }
     if (qn > 0) {
