@@ -59,7 +59,7 @@ struct MlpDev {
     double box_lo[NIN], box_hi[NIN];
     double chol[NIN * NIN];  // lower Cholesky factor of the training covariance (standardised x)
     double d2_thr = 0.0;
-    float* d_norm = nullptr;  // device copy (FP32): xm, xs, ym, ys, box_lo, box_hi, chol, d2_thr
+    float* d_norm = nullptr;  // device copy (FP32): xm, xs, ym, ys, box_lo, box_hi, chol^-1, d2_thr
 };
 
 namespace {
@@ -269,72 +269,6 @@ __global__ void mlp_unpack_y(int64_t n, const float* __restrict__ Y, float* __re
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n * NOUT) return;
     yn[i] = Y[(i / NOUT) * 16 + (i % NOUT)];
-}
-
-// ------------------------------------------------------ closure maps
-struct NormView {
-    const double* xm;
-    const double* xs;
-    const double* ym;
-    const double* ys;
-    const double* lo;
-    const double* hi;
-    const double* chol;
-    double d2_thr;
-};
-
-__device__ __forceinline__ float feature(const double* raw, int c)
-{
-    return c < 6 ? (float)(raw[c] * (1.0 / SIG_SCALE)) : log10f((float)raw[c] + (float)RHO_FLOOR);
-}
-
-// raw features [n x 30] -> standardised BF16 X [rows x 32], and the
-// trust-region flag of every point.  FP32 throughout: the values feed BF16
-// operands, and FP64 runs at 1/64 of the FP32 rate on this GPU.
-__global__ void surr_inputs(int64_t n, int64_t rows, const double* __restrict__ raw, const float* __restrict__ nv,
-                            __nv_bfloat16* __restrict__ X, uint8_t* __restrict__ in_region)
-{
-    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r >= rows) return;
-    const float* xm = nv;
-    const float* xs = nv + NIN;
-    const float* lo = nv + 2 * NIN + 2 * NOUT;
-    const float* hi = lo + NIN;
-    const float* L = hi + NIN;
-    const float d2_thr = L[NIN * NIN];
-    float z[NIN];
-    bool inbox = true;
-    if (r < n) {
-        for (int c = 0; c < NIN; ++c) {
-            z[c] = (feature(raw + r * NIN, c) - xm[c]) / xs[c];
-            inbox = inbox && z[c] >= lo[c] && z[c] <= hi[c];
-        }
-    } else {
-        for (int c = 0; c < NIN; ++c) z[c] = 0.0f;
-    }
-    for (int c = 0; c < 32; ++c) X[r * 32 + c] = __float2bfloat16_rn(c < NIN ? z[c] : 0.0f);
-    if (r < n && in_region) {
-        // Mahalanobis distance^2 = |L^{-1} z|^2 (forward substitution)
-        float w[NIN], d2 = 0.0f;
-        for (int i = 0; i < NIN; ++i) {
-            float s = z[i];
-            for (int j = 0; j < i; ++j) s -= L[i * NIN + j] * w[j];
-            w[i] = s / L[i * NIN + i];
-            d2 += w[i] * w[i];
-        }
-        in_region[r] = (inbox && d2 <= d2_thr) ? 1 : 0;
-    }
-}
-
-__global__ void surr_outputs(int64_t n, const float* __restrict__ Y, const float* __restrict__ nv,
-                             double* __restrict__ lp6)
-{
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n * NOUT) return;
-    const float* ym = nv + 2 * NIN;
-    const float* ys = ym + NOUT;
-    const int c = (int)(i % NOUT);
-    lp6[i] = (double)(Y[(i / NOUT) * 16 + c] * ys[c] + ym[c]);
 }
 
 // ------------------------------------------------------------ passes
@@ -768,6 +702,35 @@ ptadd_status ptadd_mlp_forward(ptadd_ctx* ctx, int64_t n, const float* xn, float
 
 
 // ----------------------------------------------------------- closures
+// Device copy of the maps (FP32): xm, xs, ym, ys, box lo, box hi, the inverse
+// of the Cholesky factor (lower triangle, so that the Mahalanobis distance is
+// |L^-1 z|^2 by independent dot products), threshold.
+static ptadd_status upload_maps(MlpDev& m)
+{
+    std::vector<double> inv(NIN * NIN, 0.0);
+    for (int c = 0; c < NIN; ++c)  // forward substitution for column c of L^-1
+        for (int i = c; i < NIN; ++i) {
+            double s2 = i == c ? 1.0 : 0.0;
+            for (int j = c; j < i; ++j) s2 -= m.chol[i * NIN + j] * inv[j * NIN + c];
+            inv[i * NIN + c] = s2 / m.chol[i * NIN + i];
+        }
+    std::vector<float> nvf(4 * NIN + 2 * NOUT + NIN * NIN + 1);
+    for (int c = 0; c < NIN; ++c) {
+        nvf[c] = (float)m.xm[c];
+        nvf[NIN + c] = (float)m.xs[c];
+        nvf[2 * NIN + 2 * NOUT + c] = (float)m.box_lo[c];
+        nvf[3 * NIN + 2 * NOUT + c] = (float)m.box_hi[c];
+    }
+    for (int c = 0; c < NOUT; ++c) {
+        nvf[2 * NIN + c] = (float)m.ym[c];
+        nvf[2 * NIN + NOUT + c] = (float)m.ys[c];
+    }
+    for (int i = 0; i < NIN * NIN; ++i) nvf[4 * NIN + 2 * NOUT + i] = (float)inv[i];
+    nvf[4 * NIN + 2 * NOUT + NIN * NIN] = (float)m.d2_thr;
+    PTADD_CUDA(cudaMemcpy(m.d_norm, nvf.data(), nvf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    return PTADD_OK;
+}
+
 static double host_feature(const double* raw, int c)
 {
     return c < 6 ? (double)(float)(raw[c] * (1.0 / SIG_SCALE)) : (double)log10f((float)raw[c] + (float)RHO_FLOOR);
@@ -856,19 +819,8 @@ ptadd_status ptadd_surrogate_fit(ptadd_ctx* ctx, int64_t n, const double* feat, 
     std::sort(sorted.begin(), sorted.end());
     m.d2_thr = sorted[(size_t)std::min<int64_t>(n - 1, (int64_t)ceil(0.99 * n) - 1)];
     m.have_norm = true;
-    std::vector<double> nv(4 * NIN + 2 * NOUT + NIN * NIN + 1);
-    memcpy(&nv[0], m.xm, sizeof(m.xm));
-    memcpy(&nv[NIN], m.xs, sizeof(m.xs));
-    memcpy(&nv[2 * NIN], m.ym, sizeof(m.ym));
-    memcpy(&nv[2 * NIN + NOUT], m.ys, sizeof(m.ys));
-    memcpy(&nv[2 * NIN + 2 * NOUT], m.box_lo, sizeof(m.box_lo));
-    memcpy(&nv[3 * NIN + 2 * NOUT], m.box_hi, sizeof(m.box_hi));
-    memcpy(&nv[4 * NIN + 2 * NOUT], m.chol, sizeof(m.chol));
-    nv[4 * NIN + 2 * NOUT + NIN * NIN] = m.d2_thr;
-    {
-        std::vector<float> nvf(nv.begin(), nv.end());
-        PTADD_CUDA(cudaMemcpy(m.d_norm, nvf.data(), nvf.size() * sizeof(float), cudaMemcpyHostToDevice));
-    }
+    ptadd_status st = upload_maps(m);
+    if (st != PTADD_OK) return st;
     // normalised training arrays
     std::vector<float> xn((size_t)n * NIN), yn((size_t)n * NOUT);
     for (int64_t i = 0; i < n * NIN; ++i) xn[i] = (float)z[i];
@@ -890,23 +842,11 @@ ptadd_status ptadd_surrogate_predict_dev(ptadd_ctx* ctx, int64_t n, const double
         return PTADD_ERR_STATE;
     }
     if (n < 1 || !feat_dev || !lp6_dev) return marg("need n >= 1 and arrays");
-    cudaStream_t s = ctx->stream;
-    const int64_t chunk = std::min<int64_t>((n + 127) / 128 * 128, 131072);
-    st = ensure_work(m, chunk);
-    if (st != PTADD_OK) return st;
-    int64_t launches = 0;
-    for (int64_t r0 = 0; r0 < n; r0 += chunk) {
-        const int64_t k = std::min(chunk, n - r0);
-        const int64_t rows = (k + 127) / 128 * 128;
-        surr_inputs<<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(k, rows, feat_dev + r0 * NIN, m.d_norm, m.X,
-                                                                     in_region_dev ? in_region_dev + r0 : nullptr);
-        PTADD_CUDA(cudaGetLastError());
-        PTADD_CUDA(forward(m, rows, false, s, &launches));
-        surr_outputs<<<(unsigned)((k * NOUT + 255) / 256), 256, 0, s>>>(k, m.Y, m.d_norm, lp6_dev + r0 * NOUT);
-        PTADD_CUDA(cudaGetLastError());
-        launches += 2;
-    }
-    ctx->kernel_launches += launches;
+    // one fused persistent kernel: input map, trust region, the four layers, output map
+    const __nv_bfloat16* W[4] = {m.Wb[0], m.Wb[1], m.Wb[2], m.Wb[3]};
+    const float* b[4] = {m.b[0], m.b[1], m.b[2], m.b[3]};
+    PTADD_CUDA(launch_mlp_infer(feat_dev, n, m.d_norm, W, b, lp6_dev, in_region_dev, m.err, ctx->stream));
+    ctx->kernel_launches += 1;
     return PTADD_OK;
 }
 
@@ -1017,10 +957,8 @@ ptadd_status ptadd_surrogate_set_state(ptadd_ctx* ctx, const void* buf, size_t b
     memcpy(m.box_hi, &nv[3 * NIN + 2 * NOUT], sizeof(m.box_hi));
     memcpy(m.chol, &nv[4 * NIN + 2 * NOUT], sizeof(m.chol));
     m.d2_thr = nv[4 * NIN + 2 * NOUT + NIN * NIN];
-    {
-        std::vector<float> nvf(nv.begin(), nv.end());
-        PTADD_CUDA(cudaMemcpy(m.d_norm, nvf.data(), nvf.size() * sizeof(float), cudaMemcpyHostToDevice));
-    }
+    st = upload_maps(m);
+    if (st != PTADD_OK) return st;
     m.have_norm = true;
     return PTADD_OK;
 }

@@ -1,0 +1,404 @@
+// mlp_infer.cu -- fused surrogate inference: raw closure inputs -> sym(Lp),
+// the whole 30 -> 256 -> 256 -> 256 -> 6 network in one persistent kernel.
+//
+// One CTA of 512 threads per SM walks 128-row tiles of the input.  Per tile:
+//   1. the tile's raw features arrive in a transposed shared-memory staging
+//      buffer (cp.async, issued while the previous tile was in its layers);
+//      four threads per row map it (sigma / 200 MPa, log10(rho + 1e10)),
+//      standardise it, evaluate the trust region (box, and the Mahalanobis
+//      distance |L^-1 z|^2 split over the four threads) and write one 8-column
+//      slice each of the BF16 row of the layer-1 operand;
+//   2. four tcgen05 MMA chains (BF16 x BF16 -> FP32 in one 256-column TMEM
+//      accumulator) with the hidden activations kept in shared memory: in
+//      every epilogue warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its rows),
+//      columns 64 (w / 4) .. + 63, adds the bias, applies GELU and writes BF16
+//      in the canonical operand layout of the next layer;
+//   3. the last epilogue de-standardises the 6 outputs and writes them in FP64.
+// W1 (256 x 32) and W4 (16 x 256) stay resident in shared memory; W2 and W3
+// (256 x 256 each) stream from L2 in K-chunks of 64 through two buffers
+// filled with cp.async two chunks ahead of the MMAs that read them.  Layouts
+// are the no-swizzle K-major canonical layout of the tensor core (8-row x
+// 16-byte core matrices, K-adjacent core matrices 128 B apart, 8-row groups
+// SBO bytes apart).  Every mbarrier wait has an iteration limit; a wait that
+// gives up sets the error flag and the CTA leaves after a last bounded wait.
+//
+// GELU here is 0.5 z (1 + erf(z / sqrt 2)) with erf(x) ~ tanh(x (A + B x^2)),
+// A = 1.12967582605, B = 0.0997927024 (a minimax fit of erf on [0, 6] made
+// for this kernel; |error| <= 2.8e-4), the tanh by the hardware f16x2
+// approximation (one special-function instruction per two values).  The
+// activations are rounded to BF16 (relative step 2^-8 = 3.9e-3) right after,
+// so the approximation stays below the rounding of the value it produces.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "ptadd_internal.cuh"
+#include "tc_gemm.cuh"
+
+namespace ptadd {
+
+namespace {
+
+constexpr int IT = 512;  // threads per CTA (rows per tile: 128)
+constexpr int NF = 30, NO = 6;
+constexpr int X_BYTES = 128 * 32 * 2;   // layer-1 A operand, SBO 512
+constexpr int W1_BYTES = 256 * 32 * 2;  // SBO 512
+constexpr int W4_BYTES = 16 * 256 * 2;  // SBO 4096
+constexpr int H_BYTES = 128 * 256 * 2;  // hidden activations, SBO 4096
+constexpr int WC_BYTES = 256 * 64 * 2;  // one K-chunk of W2 or W3, SBO 1024
+constexpr int NV_FLOATS = 4 * NF + 2 * NO + NF * NF + 1;
+constexpr int OFF_X = 0;
+constexpr int OFF_W1 = OFF_X + X_BYTES;
+constexpr int OFF_W4 = OFF_W1 + W1_BYTES;
+constexpr int OFF_H = OFF_W4 + W4_BYTES;
+constexpr int OFF_WC = OFF_H + H_BYTES;
+constexpr int OFF_NV = OFF_WC + 2 * WC_BYTES;
+constexpr int OFF_D2 = OFF_NV + ((NV_FLOATS * 4 + 15) / 16) * 16;  // [4][128] partial Mahalanobis sums
+constexpr int OFF_B = OFF_D2 + 4 * 128 * 4;                        // biases: 3 x 256 + 16
+constexpr int F_LD = 129;                                          // staging row pitch (doubles)
+constexpr int OFF_F = OFF_B + (3 * 256 + 16) * 4;                  // raw features [30][F_LD], transposed
+constexpr int INFER_SMEM = OFF_F + NF * F_LD * 8 + 1024;           // + alignment slack
+
+__device__ __forceinline__ uint32_t canon(int r, int k, int sbo)
+{
+    return (uint32_t)((r >> 3) * sbo + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async8(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(__cvta_generic_to_global(src))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Row-major BF16 [rows x K] (global) -> canonical layout with 8-row groups sbo apart.
+__device__ __forceinline__ void copy_canon(uint8_t* dst, const __nv_bfloat16* src, int rows, int K, int sbo)
+{
+    const int per_row = K / 8;
+    for (int v = threadIdx.x; v < rows * per_row; v += IT) {
+        const int r = v / per_row, kc = v % per_row;
+        *reinterpret_cast<uint4*>(dst + (r >> 3) * sbo + kc * 128 + (r & 7) * 16) =
+            *reinterpret_cast<const uint4*>(src + (int64_t)r * K + kc * 8);
+    }
+}
+
+// Chunk q of the W2/W3 stream (8 per tile: W2 K-chunks 0..3, W3 K-chunks 0..3).
+__device__ __forceinline__ void issue_chunk(uint32_t dst, const __nv_bfloat16* W2, const __nv_bfloat16* W3,
+                                            int64_t q)
+{
+    const int j = (int)(q & 7);
+    const __nv_bfloat16* W = j < 4 ? W2 : W3;
+    const int k0 = 64 * (j & 3);
+    // a warp covers 8 rows x 4 core-matrix columns: 64 contiguous bytes per row
+    // in global memory, 128 contiguous bytes per 8 threads in shared memory
+    for (int v = threadIdx.x; v < 256 * 8; v += IT) {
+        const int r = (v >> 6) * 8 + (v & 7), kk = (v >> 3) & 7;
+        cp_async16(dst + (r >> 3) * 1024 + kk * 128 + (r & 7) * 16, W + r * 256 + k0 + kk * 8);
+    }
+}
+
+// Raw features of one tile (rows r0 .. r0 + valid - 1) into the transposed staging buffer.
+__device__ __forceinline__ void issue_features(uint32_t dst, const double* feat, int64_t r0, int valid)
+{
+    for (int e = threadIdx.x; e < valid * 30; e += IT) {
+        const int row = e / 30, c = e - 30 * row;
+        cp_async8(dst + (uint32_t)(c * F_LD + row) * 8, feat + r0 * 30 + e);
+    }
+}
+
+// GELU of two values (see the header for the erf approximation).
+__device__ __forceinline__ uint32_t gelu2_bf16(float2 z)
+{
+    constexpr float K1 = 0.79880562f;  // A / sqrt 2
+    constexpr float K3 = 0.03528185f;  // B / (2 sqrt 2)
+    const float2 z2 = __fmul2_rn(z, z);
+    const float2 u = __fmul2_rn(z, __ffma2_rn(z2, make_float2(K3, K3), make_float2(K1, K1)));
+    const __half2 hu = __floats2half2_rn(u.x, u.y);
+    uint32_t t;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(*reinterpret_cast<const uint32_t*>(&hu)));
+    const float2 th = __half22float2(*reinterpret_cast<const __half2*>(&t));
+    const float2 hz = __fmul2_rn(z, make_float2(0.5f, 0.5f));
+    const float2 g = __ffma2_rn(hz, th, hz);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(g.x, g.y);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Accumulator + bias -> GELU -> BF16 into H: this warp's 32 rows, 64 columns.
+__device__ __forceinline__ void epilogue_hidden(uint32_t tmem_row, int row, int col0, const float* __restrict__ bias,
+                                                uint8_t* sH)
+{
+#pragma unroll
+    for (int c0 = col0; c0 < col0 + 64; c0 += 16) {
+        float v[16];
+        tmem_ld16(tmem_row + (uint32_t)c0, v);
+        uint32_t w[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            w[i] = gelu2_bf16(make_float2(v[2 * i] + bias[c0 + 2 * i], v[2 * i + 1] + bias[c0 + 2 * i + 1]));
+        *reinterpret_cast<uint4*>(sH + canon(row, c0, 4096)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(sH + canon(row, c0 + 8, 4096)) = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+}
+
+__device__ __forceinline__ float raw_feature(double v, int c)
+{
+    return c < 6 ? (float)(v * (1.0 / 200e6)) : log10f((float)v + 1e10f);
+}
+
+struct InferArgs {
+    const double* feat;  // [n x 30]
+    int64_t n;
+    const float* nv;     // xm, xs, ym, ys, box lo, box hi, inverse Cholesky factor, d2 threshold
+    const __nv_bfloat16* W[4];
+    const float* b[4];
+    double* lp6;         // [n x 6]
+    uint8_t* in_region;  // [n] or null
+    int* err;
+};
+
+__global__ void __launch_bounds__(IT, 1) mlp_infer_kernel(InferArgs g)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sX = base + OFF_X;
+    uint8_t* sW1 = base + OFF_W1;
+    uint8_t* sW4 = base + OFF_W4;
+    uint8_t* sH = base + OFF_H;
+    float* snv = reinterpret_cast<float*>(base + OFF_NV);
+    const uint32_t uX = smem_u32(sX), uW1 = smem_u32(sW1), uW4 = smem_u32(sW4), uH = smem_u32(sH);
+    const uint32_t uWC = smem_u32(base + OFF_WC);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int64_t n_tiles = (g.n + 127) / 128;
+    if ((int64_t)blockIdx.x >= n_tiles) return;  // whole CTA, before any allocation
+    const int64_t my_tiles = (n_tiles - 1 - blockIdx.x) / gridDim.x + 1;
+    const int64_t Q = 8 * my_tiles;  // chunks of the W2/W3 stream
+    const uint32_t mb = smem_u32(&mbar);
+
+    if (warp == 0) {
+        tmem_alloc(smem_u32(&tmem_base), 256);
+        tmem_relinquish();
+    }
+    if (tid == 0) mbar_init(mb, 1);
+    // resident operands and maps
+    copy_canon(sW1, g.W[0], 256, 32, 512);
+    copy_canon(sW4, g.W[3], 16, 256, 4096);
+    for (int e = tid; e < NV_FLOATS; e += IT) snv[e] = g.nv[e];
+    float* sB = reinterpret_cast<float*>(base + OFF_B);
+    for (int e = tid; e < 3 * 256 + 16; e += IT) sB[e] = e < 768 ? g.b[e >> 8][e & 255] : g.b[3][e - 768];
+    const uint32_t uF = smem_u32(base + OFF_F);
+    const double* sF = reinterpret_cast<const double*>(base + OFF_F);
+    // group 0: the first tile's features and W2 chunk 0; group 1: W2 chunk 1
+    issue_features(uF, g.feat, (int64_t)blockIdx.x * 128, (int)min((int64_t)128, g.n - (int64_t)blockIdx.x * 128));
+    issue_chunk(uWC, g.W[1], g.W[2], 0);
+    cp_async_commit();
+    if (Q > 1) issue_chunk(uWC + WC_BYTES, g.W[1], g.W[2], 1);
+    cp_async_commit();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    // epilogue roles: TMEM lane group (rows) and column quarter of this warp
+    const int lg = warp & 3, cq = warp >> 2;
+    const int erow = 32 * lg + (tid & 31);
+    const uint32_t tmem_row = tmem + ((uint32_t)(32 * lg) << 16);
+    // input-map roles: row and quarter (8 of the 32 operand columns, a share of the Mahalanobis sum)
+    const int mrow = tid & 127, part = tid >> 7;
+    const float* xm = snv;
+    const float* xs = snv + NF;
+    const float* ym = snv + 2 * NF;
+    const float* ys = ym + NO;
+    const float* lo = snv + 2 * NF + 2 * NO;
+    const float* hi = lo + NF;
+    const float* Li = hi + NF;  // inverse of the Cholesky factor, lower triangle
+    const float d2_thr = Li[NF * NF];
+    float* sd2 = reinterpret_cast<float*>(base + OFF_D2);
+    const uint32_t id_h = idesc_bf16_f32(128, 256), id_o = idesc_bf16_f32(128, 16);
+    uint32_t phase = 0;
+    bool ok = true;
+    int64_t q = 0;
+
+    for (int64_t it = 0; it < my_tiles; ++it) {
+        const int64_t r0 = ((int64_t)blockIdx.x + it * gridDim.x) * 128;
+        const int valid = (int)min((int64_t)128, g.n - r0);
+        // 1. raw features, prefetched into the staging buffer (with the first W2
+        //    chunk for the first tile, with W2 chunk 2 of the previous tile after that)
+        cp_async_wait1();
+        __syncthreads();
+        bool inbox = true;
+        {
+            float z[NF];
+#pragma unroll
+            for (int c = 0; c < NF; ++c) {
+                z[c] = mrow < valid ? (raw_feature(sF[c * F_LD + mrow], c) - xm[c]) / xs[c] : 0.0f;
+                inbox = inbox && z[c] >= lo[c] && z[c] <= hi[c];
+            }
+            // this thread's share of |L^-1 z|^2: the rows i = part, part + 4, ...
+            float d2 = 0.0f;
+#pragma unroll
+            for (int i = 0; i < NF; ++i) {
+                if ((i & 3) != part) continue;
+                float w = 0.0f;
+#pragma unroll
+                for (int j = 0; j <= i; ++j) w = fmaf(Li[i * NF + j], z[j], w);
+                d2 = fmaf(w, w, d2);
+            }
+            sd2[part * 128 + mrow] = d2;
+            // operand columns 8 part .. 8 part + 7 of this row (the same expression as z)
+            float zc[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int k = 8 * part + i;
+                zc[i] = (k < NF && mrow < valid) ? (raw_feature(sF[k * F_LD + mrow], k) - xm[k]) / xs[k] : 0.0f;
+            }
+            uint32_t w4[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(zc[2 * i], zc[2 * i + 1]);
+                w4[i] = *reinterpret_cast<const uint32_t*>(&h);
+            }
+            *reinterpret_cast<uint4*>(sX + canon(mrow, 8 * part, 512)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (part == 0 && mrow < valid && g.in_region) {
+            const float d2 = (sd2[mrow] + sd2[128 + mrow]) + (sd2[256 + mrow] + sd2[384 + mrow]);
+            g.in_region[r0 + mrow] = (inbox && d2 <= d2_thr) ? 1 : 0;
+        }
+        // 2. layer 1: X [128 x 32] W1^T
+        if (tid == 0) {
+            tc_fence_after();
+            for (int s = 0; s < 2; ++s)
+                tc_mma_bf16(tmem, smem_desc(uX + s * 256, 128, 512), smem_desc(uW1 + s * 256, 128, 512), id_h,
+                            s ? 1u : 0u);
+            tc_commit(mb);
+        }
+        ok = mbar_wait_bounded(mb, phase, MBAR_WAIT_LIMIT);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        tc_fence_after();
+        epilogue_hidden(tmem_row, erow, 64 * cq, sB, sH);
+        // layers 2 and 3: H [128 x 256] W^T, W streamed in K-chunks of 64
+        for (int l = 1; l <= 2 && ok; ++l) {
+            for (int kc = 0; kc < 4; ++kc, ++q) {
+                cp_async_wait1();  // chunk q has landed (the newest group is chunk q + 1)
+                fence_async_smem();
+                tc_fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+                    const uint32_t ub = uWC + (uint32_t)(q & 1) * WC_BYTES;
+                    for (int s = 0; s < 4; ++s)
+                        tc_mma_bf16(tmem, smem_desc(uH + (kc * 4 + s) * 256, 128, 4096), smem_desc(ub + s * 256, 128, 1024),
+                                    id_h, (kc | s) ? 1u : 0u);
+                    tc_commit(mb);
+                }
+                ok = mbar_wait_bounded(mb, phase, MBAR_WAIT_LIMIT);
+                phase ^= 1u;
+                if (!__syncthreads_and(ok)) {
+                    ok = false;
+                    break;
+                }
+                // the buffer of chunk q is free again: fetch chunk q + 2 (and, with
+                // chunk 2 of this tile, the next tile's features: the staging
+                // buffer was read before the first barrier of this layer)
+                if (q + 2 < Q) issue_chunk(uWC + (uint32_t)(q & 1) * WC_BYTES, g.W[1], g.W[2], q + 2);
+                if (l == 1 && kc == 0 && it + 1 < my_tiles) {
+                    const int64_t rn = ((int64_t)blockIdx.x + (it + 1) * gridDim.x) * 128;
+                    issue_features(uF, g.feat, rn, (int)min((int64_t)128, g.n - rn));
+                }
+                cp_async_commit();
+            }
+            if (!ok) break;
+            tc_fence_after();
+            epilogue_hidden(tmem_row, erow, 64 * cq, sB + 256 * l, sH);
+        }
+        if (!ok) break;
+        // layer 4: H [128 x 256] W4^T, N = 16 (6 used)
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            for (int s = 0; s < 16; ++s)
+                tc_mma_bf16(tmem, smem_desc(uH + s * 256, 128, 4096), smem_desc(uW4 + s * 256, 128, 4096), id_o,
+                            s ? 1u : 0u);
+            tc_commit(mb);
+        }
+        ok = mbar_wait_bounded(mb, phase, MBAR_WAIT_LIMIT);
+        phase ^= 1u;
+        if (!__syncthreads_and(ok)) {
+            ok = false;
+            break;
+        }
+        tc_fence_after();
+        if (cq == 0) {  // warps 0-3: one row each per thread
+            float v[16];
+            tmem_ld16(tmem_row, v);
+            if (erow < valid) {
+#pragma unroll
+                for (int c = 0; c < NO; ++c)
+                    g.lp6[(r0 + erow) * NO + c] = (double)((v[c] + sB[768 + c]) * ys[c] + ym[c]);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();  // accumulator read and hidden buffer free before the next tile
+    }
+    cp_async_wait0();
+    if (!ok && tid == 0) {
+        atomicExch(g.err, 1);
+        // give the tensor core a last bounded chance to finish the phase that was
+        // given up on (phase was already toggled) before TMEM is freed
+        mbar_wait_bounded(mb, phase ^ 1u, MBAR_WAIT_LIMIT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+}  // namespace
+
+cudaError_t launch_mlp_infer(const double* feat, int64_t n, const float* nv, const __nv_bfloat16* const W[4],
+                             const float* const b[4], double* lp6, uint8_t* in_region, int* err, cudaStream_t s)
+{
+    static bool attr_set[64] = {};  // the attribute is per function and device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        e = cudaFuncSetAttribute(mlp_infer_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, INFER_SMEM);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    if (n <= 0) return cudaSuccess;
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tiles = (n + 127) / 128;
+    InferArgs g{};
+    g.feat = feat;
+    g.n = n;
+    g.nv = nv;
+    for (int l = 0; l < 4; ++l) {
+        g.W[l] = W[l];
+        g.b[l] = b[l];
+    }
+    g.lp6 = lp6;
+    g.in_region = in_region;
+    g.err = err;
+    mlp_infer_kernel<<<(unsigned)(tiles < sms ? tiles : sms), IT, INFER_SMEM, s>>>(g);
+    return cudaGetLastError();
+}
+
+}  // namespace ptadd

@@ -177,4 +177,10 @@ __device__ __forceinline__ void load_chunk(uint8_t* dst, const __nv_bfloat16* sr
 // dynamic shared memory (tc_gemm.cu).
 cudaError_t launch_tc_gemm(const GemmArgs& g, cudaStream_t s);
 
+// Fused surrogate inference (mlp_infer.cu): raw features [n x 30] -> sym(Lp)
+// [n x 6] in FP64 and the trust-region flags; nv = the FP32 maps (xm, xs, ym,
+// ys, box, Cholesky factor, threshold), W/b the BF16 weights and FP32 biases.
+cudaError_t launch_mlp_infer(const double* feat, int64_t n, const float* nv, const __nv_bfloat16* const W[4],
+                             const float* const b[4], double* lp6, uint8_t* in_region, int* err, cudaStream_t s);
+
 }  // namespace ptadd

@@ -136,3 +136,60 @@ def test_surrogate_fit_predict_and_trust_region():
     assert err < 0.1
     assert inr.mean() > 0.9  # in-distribution points: box of the training set, 99th percentile
     assert not inr_far.any()
+
+
+def _parse_state(blob):
+    """Surrogate state blob -> packed FP32 params and the FP64 maps."""
+    count = int(np.frombuffer(blob[:16], np.uint64)[1])
+    params = np.frombuffer(blob[16:16 + 4 * count], np.float32).astype(np.float64)
+    nv = np.frombuffer(blob[16 + 4 * count:], np.float64)
+    m = {"xm": nv[:30], "xs": nv[30:60], "ym": nv[60:66], "ys": nv[66:72], "lo": nv[72:102],
+         "hi": nv[102:132], "L": nv[132:1032].reshape(30, 30), "thr": nv[1032]}
+    return params, m
+
+
+def test_fused_inference_matches_oracle():
+    """The fused inference kernel (input map, trust region, four layers, output
+    map in one launch) against the FP64 oracle on the BF16-rounded weights and
+    standardised inputs.  50 001 points = 391 tiles of 128 (the last one
+    ragged), so every persistent CTA walks several tiles and the W2/W3 chunk
+    stream crosses tile boundaries."""
+    rng = np.random.default_rng(21)
+    n_fit, n = 4096, 50001
+    sig = rng.uniform(-200e6, 200e6, size=(n_fit, 6))
+    rho = 10 ** rng.uniform(11, 13, size=(n_fit, 24))
+    feat = np.hstack([sig, rho])
+    lp = np.tanh(sig / 1e8) * (np.log10(rho[:, :6]) - 10.0) * 50.0
+    # half from the training distribution (mostly inside the trust region), half from a wider one
+    h = n // 2
+    test = np.vstack([np.hstack([rng.uniform(-200e6, 200e6, size=(h, 6)), 10 ** rng.uniform(11, 13, size=(h, 24))]),
+                      np.hstack([rng.uniform(-220e6, 220e6, size=(n - h, 6)),
+                                 10 ** rng.uniform(10.8, 13.2, size=(n - h, 24))])])
+    perm = rng.permutation(n)
+    test = test[perm]
+    with ptadd.Context(MAT, ptadd.PTADD_FP64, 0) as c:
+        c.surrogate_fit(feat, lp, epochs=20, batch=256, lr=2e-3, seed=3)
+        pred, inr = c.surrogate_predict(test)
+        params, m = _parse_state(c.surrogate_get_state())
+    f32 = np.float32
+    f = np.empty((n, 30), f32)
+    f[:, :6] = (test[:, :6] * (1.0 / 200e6)).astype(f32)
+    f[:, 6:] = np.log10(test[:, 6:].astype(f32) + f32(1e10))
+    z = (f - m["xm"].astype(f32)) / m["xs"].astype(f32)
+    sel = np.concatenate([rng.choice(n - 128, size=2000, replace=False), np.arange(n - 97, n)])
+    yo = O.mlp_forward(DIMS, weights_bf16(params), bf16(z[sel]))
+    ref = yo * m["ys"] + m["ym"]
+    err = relfro(pred[sel], ref)
+    print("fused inference vs oracle: %.3e" % err)
+    assert err <= 2e-2
+    # trust region in FP64 on the host, away from the decision boundaries
+    z64 = z.astype(np.float64)
+    w = np.linalg.solve(m["L"], z64.T).T
+    d2 = np.sum(w * w, axis=1)
+    inbox = np.all((z64 >= m["lo"]) & (z64 <= m["hi"]), axis=1)
+    margin = np.minimum(np.min(z64 - m["lo"], axis=1), np.min(m["hi"] - z64, axis=1))
+    clear = (np.abs(d2 - m["thr"]) > 1e-3 * m["thr"]) & (np.abs(margin) > 1e-4)
+    host = inbox & (d2 <= m["thr"])
+    assert clear.mean() > 0.9
+    assert np.array_equal(inr[clear], host[clear])
+    assert 0.2 < host.mean() < 0.8  # both outcomes occur
