@@ -13,7 +13,8 @@ over the 12 slip systems by Dirichlet-type shares (normalised exponential
 scores of smooth fields), the marginals of the surrogate's training inputs.
 Each point needs one closure per load step.  Points inside the surrogate's
 trust region take the surrogate's answer; the others fall back to the mean
-of `--members` DD realisations (batched, one launch sequence per load step).
+of `--members` DD realisations of `--loops` loops (4096 segments by default;
+batched, one launch sequence per load step).
 A random sample of (point, step) pairs is re-evaluated with
 `--check-members`-realisation DD ensembles to measure the sweep's error.
 `--eval-steps` runs an evenly spaced subset of the load steps and
@@ -73,11 +74,11 @@ def main(argv=None):
     p.add_argument("--state", required=True, help="fitted surrogate state (surrogate.py --save)")
     p.add_argument("--grid", type=int, default=16)
     p.add_argument("--load-steps", type=int, default=100)
-    p.add_argument("--members", type=int, default=8)
+    p.add_argument("--members", type=int, default=64)
     p.add_argument("--check", type=int, default=64)
     p.add_argument("--check-members", type=int, default=16)
-    p.add_argument("--loops", type=int, default=48)
-    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--loops", type=int, default=128)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--dt", type=float, default=5e-13)
     p.add_argument("--seed", type=int, default=1005)
     p.add_argument("--eval-steps", type=int, default=0,

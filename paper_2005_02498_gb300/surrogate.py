@@ -5,13 +5,17 @@
 A closure input is (sigma, mobile and sessile line density per slip
 system); a DD closure at that input is the burst-averaged plastic distortion
 rate sym(R^Lp) (Voigt order) of a realisation of `--loops` glide loops drawn
-to follow those densities (`workloads.realisation_for_densities`), computed
+to follow those densities (`workloads.realisation_for_densities`, stratified:
+class counts, radii and line senses balanced, total density exact), computed
 by batched mixed-precision DD bursts (`--dt`, `--steps`).  Realisations with
 the same input differ, so a single closure is noisy: the network is trained
 on one realisation per training point (it regresses to the conditional
-mean) and judged on hold-out points against the mean of `--members`
-realisations; the spread of single realisations around those means is
-reported as the noise floor.  A subset is relabelled with plain FP64 DD.
+mean) and judged on `--eval` hold-out points against the mean of
+`--members` realisations.  The spread of single realisations around those
+means gives the noise floor of that reference, and the model error with the
+floor removed is reported beside the raw figure.  A subset is relabelled
+with plain FP64 DD.  `--save-data` / `--load-data` keep the labelled set, so
+training can be repeated without new DD work.
 Inference is timed on `--infer` points resampled from the training
 features, device-resident, and compared with the DD closures/s of the same
 closure definition.  Prints one JSON line.
@@ -54,7 +58,7 @@ def feature_points(rng, n, rho_min=2e12, rho_max=2e13, stress_max=200e6):
     return f
 
 
-def generate(ctx, feats, members, seed, steps, dt, n_loops=48, chunk=1024):
+def generate(ctx, feats, members, seed, steps, dt, n_loops=128, chunk=512, stratified=True):
     """DD closures at the given feature points: the mean of sym(R^Lp) over
     `members` realisations drawn for each point (realisation_for_densities)."""
     rng = np.random.default_rng(seed)
@@ -65,7 +69,8 @@ def generate(ctx, feats, members, seed, steps, dt, n_loops=48, chunk=1024):
     pairs = 0
     for s0 in range(0, len(jobs), chunk):
         part = jobs[s0:s0 + chunk]
-        nets = [W.realisation_for_densities(rng, feats[i, :6], feats[i, 6:18], feats[i, 18:], n_loops=n_loops)
+        nets = [W.realisation_for_densities(rng, feats[i, :6], feats[i, 6:18], feats[i, 18:], n_loops=n_loops,
+                                            stratified=stratified)
                 for i, _ in part]
         lab = label(ctx, W.batch_from_networks(nets), steps, dt)
         pairs += ctx.batch_info()["pairs_per_step"] * steps
@@ -82,7 +87,7 @@ def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--samples", type=int, default=20000)
     p.add_argument("--holdout", type=float, default=0.1)
-    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--dt", type=float, default=5e-13)
     p.add_argument("--seed", type=int, default=1004)
     p.add_argument("--epochs", type=int, default=200, help="maximum epochs")
@@ -92,9 +97,11 @@ def main(argv=None):
     p.add_argument("--save-data", default=None, help="write the features and labels (npz)")
     p.add_argument("--batch", type=int, default=512)
     p.add_argument("--lr", type=float, default=1e-3)
-    p.add_argument("--fp64-check", type=int, default=128, help="hold-out points relabelled with FP64 DD")
+    p.add_argument("--fp64-check", type=int, default=32, help="hold-out points relabelled with FP64 DD")
     p.add_argument("--members", type=int, default=16, help="realisations per hold-out ensemble mean")
-    p.add_argument("--loops", type=int, default=48, help="loops per realisation")
+    p.add_argument("--loops", type=int, default=128, help="loops per realisation")
+    p.add_argument("--eval", type=int, default=400, help="hold-out points judged against ensemble means")
+    p.add_argument("--load-data", default=None, help="reuse a labelled set written by --save-data")
     p.add_argument("--infer", type=int, default=1 << 20)
     p.add_argument("--device", type=int, default=0)
     p.add_argument("--save", default=None, help="write the fitted surrogate state to this file")
@@ -106,14 +113,22 @@ def main(argv=None):
     rng = np.random.default_rng(a.seed)
     ntr = int(round(a.samples * (1 - a.holdout)))
     X = feature_points(rng, a.samples)
+    nev = min(a.eval, a.samples - ntr)
     with ptadd.Context(mat, ptadd.PTADD_MIXED, a.device) as ctx:
-        # training labels: one realisation per point; hold-out labels: ensemble means
-        Ytr, t_gen, pairs = generate(ctx, X[:ntr], 1, a.seed + 1, a.steps, a.dt, a.loops)
-        Yho, t_ho, _ = generate(ctx, X[ntr:], a.members, a.seed + 2, a.steps, a.dt, a.loops)
-        out.update({"dd_label_s": t_gen, "dd_closures_per_s": ntr / t_gen, "dd_pair_evals_per_s": pairs / t_gen,
-                    "holdout_label_s": t_ho})
-        # noise floor: single-realisation labels around the hold-out ensemble means
-        Y1, _, _ = generate(ctx, X[ntr:], 1, a.seed + 3, a.steps, a.dt, a.loops)
+        if a.load_data:
+            d = np.load(a.load_data)
+            X, Ytr, Yho, Y1 = d["X"], d["Ytr"], d["Yho"], d["Y1"]
+            assert X.shape[0] == a.samples and Yho.shape[0] == nev, "labelled set does not match the arguments"
+            out["labels_from"] = a.load_data
+            out["dd_closures_per_s"] = float(d["dd_closures_per_s"])
+        else:
+            # training labels: one realisation per point; the judged hold-out
+            # points: ensemble means and one independent single realisation
+            Ytr, t_gen, pairs = generate(ctx, X[:ntr], 1, a.seed + 1, a.steps, a.dt, a.loops)
+            Yho, t_ho, _ = generate(ctx, X[ntr:ntr + nev], a.members, a.seed + 2, a.steps, a.dt, a.loops)
+            out.update({"dd_label_s": t_gen, "dd_closures_per_s": ntr / t_gen, "dd_pair_evals_per_s": pairs / t_gen,
+                        "holdout_label_s": t_ho})
+            Y1, _, _ = generate(ctx, X[ntr:ntr + nev], 1, a.seed + 3, a.steps, a.dt, a.loops)
         # early stopping: the labels are single noisy realisations, so the
         # network is trained in rounds and the round with the lowest error on
         # a validation split (also single realisations) is kept
@@ -137,21 +152,25 @@ def main(argv=None):
         out["train_s"] = time.perf_counter() - t0
         out["training_curve_epoch_loss_valerr"] = curve
         out["best_val_rel_err"] = best_err
-        pred, inr = ctx.surrogate_predict(X[ntr:])
+        pred, inr = ctx.surrogate_predict(X[ntr:ntr + nev])
+        err = relerr(pred, Yho)
+        single = relerr(Y1, Yho) * np.sqrt(a.members / (a.members + 1.0))  # one realisation vs the true mean
+        floor = single / np.sqrt(a.members)
         out["holdout"] = {
-            "n": int(Yho.shape[0]),
-            "rel_err_vs_ensemble_mean": relerr(pred, Yho),
+            "n": int(nev),
+            "rel_err_vs_ensemble_mean": err,
             "rel_err_in_region": relerr(pred[inr], Yho[inr]) if inr.any() else None,
             "in_region_frac": float(inr.mean()),
-            "single_realisation_rel_err_vs_ensemble_mean": relerr(Y1, Yho),
-            "ensemble_mean_noise_floor": relerr(Y1, Yho) / np.sqrt(a.members),
+            "single_realisation_rel_spread": single,
+            "ensemble_mean_noise_floor": floor,
+            "rel_err_noise_corrected": float(np.sqrt(max(0.0, err * err - floor * floor))),
             "mean_predictor_rel_err": relerr(np.broadcast_to(Ytr.mean(0), Yho.shape), Yho),
             "label_norm_median": float(np.median(np.linalg.norm(Yho, axis=1))),
         }
         train_pred, _ = ctx.surrogate_predict(X[:nfit])
         out["train_rel_err_vs_single_labels"] = relerr(train_pred, Ytr[:nfit])
         if a.save_data:
-            np.savez_compressed(a.save_data, X=X, Ytr=Ytr, Yho=Yho, Y1=Y1)
+            np.savez_compressed(a.save_data, X=X, Ytr=Ytr, Yho=Yho, Y1=Y1, dd_closures_per_s=out["dd_closures_per_s"])
         if a.save:
             with open(a.save, "wb") as fh:
                 fh.write(ctx.surrogate_get_state())
@@ -187,7 +206,7 @@ def main(argv=None):
             out["inference"] = None
 
     if a.fp64_check > 0:
-        k = min(a.fp64_check, a.samples - ntr)
+        k = min(a.fp64_check, nev)
         with ptadd.Context(mat, ptadd.PTADD_FP64, a.device) as ctx64:
             y64, t64, _ = generate(ctx64, X[ntr:ntr + k], 1, a.seed + 3, a.steps, a.dt, a.loops)
         out["fp64_check"] = {"n": k, "mixed_vs_fp64_rel_err": relerr(Y1[:k], y64),

@@ -344,13 +344,16 @@ def closure_ensemble(seed, R, loops_min=16, loops_max=64, density_min=8.0, densi
     return batch, closure_features(batch)
 
 
-def _loops_with_systems(rng, systems, edge, nodes_per_loop, r_min=0.05 * MICRON, r_max=0.2 * MICRON):
+def _loops_with_systems(rng, systems, edge, nodes_per_loop, r_min=0.05 * MICRON, r_max=0.2 * MICRON,
+                        radius=None, sense=None):
     bh, nh = fcc_slip_systems()
     n = len(systems)
-    radius = rng.uniform(r_min, r_max, size=n)
+    if radius is None:
+        radius = rng.uniform(r_min, r_max, size=n)
     centre = rng.uniform(0.0, edge, size=(n, 3))
     phi0 = rng.uniform(0.0, 2.0 * math.pi, size=n)
-    sense = rng.choice(np.array([-1.0, 1.0]), size=n)
+    if sense is None:
+        sense = rng.choice(np.array([-1.0, 1.0]), size=n)
     e1 = bh[systems]
     nrm = nh[systems]
     e2 = np.cross(nrm, e1)
@@ -364,20 +367,54 @@ def _loops_with_systems(rng, systems, edge, nodes_per_loop, r_min=0.05 * MICRON,
 
 
 def realisation_for_densities(rng, sig6, rho_m, rho_s, n_loops=32, nodes_per_loop=32,
-                              r_min=0.05 * MICRON, r_max=0.2 * MICRON):
+                              r_min=0.05 * MICRON, r_max=0.2 * MICRON, stratified=False):
     """One realisation whose mobile/sessile line densities per slip system
-    follow rho_m[12], rho_s[12] (1/m^2) on average: n_loops loops split over
-    the 24 (system, mobile/sessile) classes in proportion to their density,
-    the cube volume set so that the total density matches."""
+    follow rho_m[12], rho_s[12] (1/m^2): n_loops loops split over the 24
+    (system, mobile/sessile) classes in proportion to their density.
+
+    stratified=False: classes drawn independently per loop, radii ~
+    U(r_min, r_max), line sense +-1, cube volume from the mean loop perimeter
+    (densities match on average).
+    stratified=True: class counts are floor or ceil of n_loops x share
+    (systematic sampling of the remainders), radii are stratified over
+    (r_min, r_max) within each class, line senses are balanced within each
+    class, and the volume is set from the drawn loops' total length, so the
+    total density matches exactly and each class's within one loop."""
     dens = np.concatenate([np.asarray(rho_m, float), np.asarray(rho_s, float)])
     tot = dens.sum()
     p = dens / tot if tot > 0 else np.full(24, 1.0 / 24)
-    cls = rng.choice(24, size=n_loops, p=p)
+    radius = sense = None
+    if not stratified:
+        cls = rng.choice(24, size=n_loops, p=p)
+    else:
+        e = n_loops * p
+        counts = np.floor(e).astype(np.int64)
+        extra = n_loops - int(counts.sum())
+        if extra > 0:
+            picks = np.searchsorted(np.cumsum(e - counts), rng.uniform() + np.arange(extra), side="right")
+            counts += np.bincount(np.minimum(picks, 23), minlength=24)
+        cls = np.repeat(np.arange(24), counts)
+        radius = np.empty(cls.size)
+        sense = np.empty(cls.size)
+        for c in range(24):
+            idx = np.flatnonzero(cls == c)
+            k = idx.size
+            if k == 0:
+                continue
+            radius[idx] = r_min + (r_max - r_min) * (rng.permutation(k) + rng.uniform(size=k)) / k
+            sg = np.where(np.arange(k) < k // 2, 1.0, -1.0)
+            if k % 2:
+                sg[-1] = rng.choice(np.array([-1.0, 1.0]))
+            sense[idx] = rng.permutation(sg)
     systems = cls % 12
     xyz_tmp_edge = 1.0 * MICRON
-    mean_perim = nodes_per_loop * 2 * (0.5 * (r_min + r_max)) * math.sin(math.pi / nodes_per_loop)
-    volume = n_loops * mean_perim / tot if tot > 0 else xyz_tmp_edge ** 3
+    chord = 2.0 * math.sin(math.pi / nodes_per_loop) * nodes_per_loop
+    if stratified:
+        length = chord * radius.sum()
+    else:
+        length = n_loops * chord * 0.5 * (r_min + r_max)
+    volume = length / tot if tot > 0 else xyz_tmp_edge ** 3
     edge = volume ** (1.0 / 3.0)
-    xyz, off, bv, nv = _loops_with_systems(rng, systems, edge, nodes_per_loop, r_min, r_max)
+    xyz, off, bv, nv = _loops_with_systems(rng, systems, edge, nodes_per_loop, r_min, r_max, radius, sense)
     pin = np.repeat((cls >= 12).astype(np.uint8), nodes_per_loop)
     return Network(xyz, off, bv, nv, pin, edge ** 3, np.asarray(sig6, float).copy())
