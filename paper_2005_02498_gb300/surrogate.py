@@ -13,7 +13,10 @@ on one realisation per training point (it regresses to the conditional
 mean) and judged on `--eval` hold-out points against the mean of
 `--members` realisations.  The spread of single realisations around those
 means gives the noise floor of that reference, and the model error with the
-floor removed is reported beside the raw figure.  A subset is relabelled
+floor removed is reported beside the raw figure.  Training uses every
+labelled sample in its 24 cube-rotated forms (`cubic_images`: the closure
+map is equivariant under the rotations of the cube, which permute the FCC
+slip systems), unless `--no-augment`.  A subset is relabelled
 with plain FP64 DD.  `--save-data` / `--load-data` keep the labelled set, so
 training can be repeated without new DD work.
 Inference is timed on `--infer` points resampled from the training
@@ -79,6 +82,57 @@ def generate(ctx, feats, members, seed, steps, dt, n_loops=128, chunk=512, strat
     return acc / members, time.perf_counter() - t0, pairs
 
 
+def cubic_rotations():
+    """The 24 proper rotations of the cube (signed permutation matrices,
+    det +1) and, for each, the permutation of the 12 FCC slip systems it
+    induces: Q b_s = +-b_perm[s], Q n_s = +-n_perm[s]."""
+    import itertools
+    bh, nh = W.fcc_slip_systems()
+    rots, perms = [], []
+    for p in itertools.permutations(range(3)):
+        for signs in itertools.product((-1.0, 1.0), repeat=3):
+            Q = np.zeros((3, 3))
+            for i in range(3):
+                Q[i, p[i]] = signs[i]
+            if np.linalg.det(Q) < 0:
+                continue
+            qb, qn = bh @ Q.T, nh @ Q.T
+            perm = np.argmax(np.abs(qb @ bh.T) * np.abs(qn @ nh.T), axis=1)
+            rots.append(Q)
+            perms.append(perm)
+    return np.array(rots), np.array(perms)
+
+
+def _voigt_rotate(v6, Q):
+    """Voigt (xx, yy, zz, yz, xz, xy) symmetric tensors [n, 6] -> Q T Q^T."""
+    T = np.zeros((v6.shape[0], 3, 3))
+    T[:, 0, 0], T[:, 1, 1], T[:, 2, 2] = v6[:, 0], v6[:, 1], v6[:, 2]
+    T[:, 1, 2] = T[:, 2, 1] = v6[:, 3]
+    T[:, 0, 2] = T[:, 2, 0] = v6[:, 4]
+    T[:, 0, 1] = T[:, 1, 0] = v6[:, 5]
+    R = np.einsum("ij,njk,lk->nil", Q, T, Q)
+    return np.stack([R[:, 0, 0], R[:, 1, 1], R[:, 2, 2], R[:, 1, 2], R[:, 0, 2], R[:, 0, 1]], axis=1)
+
+
+def cubic_images(X, Y):
+    """All 24 rotated copies of closure samples.  A rotation Q of the cube
+    maps the FCC slip systems onto themselves, so a realisation drawn for
+    (sigma, rho) and rotated is a realisation for (Q sigma Q^T, permuted rho)
+    from the same input distribution (isotropic elasticity, stratified loops
+    with balanced line senses in a cube), and its averaged rate is
+    Q Lp Q^T.  Returns ([24 n, 30], [24 n, 6])."""
+    rots, perms = cubic_rotations()
+    xs, ys = [], []
+    for Q, perm in zip(rots, perms):
+        x = np.empty_like(X)
+        x[:, :6] = _voigt_rotate(X[:, :6], Q)
+        for off in (6, 18):
+            x[:, off + perm] = X[:, off:off + 12]
+        xs.append(x)
+        ys.append(_voigt_rotate(Y, Q))
+    return np.concatenate(xs), np.concatenate(ys)
+
+
 def relerr(pred, ref):
     return float(np.linalg.norm(pred - ref) / np.linalg.norm(ref))
 
@@ -90,9 +144,12 @@ def main(argv=None):
     p.add_argument("--steps", type=int, default=100)
     p.add_argument("--dt", type=float, default=5e-13)
     p.add_argument("--seed", type=int, default=1004)
-    p.add_argument("--epochs", type=int, default=200, help="maximum epochs")
-    p.add_argument("--round-epochs", type=int, default=5)
-    p.add_argument("--patience", type=int, default=4)
+    p.add_argument("--epochs", type=int, default=60, help="maximum epochs")
+    p.add_argument("--round-epochs", type=int, default=1)
+    p.add_argument("--patience", type=int, default=3)
+    p.add_argument("--lr-drops", type=int, default=2, help="learning-rate cuts (x0.3) on a validation plateau")
+    p.add_argument("--no-augment", dest="augment", action="store_false",
+                   help="train on the labelled samples only, without their 24 cube rotations")
     p.add_argument("--val-frac", type=float, default=0.1)
     p.add_argument("--save-data", default=None, help="write the features and labels (npz)")
     p.add_argument("--batch", type=int, default=512)
@@ -131,26 +188,37 @@ def main(argv=None):
             Y1, _, _ = generate(ctx, X[ntr:ntr + nev], 1, a.seed + 3, a.steps, a.dt, a.loops)
         # early stopping: the labels are single noisy realisations, so the
         # network is trained in rounds and the round with the lowest error on
-        # a validation split (also single realisations) is kept
+        # a validation split (also single realisations, never augmented) is
+        # kept; on a plateau the best state is restored and the learning rate
+        # cut, up to --lr-drops times
         nval = max(64, int(a.val_frac * ntr))
         nfit = ntr - nval
+        Xf, Yf = X[:nfit], Ytr[:nfit]
+        if a.augment:
+            Xf, Yf = cubic_images(Xf, Yf)
+            order = np.random.default_rng(a.seed + 11).permutation(Xf.shape[0])
+            Xf, Yf = Xf[order], Yf[order]
+        out["fit_samples"] = int(Xf.shape[0])
         t0 = time.perf_counter()
-        best, best_err, curve, bad = None, np.inf, [], 0
-        for rnd in range(max(1, a.epochs // a.round_epochs)):
-            losses = ctx.surrogate_fit(X[:nfit], Ytr[:nfit], epochs=a.round_epochs, batch=a.batch, lr=a.lr,
-                                       seed=a.seed + rnd)
+        best, best_err, curve, bad, lr, drops, ep = None, np.inf, [], 0, a.lr, 0, 0
+        while ep < a.epochs:
+            losses = ctx.surrogate_fit(Xf, Yf, epochs=a.round_epochs, batch=a.batch, lr=lr, seed=a.seed + ep)
+            ep += a.round_epochs
             pv, _ = ctx.surrogate_predict(X[nfit:ntr])
             e = relerr(pv, Ytr[nfit:ntr])
-            curve.append([(rnd + 1) * a.round_epochs, float(losses[-1]), e])
+            curve.append([ep, lr, float(losses[-1]), e])
             if e < best_err - 1e-4:
                 best, best_err, bad = ctx.surrogate_get_state(), e, 0
             else:
                 bad += 1
                 if bad >= a.patience:
-                    break
+                    if drops >= a.lr_drops:
+                        break
+                    ctx.surrogate_set_state(best)
+                    lr, drops, bad = lr * 0.3, drops + 1, 0
         ctx.surrogate_set_state(best)
         out["train_s"] = time.perf_counter() - t0
-        out["training_curve_epoch_loss_valerr"] = curve
+        out["training_curve_epoch_lr_loss_valerr"] = curve
         out["best_val_rel_err"] = best_err
         pred, inr = ctx.surrogate_predict(X[ntr:ntr + nev])
         err = relerr(pred, Yho)

@@ -46,3 +46,49 @@ def test_unstratified_realisation_is_unchanged_by_the_option():
     a = W.realisation_for_densities(np.random.default_rng(9), np.zeros(6), rm, rs, n_loops=32)
     b = W.realisation_for_densities(np.random.default_rng(9), np.zeros(6), rm, rs, n_loops=32, stratified=False)
     assert np.array_equal(a.xyz, b.xyz) and a.volume == b.volume
+
+
+def test_cubic_rotations_permute_the_slip_systems():
+    from paper_2005_02498_gb300.surrogate import _voigt_rotate, cubic_rotations
+    rots, perms = cubic_rotations()
+    assert len(rots) == 24
+    bh, nh = W.fcc_slip_systems()
+    rng = np.random.default_rng(4)
+    sig = rng.normal(size=(5, 6))
+    for Q, perm in zip(rots, perms):
+        assert sorted(perm) == list(range(12))
+        assert np.allclose(np.abs(np.einsum("sj,tj->st", bh @ Q.T, bh)[np.arange(12), perm]), 1.0)
+        # resolved shear stresses are permuted (up to sign): tau_perm[s](Q s Q^T) = +-tau_s(s)
+        rs = _voigt_rotate(sig, Q)
+        for v, w in zip(sig, rs):
+            S = np.array([[v[0], v[5], v[4]], [v[5], v[1], v[3]], [v[4], v[3], v[2]]])
+            T = np.array([[w[0], w[5], w[4]], [w[5], w[1], w[3]], [w[4], w[3], w[2]]])
+            tau = np.einsum("si,ij,sj->s", bh, S, nh)
+            tau_r = np.einsum("si,ij,sj->s", bh, T, nh)
+            assert np.allclose(np.abs(tau_r[perm]), np.abs(tau))
+
+
+def test_oracle_burst_is_equivariant_under_cube_rotations():
+    """The premise of the surrogate's data augmentation: a rotated
+    realisation under the rotated stress has the rotated averaged rate."""
+    import oracle as O
+    from paper_2005_02498_gb300.surrogate import cubic_rotations
+
+    mat = W.Material().as_tuple()
+    net = W.small_loop_network()
+    net.sig_app = np.array([30e6, -20e6, 50e6, 10e6, -15e6, 25e6])
+    ref = O.burst(mat, net, 3, 5e-13)
+    rots, _ = cubic_rotations()
+    for Q in rots[[1, 7, 13, 22]]:
+        r = net.copy()
+        r.xyz = net.xyz @ Q.T
+        r.burgers = net.burgers @ Q.T
+        r.normal = net.normal @ Q.T
+        s = net.sig_app
+        S = np.array([[s[0], s[5], s[4]], [s[5], s[1], s[3]], [s[4], s[3], s[2]]])
+        T = Q @ S @ Q.T
+        r.sig_app = np.array([T[0, 0], T[1, 1], T[2, 2], T[1, 2], T[0, 2], T[0, 1]])
+        got = O.burst(mat, r, 3, 5e-13)
+        want = Q @ ref["Lp_avg"] @ Q.T
+        assert np.linalg.norm(got["Lp_avg"] - want) <= 1e-9 * np.linalg.norm(want)
+        assert abs(got["rho_avg"] / ref["rho_avg"] - 1) < 1e-12
