@@ -122,15 +122,34 @@ def cubic_images(X, Y):
     with balanced line senses in a cube), and its averaged rate is
     Q Lp Q^T.  Returns ([24 n, 30], [24 n, 6])."""
     rots, perms = cubic_rotations()
-    xs, ys = [], []
-    for Q, perm in zip(rots, perms):
-        x = np.empty_like(X)
-        x[:, :6] = _voigt_rotate(X[:, :6], Q)
-        for off in (6, 18):
-            x[:, off + perm] = X[:, off:off + 12]
-        xs.append(x)
-        ys.append(_voigt_rotate(Y, Q))
+    xs = [rotate_inputs(X, Q, perm) for Q, perm in zip(rots, perms)]
+    ys = [_voigt_rotate(Y, Q) for Q in rots]
     return np.concatenate(xs), np.concatenate(ys)
+
+
+def rotate_inputs(X, Q, perm):
+    """Closure inputs [n, 30] under the cube rotation Q (slip-system permutation perm)."""
+    x = np.empty_like(X)
+    x[:, :6] = _voigt_rotate(X[:, :6], Q)
+    for off in (6, 18):
+        x[:, off + perm] = X[:, off:off + 12]
+    return x
+
+
+def predict_symmetrised(ctx, X):
+    """The surrogate averaged over the 24 cube rotations of each input: every
+    rotated input is predicted, the prediction rotated back (Q^T y Q), and
+    the 24 answers averaged.  Returns (lp6 [n, 6], in_region of the
+    unrotated inputs)."""
+    rots, perms = cubic_rotations()
+    n = X.shape[0]
+    xs = np.concatenate([rotate_inputs(X, Q, perm) for Q, perm in zip(rots, perms)])
+    ys, inr = ctx.surrogate_predict(xs)
+    acc = np.zeros((n, 6))
+    for g, Q in enumerate(rots):
+        acc += _voigt_rotate(ys[g * n:(g + 1) * n], Q.T)
+    g0 = int(np.argmax([np.array_equal(Q, np.eye(3)) for Q in rots]))  # the identity
+    return acc / len(rots), inr[g0 * n:(g0 + 1) * n]
 
 
 def relerr(pred, ref):
@@ -232,6 +251,7 @@ def main(argv=None):
             "single_realisation_rel_spread": single,
             "ensemble_mean_noise_floor": floor,
             "rel_err_noise_corrected": float(np.sqrt(max(0.0, err * err - floor * floor))),
+            "rel_err_symmetrised": relerr(predict_symmetrised(ctx, X[ntr:ntr + nev])[0], Yho),
             "mean_predictor_rel_err": relerr(np.broadcast_to(Ytr.mean(0), Yho.shape), Yho),
             "label_norm_median": float(np.median(np.linalg.norm(Yho, axis=1))),
         }
