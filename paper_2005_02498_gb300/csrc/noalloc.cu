@@ -28,7 +28,7 @@ constexpr int64_t NA_DOUBLES_PER_SEG = 3 + SRC_STRIDE + 6 * NA_CHUNKS + 3 + 3 + 
 // the eight regions (each pad < 32 doubles)
 constexpr int64_t NA_DOUBLES = NA_DOUBLES_PER_SEG * NA_MAX + NA_MAX + 512;
 
-__device__ __align__(256) double g_noalloc_scratch[NA_DOUBLES];
+static __device__ __align__(256) double g_noalloc_scratch[NA_DOUBLES];
 
 constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_na_mutex;
