@@ -4,16 +4,16 @@
 //
 //   C[M x N] = A[M x K] * B[N x K]^T     (A and B K-contiguous, "TN")
 //
-// One CTA of 128 threads owns a 128-row tile of C and all N <= 256 columns.
-// Per K-chunk of 64 the threads copy the A and B chunks from global memory
-// into shared memory in the canonical no-swizzle K-major layout of the
-// tensor core (8-row x 16-byte core matrices; core matrices adjacent in K are
-// 128 B apart (leading byte offset), 8-row groups are 1024 B apart (stride
-// byte offset)), fence them into the async proxy, and one elected thread
-// issues four 128xNx16 MMAs into the TMEM accumulator and commits them to an
-// mbarrier that every thread waits on (with an iteration limit) before the
-// chunk buffers are reused.  The epilogue reads the accumulator back with
-// tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = rows of the tile).
+// One CTA of 128 threads owns a 128-row x 64-column tile of C.  K runs in
+// chunks of 64 through two shared-memory stages: the chunks are copied with
+// cp.async into the canonical no-swizzle K-major layout of the tensor core
+// (8-row x 16-byte core matrices; core matrices adjacent in K are 128 B apart
+// (leading byte offset), 8-row groups are 1024 B apart (stride byte offset)),
+// two chunks ahead of the MMAs that read them.  One elected thread issues
+// four 128x64x16 MMAs per chunk into the TMEM accumulator and commits them to
+// an mbarrier that every thread waits on (with an iteration limit) before
+// the chunk's stage is refilled.  The epilogue reads the accumulator back
+// with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31 = rows of the tile).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -143,13 +143,12 @@ struct GemmArgs {
 };
 
 constexpr int GEMM_THREADS = 128;
-constexpr int GEMM_KC = 64;                   // K per chunk
-constexpr int GEMM_A_BYTES = 128 * GEMM_KC * 2;  // 16 KB
-constexpr int GEMM_B_BYTES = 256 * GEMM_KC * 2;  // 32 KB (N <= 256)
-// a guard region after the operand buffers keeps every address a descriptor can
-// reach inside this CTA's shared memory
-constexpr int GEMM_GUARD = 64 * 1024;
-constexpr int GEMM_SMEM = GEMM_A_BYTES + GEMM_B_BYTES + GEMM_GUARD + 1024;  // + alignment slack
+constexpr int GEMM_KC = 64;                          // K per chunk
+constexpr int GEMM_NT = 64;                          // output columns per CTA
+constexpr int GEMM_A_BYTES = 128 * GEMM_KC * 2;      // 16 KB per stage
+constexpr int GEMM_B_BYTES = GEMM_NT * GEMM_KC * 2;  // 8 KB per stage
+constexpr int GEMM_STAGE = GEMM_A_BYTES + GEMM_B_BYTES;
+constexpr int GEMM_SMEM = 2 * GEMM_STAGE + 1024;     // two stages + alignment slack
 constexpr long long MBAR_WAIT_LIMIT = 4000000000LL;  // ~2 s of SM clocks
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
@@ -158,23 +157,31 @@ __device__ __forceinline__ float gelu_grad_f(float z)
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
 }
 
-// Copy a [rows x 64] K-chunk (columns k0..k0+63 of a K-contiguous matrix) into
-// the canonical layout at dst; rows >= row_lim or columns >= K read as zero.
-__device__ __forceinline__ void load_chunk(uint8_t* dst, const __nv_bfloat16* src, int64_t ld, int64_t row0,
-                                           int rows, int64_t row_lim, int k0, int K)
+// Asynchronous copy of a [rows x 64] K-chunk (columns k0..k0+63 of a
+// K-contiguous matrix, rows row0..row0+rows-1) into the canonical layout at
+// dst (shared-window address); rows >= row_lim or columns >= K are filled
+// with zeros (source size 0).  A warp covers 8 rows x 4 core-matrix columns:
+// 64 contiguous bytes per row in global memory, 128 contiguous bytes per 8
+// threads in shared memory.  rows is a multiple of 8.
+__device__ __forceinline__ void load_chunk_async(uint32_t dst, const __nv_bfloat16* src, int64_t ld, int64_t row0,
+                                                 int rows, int64_t row_lim, int k0, int K)
 {
     for (int v = threadIdx.x; v < rows * 8; v += GEMM_THREADS) {
-        const int r = v >> 3, kk = v & 7;
+        const int r = (v >> 6) * 8 + (v & 7), kk = (v >> 3) & 7;
         const int64_t gr = row0 + r;
         const int gk = k0 + 8 * kk;
-        uint4 val = make_uint4(0u, 0u, 0u, 0u);
-        if (gr < row_lim && gk < K) val = *reinterpret_cast<const uint4*>(src + gr * ld + gk);
-        *reinterpret_cast<uint4*>(dst + (r >> 3) * 1024 + kk * 128 + (r & 7) * 16) = val;
+        const bool in = gr < row_lim && gk < K;
+        const __nv_bfloat16* p = in ? src + gr * ld + gk : src;
+        const uint32_t bytes = in ? 16u : 0u;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst + (r >> 3) * 1024 + kk * 128 +
+                                                                          (r & 7) * 16),
+                     "l"(__cvta_generic_to_global(p)), "r"(bytes)
+                     : "memory");
     }
 }
 
-// Launch: ceil(M / 128) CTAs of GEMM_THREADS threads, GEMM_SMEM bytes of
-// dynamic shared memory (tc_gemm.cu).
+// Launch: ceil(M / 128) x ceil(N / GEMM_NT) CTAs of GEMM_THREADS threads,
+// GEMM_SMEM bytes of dynamic shared memory (tc_gemm.cu).
 cudaError_t launch_tc_gemm(const GemmArgs& g, cudaStream_t s);
 
 // Fused surrogate inference (mlp_infer.cu): raw features [n x 30] -> sym(Lp)

@@ -9,7 +9,8 @@ from paper_2005_02498_gb300 import ptadd
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("M,N,K", [(128, 16, 16), (200, 256, 256), (64, 32, 96), (1000, 48, 512), (37, 16, 32)])
+@pytest.mark.parametrize("M,N,K", [(128, 16, 16), (200, 256, 256), (64, 32, 96), (1000, 48, 512), (37, 16, 32),
+                                   (300, 112, 80), (128, 80, 64), (513, 256, 272)])
 def test_tc_gemm_matches_float64(M, N, K):
     rng = np.random.default_rng(M * 7 + N * 3 + K)
     A = ptadd.to_bf16_bits(rng.normal(size=(M, K)).astype(np.float32))
