@@ -69,6 +69,26 @@ def parse():
     return p.parse_args()
 
 
+def rank_seed(rank):
+    """Seed of the realisation rank `rank` runs (independent realisations: weak scaling)."""
+    return W.LARGE_LOOPS["seed"] + rank
+
+
+def max_over_ranks(x, dist, device):
+    """The maximum of a per-rank float over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, seconds):
+    """Units processed by all ranks per second of the slowest rank."""
+    return world * units_per_rank / seconds
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -231,7 +251,7 @@ def run_ours(args):
     ptadd.load()
     prec = ptadd.PTADD_FP64 if args.precision == "fp64" else ptadd.PTADD_MIXED
     mat = W.Material()
-    net = W.large_loop_network(seed=W.LARGE_LOOPS["seed"] + rank)
+    net = W.large_loop_network(seed=rank_seed(rank))
     dt = W.LARGE_LOOPS["dt"]
     stream = torch.cuda.Stream()  # a real stream shared by the library and the timing events
     torch.cuda.set_stream(stream)
@@ -272,12 +292,8 @@ def run_ours(args):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    elapsed_ms = sum(a.elapsed_time(b) for a, b in evs)
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = world * pairs_per_bench_step * args.steps / (elapsed_ms * 1e-3)
+    elapsed_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dist, "cuda")
+    value = whole_job_rate(pairs_per_bench_step * args.steps, world, elapsed_ms * 1e-3)
 
     # ---- plain FP64 DD on the same GPU and workload, for the ratio
     fp64_cmp = None
@@ -298,7 +314,8 @@ def run_ours(args):
         torch.cuda.synchronize()
         p64 = ctx.profile_read()
         ms64 = sum(a.elapsed_time(b) for a, b in evs64)
-        v64 = world * pairs_per_bench_step * args.fp64_steps / (ms64 * 1e-3)
+        ms64 = max_over_ranks(ms64, dist, "cuda")
+        v64 = whole_job_rate(pairs_per_bench_step * args.fp64_steps, world, ms64 * 1e-3)
         fp64_cmp = {"value": v64, "unit": "pair-evals/s", "steps": args.fp64_steps,
                     "ms_per_step": ms64 / args.fp64_steps, "speedup_of_mixed": value / v64,
                     "pair_kernel_tflops": FLOPS_PER_PAIR * p64["pair_evals"] / (p64["pair_ms"] * 1e-3) / 1e12}
@@ -320,12 +337,8 @@ def run_ours(args):
         t1 = time.perf_counter()
         if i > 0:  # the first round trip is a warm-up
             e2e_times.append(t1 - t0)
-    e2e_s = float(np.sum(e2e_times))
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * pairs_per_bench_step * len(e2e_times) / e2e_s
+    e2e_s = max_over_ranks(float(np.sum(e2e_times)), dist, "cuda")
+    e2e_value = whole_job_rate(pairs_per_bench_step * len(e2e_times), world, e2e_s)
     h2d = 3 * n * 8
     d2h = 3 * n * 8 + 10 * 8 + 4
 
