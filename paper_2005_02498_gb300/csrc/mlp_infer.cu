@@ -4,10 +4,11 @@
 // One CTA of 512 threads per SM walks 128-row tiles of the input.  Per tile:
 //   1. the tile's raw features arrive in a transposed shared-memory staging
 //      buffer (cp.async, issued while the previous tile was in its layers);
-//      four threads per row map it (sigma / 200 MPa, log10(rho + 1e10)),
-//      standardise it, evaluate the trust region (box, and the Mahalanobis
-//      distance |L^-1 z|^2 split over the four threads) and write one 8-column
-//      slice each of the BF16 row of the layer-1 operand;
+//      four threads per row each map and standardise 8 of its features
+//      (sigma / 200 MPa, log10(rho + 1e10)), write them as one 8-column slice
+//      of the BF16 row of the layer-1 operand and share them through shared
+//      memory; the trust region (box, and the Mahalanobis distance |L^-1 z|^2
+//      split over the four threads) follows;
 //   2. four tcgen05 MMA chains (BF16 x BF16 -> FP32 in one 256-column TMEM
 //      accumulator) with the hidden activations kept in shared memory: in
 //      every epilogue warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its rows),
@@ -57,7 +58,8 @@ constexpr int OFF_D2 = OFF_NV + ((NV_FLOATS * 4 + 15) / 16) * 16;  // [4][128] p
 constexpr int OFF_B = OFF_D2 + 4 * 128 * 4;                        // biases: 3 x 256 + 16
 constexpr int F_LD = 129;                                          // staging row pitch (doubles)
 constexpr int OFF_F = OFF_B + (3 * 256 + 16) * 4;                  // raw features [30][F_LD], transposed
-constexpr int INFER_SMEM = OFF_F + NF * F_LD * 8 + 1024;           // + alignment slack
+constexpr int OFF_Z = OFF_F + NF * F_LD * 8;                       // standardised features [30][128]
+constexpr int INFER_SMEM = OFF_Z + NF * 128 * 4;
 
 __device__ __forceinline__ uint32_t canon(int r, int k, int sbo)
 {
@@ -141,7 +143,8 @@ __device__ __forceinline__ void epilogue_hidden(uint32_t tmem_row, int row, int 
         uint32_t w[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-            w[i] = gelu2_bf16(make_float2(v[2 * i] + bias[c0 + 2 * i], v[2 * i + 1] + bias[c0 + 2 * i + 1]));
+            w[i] = gelu2_bf16(__fadd2_rn(make_float2(v[2 * i], v[2 * i + 1]),
+                                         *reinterpret_cast<const float2*>(bias + c0 + 2 * i)));
         *reinterpret_cast<uint4*>(sH + canon(row, c0, 4096)) = make_uint4(w[0], w[1], w[2], w[3]);
         *reinterpret_cast<uint4*>(sH + canon(row, c0 + 8, 4096)) = make_uint4(w[4], w[5], w[6], w[7]);
     }
@@ -165,10 +168,13 @@ struct InferArgs {
 
 __global__ void __launch_bounds__(IT, 1) mlp_infer_kernel(InferArgs g)
 {
-    extern __shared__ uint8_t smem_raw[];
+    // every region below starts at a multiple of 16 bytes, all the no-swizzle
+    // operand layouts need; pointers derived from the array itself keep the
+    // compiler's shared-memory address space (plain shared loads and stores)
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
-    uint8_t* base = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* base = smem_raw;
     uint8_t* sX = base + OFF_X;
     uint8_t* sW1 = base + OFF_W1;
     uint8_t* sW4 = base + OFF_W4;
@@ -221,6 +227,7 @@ __global__ void __launch_bounds__(IT, 1) mlp_infer_kernel(InferArgs g)
     const float* Li = hi + NF;  // inverse of the Cholesky factor, lower triangle
     const float d2_thr = Li[NF * NF];
     float* sd2 = reinterpret_cast<float*>(base + OFF_D2);
+    float* sZ = reinterpret_cast<float*>(base + OFF_Z);
     const uint32_t id_h = idesc_bf16_f32(128, 256), id_o = idesc_bf16_f32(128, 16);
     uint32_t phase = 0;
     bool ok = true;
@@ -233,15 +240,37 @@ __global__ void __launch_bounds__(IT, 1) mlp_infer_kernel(InferArgs g)
         //    chunk for the first tile, with W2 chunk 2 of the previous tile after that)
         cp_async_wait1();
         __syncthreads();
+        // features 8 part .. 8 part + 7 of this row: standardised once, kept
+        // for the other three threads of the row, and written as the BF16
+        // slice of the layer-1 operand
+        {
+            float zc[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int k = 8 * part + i;
+                zc[i] = (k < NF && mrow < valid) ? (raw_feature(sF[k * F_LD + mrow], k) - xm[k]) / xs[k] : 0.0f;
+                if (k < NF) sZ[k * 128 + mrow] = zc[i];
+            }
+            uint32_t w4[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const __nv_bfloat162 h = __floats2bfloat162_rn(zc[2 * i], zc[2 * i + 1]);
+                w4[i] = *reinterpret_cast<const uint32_t*>(&h);
+            }
+            *reinterpret_cast<uint4*>(sX + canon(mrow, 8 * part, 512)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+        }
+        __syncthreads();
+        // this thread's share of |L^-1 z|^2 (rows i = part, part + 4, ...);
+        // the box test once per row
         bool inbox = true;
         {
             float z[NF];
 #pragma unroll
-            for (int c = 0; c < NF; ++c) {
-                z[c] = mrow < valid ? (raw_feature(sF[c * F_LD + mrow], c) - xm[c]) / xs[c] : 0.0f;
-                inbox = inbox && z[c] >= lo[c] && z[c] <= hi[c];
+            for (int c = 0; c < NF; ++c) z[c] = sZ[c * 128 + mrow];
+            if (part == 0) {
+#pragma unroll
+                for (int c = 0; c < NF; ++c) inbox = inbox && z[c] >= lo[c] && z[c] <= hi[c];
             }
-            // this thread's share of |L^-1 z|^2: the rows i = part, part + 4, ...
             float d2 = 0.0f;
 #pragma unroll
             for (int i = 0; i < NF; ++i) {
@@ -252,20 +281,6 @@ __global__ void __launch_bounds__(IT, 1) mlp_infer_kernel(InferArgs g)
                 d2 = fmaf(w, w, d2);
             }
             sd2[part * 128 + mrow] = d2;
-            // operand columns 8 part .. 8 part + 7 of this row (the same expression as z)
-            float zc[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int k = 8 * part + i;
-                zc[i] = (k < NF && mrow < valid) ? (raw_feature(sF[k * F_LD + mrow], k) - xm[k]) / xs[k] : 0.0f;
-            }
-            uint32_t w4[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const __nv_bfloat162 h = __floats2bfloat162_rn(zc[2 * i], zc[2 * i + 1]);
-                w4[i] = *reinterpret_cast<const uint32_t*>(&h);
-            }
-            *reinterpret_cast<uint4*>(sX + canon(mrow, 8 * part, 512)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
         }
         fence_async_smem();
         tc_fence_before();
