@@ -86,16 +86,26 @@ def test_mixed_burst_rates_small_workload():
 
 def test_mixed_burst_rates_large_workload_against_fp64_gpu():
     """20 steps of the 32768-segment workload at dt = 5e-13 s (well
-    conditioned): mixed vs the FP64 GPU path (itself within 1e-11 of the
-    oracle on forces)."""
+    conditioned): mixed vs the FP64 GPU path on the averaged rates, and both
+    against the oracle on the forces at the positions reached after 20 steps."""
     net = W.large_loop_network()
     dt = 5e-13
     with ctx_for(net, ptadd.PTADD_FP64) as c:
         Lp64, rho64 = c.advance(20, dt)
+        x20 = c.get_nodes()
+        F64 = c.get_forces()
     with ctx_for(net, ptadd.PTADD_MIXED) as c:
         Lpm, rhom = c.advance(20, dt)
+        c.set_nodes(x20)
+        Fm = c.get_forces()
     assert relfro(Lpm, Lp64) <= 1e-2
     assert abs(rhom / rho64 - 1) <= 1e-4
+    # along the trajectory: both precisions' forces at the FP64 path's step-20
+    # positions against the oracle at the same positions (sampled nodes)
+    sel = np.sort(np.random.default_rng(21).choice(net.n_nodes, size=32, replace=False))
+    Fo = O.nodal_forces_subset(MAT, net, sel, xyz=x20)
+    assert relmax(F64[sel], Fo) <= 1e-11
+    assert relmax(Fm[sel], Fo) <= 1e-4
 
 
 def test_stated_dt_amplifies_any_perturbation():
