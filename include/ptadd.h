@@ -215,8 +215,8 @@ ptadd_status ptadd_batch_run(ptadd_ctx* ctx, int32_t R, const int64_t* node_off,
  * accumulation in tensor memory).  Host arrays: A and B hold BF16 bit
  * patterns (uint16), K contiguous; C is FP32 row-major.  N a multiple of 16
  * in [16, 256], K a multiple of 16.  Allocates its own device buffers; the
- * surrogate's kernels use the same GEMM tile.  Returns PTADD_ERR_TIMEOUT if a
- * bounded wait for the tensor core gave up. */
+ * surrogate's training uses the same GEMM kernel.  Returns PTADD_ERR_TIMEOUT
+ * if a bounded wait for the tensor core gave up. */
 ptadd_status ptadd_gemm_bf16(int device, int64_t M, int32_t N, int32_t K, const uint16_t* A, const uint16_t* B,
                              float* C);
 
@@ -255,7 +255,12 @@ ptadd_status ptadd_mlp_forward(ptadd_ctx* ctx, int64_t n, const float* xn, float
  * current weights (initialised from `seed` if none). */
 ptadd_status ptadd_surrogate_fit(ptadd_ctx* ctx, int64_t n, const double* feat, const double* lp6, int epochs,
                                  int batch, float lr, uint64_t seed, float* loss_per_epoch);
-/* Host arrays; in_region (or NULL) receives 1 inside the trust region. */
+/* Host arrays; in_region (or NULL) receives 1 inside the trust region.
+ * Prediction runs one fused kernel (input map, trust region, the four layers,
+ * output map).  Its GELU evaluates erf through tanh(x (A + B x^2)), a fit
+ * with |error| <= 2.8e-4, below the BF16 rounding of the activations; so its
+ * answers can differ from ptadd_mlp_forward (exact erf) in the last BF16
+ * bits. */
 ptadd_status ptadd_surrogate_predict(ptadd_ctx* ctx, int64_t n, const double* feat, double* lp6, uint8_t* in_region);
 /* Device arrays, enqueued on the context's stream without synchronising. */
 ptadd_status ptadd_surrogate_predict_dev(ptadd_ctx* ctx, int64_t n, const double* feat_dev, double* lp6_dev,
