@@ -100,7 +100,7 @@ def test_regularised_infinite_screw(r_over_a):
         assert np.max(np.abs(s - exp)) / scale < 1e-12
 
 
-def test_north_star_screw_expression_is_far_field_limit():
+def test_short_screw_expression_is_far_field_limit():
     """mu b r/(2 pi (r^2+a^2)) differs from the full form by a^2/(r^2+a^2)."""
     half = 0.5e10 * A
     x1, x2, bv = np.array([0, 0, -half]), np.array([0, 0, half]), np.array([0, 0, BB])
