@@ -12,8 +12,8 @@ log-uniformly distributed between 2e12 and 2e13 1/m^2 over the grid, split
 over the 12 slip systems by Dirichlet-type shares (normalised exponential
 scores of smooth fields), the marginals of the surrogate's training inputs.
 Each point needs one closure per load step.  Points inside the surrogate's
-trust region take the surrogate's answer (averaged over the 24 cube-rotated
-images of the point unless --no-symmetrise); the others fall back to the mean
+trust region take the surrogate's answer (averaged over the 48 symmetric
+images of the point, `surrogate.closure_symmetries`, unless --no-symmetrise); the others fall back to the mean
 of `--members` DD realisations of `--loops` loops (4096 segments by default;
 batched, one launch sequence per load step).
 A random sample of (point, step) pairs is re-evaluated with
@@ -32,7 +32,7 @@ import numpy as np
 
 from . import ptadd
 from . import workloads as W
-from .surrogate import _voigt_rotate, cubic_rotations, generate, rotate_inputs
+from .surrogate import closure_symmetries, generate, symmetrised_answers, symmetrised_inputs
 
 
 def smooth_field(rng, pts, n_modes=4, kmax=2):
@@ -87,7 +87,7 @@ def main(argv=None):
     p.add_argument("--max-fallback-s", type=float, default=600.0,
                    help="stop before the fallback DD work of a run is estimated to exceed this")
     p.add_argument("--no-symmetrise", dest="symmetrise", action="store_false",
-                   help="answer with the plain surrogate instead of its average over the 24 cube rotations")
+                   help="answer with the plain surrogate instead of its average over the 48 symmetric images")
     p.add_argument("--device", type=int, default=0)
     a = p.parse_args(argv)
 
@@ -106,9 +106,7 @@ def main(argv=None):
         ctx.surrogate_set_state(open(a.state, "rb").read())
         st = torch.cuda.Stream(device=a.device)
         ctx.set_stream(st.cuda_stream)
-        rots, perms = cubic_rotations()
-        g0 = int(np.argmax([np.array_equal(Q, np.eye(3)) for Q in rots]))
-        G = len(rots) if a.symmetrise else 1
+        G = len(closure_symmetries()) if a.symmetrise else 1
         feat_d = torch.empty((G * n, 30), dtype=torch.float64, device="cuda:%d" % a.device)
         lp_d = torch.empty((G * n, 6), dtype=torch.float64, device=feat_d.device)
         reg_d = torch.empty(G * n, dtype=torch.uint8, device=feat_d.device)
@@ -121,13 +119,13 @@ def main(argv=None):
             n_run += 1
             feats = np.hstack([S * (k / K), rho])
             t0 = time.perf_counter()
-            xs = np.concatenate([rotate_inputs(feats, Q, pm) for Q, pm in zip(rots, perms)]) if G > 1 else feats
+            xs = symmetrised_inputs(feats) if G > 1 else feats
             feat_d.copy_(torch.from_numpy(xs))
             ctx.surrogate_predict_dev(G * n, feat_d.data_ptr(), lp_d.data_ptr(), reg_d.data_ptr())
             st.synchronize()
             ys = lp_d.cpu().numpy()
             if G > 1:
-                lp = sum(_voigt_rotate(ys[g * n:(g + 1) * n], Q.T) for g, Q in enumerate(rots)) / G
+                lp, g0 = symmetrised_answers(ys, n)
                 inr = reg_d[g0 * n:(g0 + 1) * n].cpu().numpy().astype(bool)
             else:
                 lp = ys

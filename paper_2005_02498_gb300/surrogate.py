@@ -14,9 +14,10 @@ mean) and judged on `--eval` hold-out points against the mean of
 `--members` realisations.  The spread of single realisations around those
 means gives the noise floor of that reference, and the model error with the
 floor removed is reported beside the raw figure.  Training uses every
-labelled sample in its 24 cube-rotated forms (`cubic_images`: the closure
-map is equivariant under the rotations of the cube, which permute the FCC
-slip systems), unless `--no-augment`.  A subset is relabelled
+labelled sample in its 48 symmetric forms (`cubic_images`: the closure map
+is equivariant under the 24 rotations of the cube, which permute the FCC
+slip systems, and odd in the stress; see `closure_symmetries`), unless
+`--no-augment`.  A subset is relabelled
 with plain FP64 DD.  `--save-data` / `--load-data` keep the labelled set, so
 training can be repeated without new DD work.
 Inference is timed on `--infer` points resampled from the training
@@ -114,16 +115,37 @@ def _voigt_rotate(v6, Q):
     return np.stack([R[:, 0, 0], R[:, 1, 1], R[:, 2, 2], R[:, 1, 2], R[:, 0, 2], R[:, 0, 1]], axis=1)
 
 
-def cubic_images(X, Y):
-    """All 24 rotated copies of closure samples.  A rotation Q of the cube
-    maps the FCC slip systems onto themselves, so a realisation drawn for
-    (sigma, rho) and rotated is a realisation for (Q sigma Q^T, permuted rho)
-    from the same input distribution (isotropic elasticity, stratified loops
-    with balanced line senses in a cube), and its averaged rate is
-    Q Lp Q^T.  Returns ([24 n, 30], [24 n, 6])."""
+def closure_symmetries():
+    """The 48 exact symmetries of the closure map used here: the 24 cube
+    rotations Q (with their slip-system permutations), each with a stress sign
+    s = +-1.  Under (Q, s) the input maps to (s Q sigma Q^T, permuted
+    densities) and the averaged rate to s Q Lp Q^T.
+
+    Rotations: Q maps the FCC slip systems onto themselves, elasticity is
+    isotropic, and the stratified realisations (loops in a cube, balanced
+    line senses) and the input distribution are invariant.  Sign: negating
+    sigma together with every Burgers vector leaves every force and velocity
+    unchanged and negates Lp; negating a loop's Burgers vector is the same as
+    reversing its line sense, which the balanced senses make a symmetry of
+    the realisation distribution.  Returns a list of (Q, perm, s)."""
     rots, perms = cubic_rotations()
-    xs = [rotate_inputs(X, Q, perm) for Q, perm in zip(rots, perms)]
-    ys = [_voigt_rotate(Y, Q) for Q in rots]
+    return [(Q, perm, sg) for Q, perm in zip(rots, perms) for sg in (1.0, -1.0)]
+
+
+def image_inputs(X, Q, perm, sg=1.0):
+    """Closure inputs [n, 30] under the symmetry (Q, perm, sg)."""
+    x = rotate_inputs(X, Q, perm)
+    x[:, :6] *= sg
+    return x
+
+
+def cubic_images(X, Y):
+    """All 48 symmetric copies (closure_symmetries) of closure samples.
+    Returns ([48 n, 30], [48 n, 6])."""
+    xs, ys = [], []
+    for Q, perm, sg in closure_symmetries():
+        xs.append(image_inputs(X, Q, perm, sg))
+        ys.append(sg * _voigt_rotate(Y, Q))
     return np.concatenate(xs), np.concatenate(ys)
 
 
@@ -136,20 +158,30 @@ def rotate_inputs(X, Q, perm):
     return x
 
 
-def predict_symmetrised(ctx, X):
-    """The surrogate averaged over the 24 cube rotations of each input: every
-    rotated input is predicted, the prediction rotated back (Q^T y Q), and
-    the 24 answers averaged.  Returns (lp6 [n, 6], in_region of the
-    unrotated inputs)."""
-    rots, perms = cubic_rotations()
-    n = X.shape[0]
-    xs = np.concatenate([rotate_inputs(X, Q, perm) for Q, perm in zip(rots, perms)])
-    ys, inr = ctx.surrogate_predict(xs)
+def symmetrised_inputs(X):
+    """[48 n, 30]: the images of X under closure_symmetries, image-major."""
+    return np.concatenate([image_inputs(X, Q, perm, sg) for Q, perm, sg in closure_symmetries()])
+
+
+def symmetrised_answers(ys, n):
+    """Answers [48 n, 6] for symmetrised_inputs(X) -> their average mapped
+    back to X (s Q^T y Q per image), and the index of the identity image."""
+    syms = closure_symmetries()
     acc = np.zeros((n, 6))
-    for g, Q in enumerate(rots):
-        acc += _voigt_rotate(ys[g * n:(g + 1) * n], Q.T)
-    g0 = int(np.argmax([np.array_equal(Q, np.eye(3)) for Q in rots]))  # the identity
-    return acc / len(rots), inr[g0 * n:(g0 + 1) * n]
+    for g, (Q, _, sg) in enumerate(syms):
+        acc += sg * _voigt_rotate(ys[g * n:(g + 1) * n], Q.T)
+    g0 = next(g for g, (Q, _, sg) in enumerate(syms) if sg > 0 and np.array_equal(Q, np.eye(3)))
+    return acc / len(syms), g0
+
+
+def predict_symmetrised(ctx, X):
+    """The surrogate averaged over the 48 symmetric images of each input (an
+    exactly symmetric answer; in particular odd in sigma, so zero at zero
+    stress).  Returns (lp6 [n, 6], in_region of the inputs themselves)."""
+    n = X.shape[0]
+    ys, inr = ctx.surrogate_predict(symmetrised_inputs(X))
+    lp, g0 = symmetrised_answers(ys, n)
+    return lp, inr[g0 * n:(g0 + 1) * n]
 
 
 def relerr(pred, ref):
@@ -168,7 +200,7 @@ def main(argv=None):
     p.add_argument("--patience", type=int, default=3)
     p.add_argument("--lr-drops", type=int, default=2, help="learning-rate cuts (x0.3) on a validation plateau")
     p.add_argument("--no-augment", dest="augment", action="store_false",
-                   help="train on the labelled samples only, without their 24 cube rotations")
+                   help="train on the labelled samples only, without their 48 symmetric images")
     p.add_argument("--val-frac", type=float, default=0.1)
     p.add_argument("--save-data", default=None, help="write the features and labels (npz)")
     p.add_argument("--batch", type=int, default=512)

@@ -92,3 +92,39 @@ def test_oracle_burst_is_equivariant_under_cube_rotations():
         want = Q @ ref["Lp_avg"] @ Q.T
         assert np.linalg.norm(got["Lp_avg"] - want) <= 1e-9 * np.linalg.norm(want)
         assert abs(got["rho_avg"] / ref["rho_avg"] - 1) < 1e-12
+
+
+def test_oracle_burst_is_odd_under_stress_and_burgers_flip():
+    """The premise of the sign symmetry: negating the applied stress and
+    every Burgers vector leaves the motion unchanged and negates the averaged
+    rate (the balanced line senses make a Burgers flip a symmetry of the
+    realisations)."""
+    import oracle as O
+
+    mat = W.Material().as_tuple()
+    net = W.small_loop_network()
+    net.sig_app = np.array([30e6, -20e6, 50e6, 10e6, -15e6, 25e6])
+    ref = O.burst(mat, net, 3, 5e-13)
+    f = net.copy()
+    f.burgers = -net.burgers
+    f.sig_app = -net.sig_app
+    got = O.burst(mat, f, 3, 5e-13)
+    assert np.linalg.norm(got["Lp_avg"] + ref["Lp_avg"]) <= 1e-12 * np.linalg.norm(ref["Lp_avg"])
+    assert np.array_equal(got["xyz"], ref["xyz"])
+
+
+def test_symmetric_images_map_back_to_their_source():
+    from paper_2005_02498_gb300.surrogate import (closure_symmetries, cubic_images, symmetrised_answers,
+                                                  symmetrised_inputs)
+    rng = np.random.default_rng(6)
+    X = np.hstack([rng.uniform(-2e8, 2e8, size=(7, 6)), 10 ** rng.uniform(12, 13, size=(7, 24))])
+    Y = rng.normal(size=(7, 6))
+    xs, ys = cubic_images(X, Y)
+    assert len(closure_symmetries()) == 48 and xs.shape == (48 * 7, 30)
+    assert np.array_equal(xs, symmetrised_inputs(X))
+    back, g0 = symmetrised_answers(ys, 7)
+    assert np.allclose(back, Y, rtol=1e-13, atol=1e-13)
+    assert np.array_equal(xs[g0 * 7:(g0 + 1) * 7], X)
+    # a constant answer (even in the stress) averages to zero: the symmetrised
+    # surrogate is odd in sigma
+    assert np.allclose(symmetrised_answers(np.ones((48 * 7, 6)), 7)[0], 0.0, atol=1e-15)
