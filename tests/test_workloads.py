@@ -128,3 +128,29 @@ def test_symmetric_images_map_back_to_their_source():
     # a constant answer (even in the stress) averages to zero: the symmetrised
     # surrogate is odd in sigma
     assert np.allclose(symmetrised_answers(np.ones((48 * 7, 6)), 7)[0], 0.0, atol=1e-15)
+
+
+def test_closure_input_generators_follow_their_recipes():
+    from paper_2005_02498_gb300.closure_sweep import material_points
+    from paper_2005_02498_gb300.surrogate import feature_points
+
+    f = feature_points(np.random.default_rng(3), 2000)
+    assert f.shape == (2000, 30)
+    assert np.all(np.abs(f[:, :6]) <= 200e6)
+    for off in (6, 18):
+        tot = f[:, off:off + 12].sum(1)
+        assert np.all(f[:, off:off + 12] >= 0)
+        assert tot.min() >= 2e12 * (1 - 1e-12) and tot.max() <= 2e13 * (1 + 1e-12)
+        # log-uniform totals: the median of log10 sits mid-range
+        assert abs(np.median(np.log10(tot)) - np.log10(2e12 * np.sqrt(10))) < 0.05
+
+    pts, S, rho = material_points(5, 8)
+    assert pts.shape == (512, 3) and S.shape == (512, 6) and rho.shape == (512, 24)
+    assert np.allclose(np.max(np.abs(S), axis=0), 200e6)  # every component scaled to 200 MPa
+    for off in (0, 12):
+        tot = rho[:, off:off + 12].sum(1)
+        assert np.all(rho[:, off:off + 12] > 0)
+        # rank-uniform log10 totals between the bounds (the training marginals)
+        lg = np.sort(np.log10(tot))
+        u = (np.arange(lg.size) + 0.5) / lg.size
+        assert np.allclose(lg, np.log10(2e12) + u * (np.log10(2e13) - np.log10(2e12)))
