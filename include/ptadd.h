@@ -34,8 +34,12 @@
  *     pointers ("_dev" calls) must stay valid until the call's work on the
  *     context's stream has completed.
  *   - A context is not thread-safe; use one context per host thread.
- *   - All device memory a context needs is allocated by ptadd_create /
- *     ptadd_set_network / ptadd_batch_run and freed by ptadd_destroy.
+ *   - All device memory a context needs is allocated by the calls that
+ *     create it or load data into it (ptadd_create, ptadd_set_network,
+ *     ptadd_batch_set / ptadd_batch_run, the ptadd_mlp_* and
+ *     ptadd_surrogate_* calls) and freed by ptadd_destroy.  ptadd_gemm_bf16
+ *     allocates and frees its own buffers; ptadd_forces_noalloc allocates
+ *     nothing.
  */
 #ifndef PTADD_H
 #define PTADD_H
