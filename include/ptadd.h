@@ -270,6 +270,42 @@ ptadd_status ptadd_surrogate_predict(ptadd_ctx* ctx, int64_t n, const double* fe
 ptadd_status ptadd_surrogate_predict_dev(ptadd_ctx* ctx, int64_t n, const double* feat_dev, double* lp6_dev,
                                          uint8_t* in_region_dev);
 
+/* Closure sweep: one closure per point of a mesoscale load path (the PTA
+ * closure of Sec. 3 asked for at many material points).  Per point i:
+ * sig6[6i..] (Pa, Voigt order) and rho24[24i..] (12 mobile then 12 sessile
+ * line densities per FCC slip system, 1/m^2, systems in the order of
+ * ptadd_closure_realisation).  Points inside the fitted surrogate's trust
+ * region take its answer; the others fall back to DD: the mean of sym(R^Lp)
+ * (Eq. 2.5, Voigt order) over `ens` realisations from
+ * ptadd_closure_realisation (segments/32 loops; realisation q of the sweep
+ * uses seed ^ (q * 0x9E3779B97F4A7C15), q = index among the fallback points
+ * * ens + member), all run as batched bursts of `steps` steps of dt (s) in
+ * the context's precision.  Outputs: Lp_sym6[6 n_pts] (1/s) and
+ * used_fallback[n_pts] (1 where DD answered; may be NULL).  Needs a fitted
+ * surrogate (PTADD_ERR_STATE otherwise); segments a multiple of 32, >= 64.
+ * Replaces the context's loaded batch; allocates device memory through the
+ * surrogate and batch calls. */
+ptadd_status ptadd_closure_sweep(ptadd_ctx* ctx, int64_t n_pts, const double* sig6, const double* rho24, int32_t ens,
+                                 int64_t segments, int64_t steps, double dt, uint64_t seed, double* Lp_sym6,
+                                 uint8_t* used_fallback);
+
+/* One realisation for a closure input (host only, no GPU): n_loops circular
+ * glide loops of 32 nodes following the 24 densities rho24 (1/m^2; 12
+ * mobile then 12 sessile, FCC systems in the order: planes (111), (-111),
+ * (1-11), (11-1), in each the <110> directions [01-1], [10-1], [1-10],
+ * [011], [101], [110] that lie in it).  Class counts are the floor of
+ * n_loops x share, plus one for the classes picked by systematic sampling of
+ * the remainders; radii are stratified over (0.05, 0.2) um and line senses
+ * balanced within each class; centres uniform in a cube whose volume makes
+ * the total density exact; sessile loops pinned.  Random numbers: xoshiro256**
+ * seeded by SplitMix64 from `seed`.  Outputs (caller-owned host arrays):
+ * xyz[n_loops*32*3] (m), burgers[n_loops*3] (m, |b| = mat->b),
+ * normal[n_loops*3], pinned[n_loops*32], *volume (m^3).  Loop l owns nodes
+ * 32l .. 32l+31. */
+ptadd_status ptadd_closure_realisation(const ptadd_material* mat, uint64_t seed, const double* rho24,
+                                       int32_t n_loops, double* xyz, double* burgers, double* normal,
+                                       uint8_t* pinned, double* volume);
+
 /* Save / restore a fitted surrogate (weights, input/output maps, trust
  * region) as one blob; buf = NULL asks for the size. */
 ptadd_status ptadd_surrogate_get_state(ptadd_ctx* ctx, void* buf, size_t* bytes);

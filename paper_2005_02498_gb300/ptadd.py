@@ -31,6 +31,7 @@ EXPORTS = ["ptadd_version", "ptadd_create", "ptadd_destroy", "ptadd_last_error",
            "ptadd_gemm_bf16", "ptadd_mlp_param_count", "ptadd_mlp_init", "ptadd_mlp_set_params",
            "ptadd_mlp_get_params", "ptadd_mlp_loss_grad", "ptadd_mlp_train", "ptadd_mlp_forward",
            "ptadd_surrogate_fit", "ptadd_surrogate_predict", "ptadd_surrogate_predict_dev",
+           "ptadd_closure_sweep", "ptadd_closure_realisation",
            "ptadd_surrogate_get_state", "ptadd_surrogate_set_state"]
 NOALLOC_MAX_SEGMENTS = 16384
 
@@ -162,6 +163,12 @@ def load(build_if_missing=True):
     lib.ptadd_surrogate_predict.restype = st
     lib.ptadd_surrogate_predict_dev.argtypes = [_VP, ctypes.c_int64, _VP, _VP, _VP]
     lib.ptadd_surrogate_predict_dev.restype = st
+    lib.ptadd_closure_sweep.argtypes = [_VP, ctypes.c_int64, _D, _D, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.c_double, ctypes.c_uint64, _D, _U8]
+    lib.ptadd_closure_sweep.restype = st
+    lib.ptadd_closure_realisation.argtypes = [ctypes.POINTER(Material), ctypes.c_uint64, _D, ctypes.c_int32, _D, _D,
+                                              _D, _U8, _D]
+    lib.ptadd_closure_realisation.restype = st
     lib.ptadd_surrogate_get_state.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_size_t)]
     lib.ptadd_surrogate_get_state.restype = st
     lib.ptadd_surrogate_set_state.argtypes = [_VP, _VP, ctypes.c_size_t]
@@ -217,6 +224,23 @@ def mlp_param_count():
 
 def _fptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def closure_realisation(material, seed, rho24, n_loops):
+    """ptadd_closure_realisation: one stratified realisation for the 24
+    densities (host only).  Returns (xyz [32 n_loops, 3], burgers [n_loops, 3],
+    normal [n_loops, 3], pinned [32 n_loops], volume)."""
+    lib = load()
+    m = Material(*tuple(material))
+    r = _c(rho24, np.float64)
+    xyz = np.zeros((32 * n_loops, 3))
+    b = np.zeros((n_loops, 3))
+    nv = np.zeros((n_loops, 3))
+    pin = np.zeros(32 * n_loops, np.uint8)
+    vol = ctypes.c_double(0.0)
+    _check(lib.ptadd_closure_realisation(ctypes.byref(m), ctypes.c_uint64(seed), _dptr(r), int(n_loops), _dptr(xyz),
+                                         _dptr(b), _dptr(nv), pin.ctypes.data_as(_U8), ctypes.byref(vol)))
+    return xyz, b, nv, pin, vol.value
 
 
 def gemm_bf16(A_bits, B_bits, device=0):
@@ -452,6 +476,17 @@ class Context:
     def surrogate_predict_dev(self, n, feat_ptr, lp6_ptr, region_ptr=None):
         _check(self._lib.ptadd_surrogate_predict_dev(self._h, int(n), _VP(feat_ptr), _VP(lp6_ptr),
                                                      _VP(region_ptr) if region_ptr else None))
+
+    def closure_sweep(self, sig6, rho24, ens, segments, steps, dt, seed):
+        """ptadd_closure_sweep: (lp6 [n, 6], used_fallback [n] bool)."""
+        s6 = _c(sig6, np.float64)
+        r = _c(rho24, np.float64)
+        n = s6.shape[0]
+        out = np.zeros((n, 6))
+        used = np.zeros(n, np.uint8)
+        _check(self._lib.ptadd_closure_sweep(self._h, n, _dptr(s6), _dptr(r), int(ens), int(segments), int(steps),
+                                             float(dt), ctypes.c_uint64(seed), _dptr(out), used.ctypes.data_as(_U8)))
+        return out, used.astype(bool)
 
     def surrogate_get_state(self):
         n = ctypes.c_size_t(0)

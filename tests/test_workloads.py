@@ -154,3 +154,36 @@ def test_closure_input_generators_follow_their_recipes():
         lg = np.sort(np.log10(tot))
         u = (np.arange(lg.size) + 0.5) / lg.size
         assert np.allclose(lg, np.log10(2e12) + u * (np.log10(2e13) - np.log10(2e12)))
+
+
+def test_native_closure_realisation_follows_the_densities():
+    """The library's realisation generator (host code, no GPU): same recipe
+    and slip-system order as the Python one, exact total density, class
+    counts within one loop, balanced senses, reproducible streams."""
+    from paper_2005_02498_gb300 import ptadd
+    mat = W.Material().as_tuple()
+    rng = np.random.default_rng(12)
+    for trial in range(10):
+        rho = np.concatenate([rng.dirichlet(np.ones(12)) * 10 ** rng.uniform(12.3, 13.3),
+                              rng.dirichlet(np.ones(12)) * 10 ** rng.uniform(12.3, 13.3)])
+        n_loops = int(rng.choice([8, 48, 128]))
+        xyz, b, nv, pin, vol = ptadd.closure_realisation(mat, 1000 + trial, rho, n_loops)
+        net = W.Network(xyz, np.arange(n_loops + 1, dtype=np.int64) * 32, b, nv, pin, vol, np.zeros(6))
+        L = _loop_lengths(net)
+        assert abs(L.sum() / vol / rho.sum() - 1) < 1e-12
+        assert np.allclose(np.linalg.norm(b, axis=1), mat[2]) and np.allclose(np.linalg.norm(nv, axis=1), 1.0)
+        assert np.allclose(np.einsum("ij,ij->i", b, nv), 0.0, atol=1e-20)
+        cls = W.slip_system_index(b, nv) + 12 * pin.reshape(-1, 32)[:, 0]
+        expect = n_loops * rho / rho.sum()
+        counts = np.bincount(cls, minlength=24)
+        assert np.all(counts >= np.floor(expect)) and np.all(counts <= np.ceil(expect))
+        r = L / (2 * 32 * np.sin(np.pi / 32))
+        assert np.all(r >= 0.05e-6 * (1 - 1e-12)) and np.all(r <= 0.2e-6 * (1 + 1e-12))
+        x = xyz.reshape(-1, 32, 3)
+        sense = np.sign(np.einsum("ij,ij->i", np.cross(x[:, 0] - x.mean(1), x[:, 1] - x.mean(1)), nv))
+        for c in range(24):
+            assert abs(sense[cls == c].sum()) <= 1
+    a = ptadd.closure_realisation(mat, 5, rho, 16)
+    b2 = ptadd.closure_realisation(mat, 5, rho, 16)
+    c = ptadd.closure_realisation(mat, 6, rho, 16)
+    assert np.array_equal(a[0], b2[0]) and not np.array_equal(a[0], c[0])
