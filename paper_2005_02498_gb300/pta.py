@@ -1,0 +1,146 @@
+"""Practical Time Averaging of one DD box (Sec. 3.1): the slow-time loop
+around the DD burst.
+
+    python -m paper_2005_02498_gb300.pta --slow-steps 5
+
+The applied stress follows the load l(t) = c1 (t + Delta) along a fixed unit
+pattern, so that l(-Delta) = 0.  At slow time t, from the microstructure left
+by the previous slow step:
+  1. burst at l(t - Delta) until the running averages R^Lp and R^rho (Eq. 2.5)
+     change by less than the tolerances over one chunk of DD steps;
+  2. from the state that step 1 ends in, burst at l(t) to the same test;
+  3. Lpdot(t) = (R^Lp_t - R^Lp_{t-Delta}) / Delta, rhodot likewise;
+  4. if |Lpdot| exceeds the jump threshold, restart at step 1 from the state
+     step 2 ended in (a jump of the state on the slow time scale);
+  5. if |R^Lp_{t-Delta}| > |R^Lp_t|, keep running the t - Delta average (from
+     where step 1 ended) until it is not, or a cap is reached;
+  6. the next slow step is h = min(h_max, 0.002 / |R^Lp_t|), so that the
+     plastic strain of one step stays below 0.002.
+Norms are Frobenius norms.  The bursts run through the C ABI
+(ptadd_set_applied_stress, ptadd_advance, ptadd_get_state/ptadd_set_state).
+"""
+
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import json
+
+import numpy as np
+
+from . import ptadd
+from . import workloads as W
+
+
+@dataclasses.dataclass
+class PTAParams:
+    rate: float = 1e9            # c1, Pa per slow-time second
+    pattern: tuple = (0.0, 0.0, 1.0, 0.0, 0.0, 0.0)  # unit stress pattern (Voigt)
+    delta: float = 5e-3          # Delta, slow-time s
+    h0: float = 1e-2             # first slow step, s
+    h_max: float = 1e-1
+    dt: float = 5e-13            # DD time step, s
+    chunk: int = 20              # DD steps between convergence checks
+    tol_lp: float = 2e-2
+    tol_rho: float = 1e-3
+    max_chunks: int = 10
+    extend_chunks: int = 10
+    lpdot_max: float = 1e12      # jump threshold on |Lpdot|, 1/s^2
+    max_jumps: int = 3
+    strain_step: float = 0.002
+
+
+class _Average:
+    """Running averages over chunks of equal length."""
+
+    def __init__(self):
+        self.sum_lp = np.zeros((3, 3))
+        self.sum_rho = 0.0
+        self.chunks = 0
+
+    def add(self, lp, rho):
+        self.sum_lp += lp
+        self.sum_rho += rho
+        self.chunks += 1
+
+    @property
+    def lp(self):
+        return self.sum_lp / self.chunks
+
+    @property
+    def rho(self):
+        return self.sum_rho / self.chunks
+
+
+def _converge(ctx, sigma, p):
+    """Steps 1/2: bursts of p.chunk steps from the current state until the
+    running averages move by less than the tolerances over one chunk."""
+    ctx.set_applied_stress(sigma)
+    avg = _Average()
+    prev = None
+    while avg.chunks < p.max_chunks:
+        avg.add(*ctx.advance(p.chunk, p.dt))
+        cur = (avg.lp.copy(), avg.rho)
+        if prev is not None:
+            dl = np.linalg.norm(cur[0] - prev[0]) <= p.tol_lp * np.linalg.norm(cur[0])
+            dr = abs(cur[1] - prev[1]) <= p.tol_rho * abs(cur[1])
+            if dl and dr:
+                break
+        prev = cur
+    return avg
+
+
+def run(ctx, net, p, slow_steps):
+    """Run `slow_steps` slow steps; returns one record per step."""
+    pattern = np.asarray(p.pattern, float)
+    load = lambda t: p.rate * (t + p.delta) * pattern  # noqa: E731
+    ctx.set_network(net)
+    state = ctx.get_state()
+    t, h = 0.0, p.h0
+    out = []
+    for _ in range(slow_steps):
+        jumps = 0
+        while True:
+            ctx.set_state(state)
+            a1 = _converge(ctx, load(t - p.delta), p)
+            s1 = ctx.get_state()
+            a2 = _converge(ctx, load(t), p)
+            s2 = ctx.get_state()
+            lpdot = (a2.lp - a1.lp) / p.delta
+            if np.linalg.norm(lpdot) > p.lpdot_max and jumps < p.max_jumps:
+                state, jumps = s2, jumps + 1
+                continue
+            break
+        extended = 0
+        if np.linalg.norm(a1.lp) > np.linalg.norm(a2.lp):
+            ctx.set_state(s1)
+            ctx.set_applied_stress(load(t - p.delta))
+            while np.linalg.norm(a1.lp) > np.linalg.norm(a2.lp) and extended < p.extend_chunks:
+                a1.add(*ctx.advance(p.chunk, p.dt))
+                extended += 1
+            lpdot = (a2.lp - a1.lp) / p.delta
+        rhodot = (a2.rho - a1.rho) / p.delta
+        out.append({"t": t, "h": h, "load": float(p.rate * (t + p.delta)), "Lp": a2.lp.tolist(), "rho": a2.rho,
+                    "Lp_prev": a1.lp.tolist(), "Lpdot": lpdot.tolist(), "rhodot": rhodot, "jumps": jumps,
+                    "chunks": [a1.chunks - extended, a2.chunks], "extended": extended})
+        h = min(p.h_max, p.strain_step / max(np.linalg.norm(a2.lp), 1e-300))
+        state = s2
+        t += h
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--slow-steps", type=int, default=5)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--device", type=int, default=0)
+    a = ap.parse_args(argv)
+    prec = ptadd.PTADD_FP64 if a.precision == "fp64" else ptadd.PTADD_MIXED
+    with ptadd.Context(W.Material().as_tuple(), prec, a.device) as ctx:
+        recs = run(ctx, W.small_loop_network(), PTAParams(), a.slow_steps)
+    print(json.dumps({"workload": "16 loops, 512 segments", "precision": a.precision, "steps": recs}))
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

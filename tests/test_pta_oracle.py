@@ -1,0 +1,71 @@
+"""The oracle's Practical Time Averaging loop (Sec. 3.1) against the rules of
+the paper's single-box algorithm, on the 512-segment network (CPU).  The
+bursts themselves are pinned in test_oracle_pins.py; here the control flow:
+the difference quotient, the jump rule, the extension rule, the step control
+and the load ramp."""
+
+import dataclasses
+
+import numpy as np
+
+import oracle as O
+from oracle import pta as OP
+from paper_2005_02498_gb300 import workloads as W
+
+MAT = W.Material().as_tuple()
+
+
+@dataclasses.dataclass
+class P:
+    rate: float = 1e9
+    pattern: tuple = (0.0, 0.0, 1.0, 0.0, 0.0, 0.0)
+    delta: float = 5e-3
+    h0: float = 1e-2
+    h_max: float = 1e-1
+    dt: float = 5e-13
+    chunk: int = 10
+    tol_lp: float = 2e-2
+    tol_rho: float = 1e-3
+    max_chunks: int = 4
+    extend_chunks: int = 3
+    lpdot_max: float = 1e30
+    max_jumps: int = 2
+    strain_step: float = 0.002
+
+
+def test_pta_records_follow_the_rules():
+    p = P()
+    recs = OP.run(MAT, W.small_loop_network(), p, 3)
+    assert recs[0]["t"] == 0.0 and recs[0]["load"] == p.rate * p.delta  # l(-Delta) = 0
+    for k, r in enumerate(recs):
+        assert r["jumps"] == 0  # threshold out of reach
+        assert np.allclose(r["Lpdot"], (r["Lp"] - r["Lp_prev"]) / p.delta, rtol=1e-12, atol=0)
+        # the t - Delta average was extended until it no longer exceeded the t one, or the cap was hit
+        assert np.linalg.norm(r["Lp_prev"]) <= np.linalg.norm(r["Lp"]) or r["extended"] == p.extend_chunks
+        assert 1 <= r["chunks"][0] <= p.max_chunks and 1 <= r["chunks"][1] <= p.max_chunks
+        assert r["load"] == p.rate * (r["t"] + p.delta)
+        if k + 1 < len(recs):
+            h = min(p.h_max, p.strain_step / np.linalg.norm(r["Lp"]))
+            assert abs(recs[k + 1]["t"] - (r["t"] + h)) <= 1e-15 * max(1.0, r["t"] + h)
+
+
+def test_pta_jump_rule_restarts_until_the_cap():
+    p = P(lpdot_max=0.0, max_jumps=2, max_chunks=2)
+    recs = OP.run(MAT, W.small_loop_network(), p, 1)
+    assert recs[0]["jumps"] == 2
+
+
+def test_pta_first_step_is_two_plain_bursts_when_one_chunk_is_allowed():
+    """With one chunk per average and no extension, step 1 is one burst at
+    l(-Delta) = 0 and step 2 one burst at l(0) from where step 1 ended."""
+    p = P(max_chunks=1, extend_chunks=0)
+    net = W.small_loop_network()
+    rec = OP.run(MAT, net, p, 1)[0]
+    n1 = net.copy()
+    n1.sig_app = np.zeros(6)
+    r1 = O.burst(MAT, n1, p.chunk, p.dt)
+    n2 = net.copy()
+    n2.xyz = r1["xyz"]
+    n2.sig_app = np.array(p.pattern) * p.rate * p.delta
+    r2 = O.burst(MAT, n2, p.chunk, p.dt)
+    assert np.array_equal(rec["Lp_prev"], r1["Lp_avg"]) and np.array_equal(rec["Lp"], r2["Lp_avg"])
