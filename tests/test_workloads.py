@@ -187,3 +187,21 @@ def test_native_closure_realisation_follows_the_densities():
     b2 = ptadd.closure_realisation(mat, 5, rho, 16)
     c = ptadd.closure_realisation(mat, 6, rho, 16)
     assert np.array_equal(a[0], b2[0]) and not np.array_equal(a[0], c[0])
+
+
+def test_native_closure_realisation_rejects_bad_arguments():
+    import pytest
+    from paper_2005_02498_gb300 import ptadd
+    mat = W.Material().as_tuple()
+    good = np.full(24, 1e11)
+    bad = good.copy()
+    bad[3] = -1.0
+    with pytest.raises(ptadd.PtaddError):
+        ptadd.closure_realisation(mat, 1, bad, 8)
+    bad[3] = np.nan
+    with pytest.raises(ptadd.PtaddError):
+        ptadd.closure_realisation(mat, 1, bad, 8)
+    with pytest.raises(ptadd.PtaddError):
+        ptadd.closure_realisation(mat, 1, good, 0)
+    with pytest.raises(ptadd.PtaddError):
+        ptadd.closure_realisation((48e9, 0.34, 0.0, 2.556e-10, 1e-4), 1, good, 8)  # b = 0
