@@ -306,6 +306,17 @@ ptadd_status ptadd_closure_realisation(const ptadd_material* mat, uint64_t seed,
                                        int32_t n_loops, double* xyz, double* burgers, double* normal,
                                        uint8_t* pinned, double* volume);
 
+/* Non-negative dissipation at a material point (Sec. 4, "Ensuring
+ * non-negative dissipation"; host only, no GPU).  T6: Cauchy stress in
+ * Voigt order xx, yy, zz, yz, xz, xy (any unit); Lp[9]: plastic distortion rate, row-major, corrected in
+ * place: if T : Lp < 0 its component along T is removed (Lp -= (T:Lp) T /
+ * |T|^2).  V[3] (or NULL): polar dislocation velocity, corrected in place
+ * with alpha[9] (dislocation density tensor, row-major): if
+ * beta = V . X(T alpha) < 0, V -= beta X(T alpha) / |X(T alpha)|^2, where
+ * (X A)_i = e_ijk A_jk.  Zero T (or zero X(T alpha)) leaves the input as is.
+ * PTADD_ERR_ARG on NULL T/Lp, V without alpha, or non-finite values. */
+ptadd_status ptadd_dissipation_projection(const double T6[6], const double alpha[9], double Lp[9], double V[3]);
+
 /* Save / restore a fitted surrogate (weights, input/output maps, trust
  * region) as one blob; buf = NULL asks for the size. */
 ptadd_status ptadd_surrogate_get_state(ptadd_ctx* ctx, void* buf, size_t* bytes);

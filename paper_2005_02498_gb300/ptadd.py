@@ -31,7 +31,7 @@ EXPORTS = ["ptadd_version", "ptadd_create", "ptadd_destroy", "ptadd_last_error",
            "ptadd_gemm_bf16", "ptadd_mlp_param_count", "ptadd_mlp_init", "ptadd_mlp_set_params",
            "ptadd_mlp_get_params", "ptadd_mlp_loss_grad", "ptadd_mlp_train", "ptadd_mlp_forward",
            "ptadd_surrogate_fit", "ptadd_surrogate_predict", "ptadd_surrogate_predict_dev",
-           "ptadd_closure_sweep", "ptadd_closure_realisation",
+           "ptadd_closure_sweep", "ptadd_closure_realisation", "ptadd_dissipation_projection",
            "ptadd_surrogate_get_state", "ptadd_surrogate_set_state"]
 NOALLOC_MAX_SEGMENTS = 16384
 
@@ -169,6 +169,8 @@ def load(build_if_missing=True):
     lib.ptadd_closure_realisation.argtypes = [ctypes.POINTER(Material), ctypes.c_uint64, _D, ctypes.c_int32, _D, _D,
                                               _D, _U8, _D]
     lib.ptadd_closure_realisation.restype = st
+    lib.ptadd_dissipation_projection.argtypes = [_D, _D, _D, _D]
+    lib.ptadd_dissipation_projection.restype = st
     lib.ptadd_surrogate_get_state.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_size_t)]
     lib.ptadd_surrogate_get_state.restype = st
     lib.ptadd_surrogate_set_state.argtypes = [_VP, _VP, ctypes.c_size_t]
@@ -241,6 +243,19 @@ def closure_realisation(material, seed, rho24, n_loops):
     _check(lib.ptadd_closure_realisation(ctypes.byref(m), ctypes.c_uint64(seed), _dptr(r), int(n_loops), _dptr(xyz),
                                          _dptr(b), _dptr(nv), pin.ctypes.data_as(_U8), ctypes.byref(vol)))
     return xyz, b, nv, pin, vol.value
+
+
+def dissipation_projection(T6, Lp, V=None, alpha=None):
+    """ptadd_dissipation_projection (host only): returns the corrected
+    (Lp [3,3], V [3] or None)."""
+    lib = load()
+    t = _c(T6, np.float64)
+    L = np.array(Lp, dtype=np.float64).reshape(9)
+    v = None if V is None else np.array(V, dtype=np.float64).reshape(3)
+    a = None if alpha is None else _c(np.asarray(alpha, np.float64).reshape(9), np.float64)
+    _check(lib.ptadd_dissipation_projection(_dptr(t), _dptr(a) if a is not None else None, _dptr(L),
+                                            _dptr(v) if v is not None else None))
+    return L.reshape(3, 3), v
 
 
 def gemm_bf16(A_bits, B_bits, device=0):
