@@ -317,6 +317,34 @@ ptadd_status ptadd_closure_realisation(const ptadd_material* mat, uint64_t seed,
  * PTADD_ERR_ARG on NULL T/Lp, V without alpha, or non-finite values. */
 ptadd_status ptadd_dissipation_projection(const double T6[6], const double alpha[9], double Lp[9], double V[3]);
 
+/* Block stress average of the coupling (Sec. 4.2, the stress-averaging
+ * block; host only, no GPU): <T>_r = sum_{g in r} w_g T_g / sum_{g in r} w_g
+ * over the Gauss points g of block r.  T6[6g..]: stress at point g (Voigt
+ * order, any unit); w[g] > 0: its volume weight (quadrature weight times
+ * Jacobian, so that the weights of a block add up to its volume);
+ * block[g] in [0, n_blocks).  T6_avg[6r..] (caller-owned) receives <T>_r.
+ * Sums run in point order.  PTADD_ERR_ARG on NULL arrays, bad sizes, a block
+ * index out of range, a weight that is not positive and finite, a
+ * non-finite stress, or a block that holds no point. */
+ptadd_status ptadd_block_average(int64_t n_gp, const double* T6, const double* w, const int32_t* block,
+                                 int32_t n_blocks, double* T6_avg);
+
+/* The two stresses one coupling increment k hands to PTA at each block
+ * (Sec. 4.2.1, stress extrapolation and the minimum stress gap; host only):
+ *   T6_prev[r] = <T>^k_r                                  (T^_{r,t-Delta})
+ *   T6_t[r]    = <T>^k_r + (delta_star/dt_prev)(<T>^k_r - <T>^{k-1}_r)
+ * and, when the gap |T6_t - T6_prev| (Frobenius norm of the full tensor) is
+ * below gap_min, T6_t = T6_prev + mag (T6_t - T6_prev) with
+ * mag[r] = gap_min / gap > 1, so that the gap is gap_min; otherwise mag = 1.
+ * The rates PTA returns for block r are to be divided by mag[r].  A zero gap
+ * leaves T6_t = T6_prev with mag = +inf (rates 0).  T6_km1 = NULL or
+ * dt_prev <= 0 means no extrapolation (T6_t = <T>^k before the gap rule).
+ * Arrays [n_blocks][6] (Voigt, any unit) and mag[n_blocks], caller-owned.
+ * PTADD_ERR_ARG on NULL arrays, delta_star <= 0, gap_min < 0, or
+ * non-finite values. */
+ptadd_status ptadd_block_stress_pair(int32_t n_blocks, const double* T6_k, const double* T6_km1, double delta_star,
+                                     double dt_prev, double gap_min, double* T6_prev, double* T6_t, double* mag);
+
 /* Save / restore a fitted surrogate (weights, input/output maps, trust
  * region) as one blob; buf = NULL asks for the size. */
 ptadd_status ptadd_surrogate_get_state(ptadd_ctx* ctx, void* buf, size_t* bytes);

@@ -32,6 +32,7 @@ EXPORTS = ["ptadd_version", "ptadd_create", "ptadd_destroy", "ptadd_last_error",
            "ptadd_mlp_get_params", "ptadd_mlp_loss_grad", "ptadd_mlp_train", "ptadd_mlp_forward",
            "ptadd_surrogate_fit", "ptadd_surrogate_predict", "ptadd_surrogate_predict_dev",
            "ptadd_closure_sweep", "ptadd_closure_realisation", "ptadd_dissipation_projection",
+           "ptadd_block_average", "ptadd_block_stress_pair",
            "ptadd_surrogate_get_state", "ptadd_surrogate_set_state"]
 NOALLOC_MAX_SEGMENTS = 16384
 
@@ -171,6 +172,11 @@ def load(build_if_missing=True):
     lib.ptadd_closure_realisation.restype = st
     lib.ptadd_dissipation_projection.argtypes = [_D, _D, _D, _D]
     lib.ptadd_dissipation_projection.restype = st
+    lib.ptadd_block_average.argtypes = [ctypes.c_int64, _D, _D, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _D]
+    lib.ptadd_block_average.restype = st
+    lib.ptadd_block_stress_pair.argtypes = [ctypes.c_int32, _D, _D, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, _D, _D, _D]
+    lib.ptadd_block_stress_pair.restype = st
     lib.ptadd_surrogate_get_state.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_size_t)]
     lib.ptadd_surrogate_get_state.restype = st
     lib.ptadd_surrogate_set_state.argtypes = [_VP, _VP, ctypes.c_size_t]
@@ -256,6 +262,38 @@ def dissipation_projection(T6, Lp, V=None, alpha=None):
     _check(lib.ptadd_dissipation_projection(_dptr(t), _dptr(a) if a is not None else None, _dptr(L),
                                             _dptr(v) if v is not None else None))
     return L.reshape(3, 3), v
+
+
+def block_average(T6, w, block, n_blocks):
+    """ptadd_block_average (host only): volume-weighted block averages of the
+    Gauss-point stresses T6 [n, 6] with weights w [n] and block indices
+    block [n]; returns [n_blocks, 6]."""
+    lib = load()
+    t = _c(T6, np.float64).reshape(-1, 6)
+    ww = _c(w, np.float64).reshape(-1)
+    bl = _c(block, np.int32).reshape(-1)
+    if not (t.shape[0] == ww.shape[0] == bl.shape[0]):
+        raise ValueError("T6, w and block must describe the same Gauss points")
+    out = np.zeros((int(n_blocks), 6))
+    _check(lib.ptadd_block_average(t.shape[0], _dptr(t), _dptr(ww), bl.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   int(n_blocks), _dptr(out)))
+    return out
+
+
+def block_stress_pair(T6_k, T6_km1, delta_star, dt_prev, gap_min):
+    """ptadd_block_stress_pair (host only): returns (T_prev [R, 6],
+    T_t [R, 6], mag [R]) for the block stresses T6_k [R, 6] and
+    T6_km1 [R, 6] (or None)."""
+    lib = load()
+    tk = _c(T6_k, np.float64).reshape(-1, 6)
+    tm = None if T6_km1 is None else _c(T6_km1, np.float64).reshape(-1, 6)
+    if tm is not None and tm.shape != tk.shape:
+        raise ValueError("T6_k and T6_km1 differ in shape")
+    R = tk.shape[0]
+    tp, tt, mag = np.zeros((R, 6)), np.zeros((R, 6)), np.zeros(R)
+    _check(lib.ptadd_block_stress_pair(R, _dptr(tk), _dptr(tm) if tm is not None else None, float(delta_star),
+                                       float(dt_prev), float(gap_min), _dptr(tp), _dptr(tt), _dptr(mag)))
+    return tp, tt, mag
 
 
 def gemm_bf16(A_bits, B_bits, device=0):
