@@ -163,7 +163,8 @@ def run_synthetic(ctx, net, p, side=3, increments=4, rate=1e6, gradient=0.5, dt0
         dt, T_next = stress_step_control(
             lambda h: ptadd.block_average(bending_field(pts, load + rise * h, gradient, height), w, blk, n_blocks),
             T_k, step, p)
-        out.append({"t": t, "dt": dt, "load": load, "mag": rec["mag"].tolist(), "chunks": rec["chunks"],
+        out.append({"t": t, "dt": dt, "load": load, "chunks": rec["chunks"],
+                    "mag": [float(m) if np.isfinite(m) else None for m in rec["mag"]],  # None: no gap
                     "Lpdot_norm": _norms(rec["Lpdot"]).tolist(), "Lp_norm": _norms(rec["Lp"]).tolist(),
                     "limit": rec["limit"].tolist()})
         load += rise * dt
