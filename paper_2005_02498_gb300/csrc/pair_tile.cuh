@@ -95,9 +95,10 @@ __device__ __forceinline__ void pair_tile_fp64(const TileArgs& a, const Consts& 
         xq[qp][1] = __dadd_rn(ya, __dmul_rn(xi, Dy));
         xq[qp][2] = __dadd_rn(za, __dmul_rn(xi, Dz));
     }
-    double acc[4][3];
+    double acc[4][3];  // (sigma b') / c2 at the Gauss points
 #pragma unroll
     for (int qp = 0; qp < 4; ++qp) acc[qp][0] = acc[qp][1] = acc[qp][2] = 0.0;
+    const double nr = -c.c1 / c.c2;
 
     for (int64_t j0 = a.js; j0 < a.je; j0 += TILE) {
         const int cnt = (int)min((int64_t)TILE, a.je - j0);
@@ -113,14 +114,16 @@ __device__ __forceinline__ void pair_tile_fp64(const TileArgs& a, const Consts& 
             const double t[3] = {r[4], r[5], r[6]};
             const double b[3] = {r[8], r[9], r[10]};
             const double q[3] = {r[12], r[13], r[14]};
-            PairK<double> k;
-            pair_constants(t, b, q, bt, k);
+            PairK k;
+            pair_constants(t, q, bt, nr, k);
 #pragma unroll
             for (int qp = 0; qp < 4; ++qp)
-                seg_sigma_b(xq[qp][0] - x1[0], xq[qp][1] - x1[1], xq[qp][2] - x1[2], t, L, b, q, bt, k, c.a2,
-                            c.c1, c.c2, acc[qp]);
+                seg_sigma_b(xq[qp][0] - x1[0], xq[qp][1] - x1[1], xq[qp][2] - x1[2], t, L, b, q, bt, k, c.a2, nr,
+                            acc[qp]);
         }
     }
+#pragma unroll
+    for (int qp = 0; qp < 4; ++qp) acc[qp][0] *= c.c2, acc[qp][1] *= c.c2, acc[qp][2] *= c.c2;
     if (active) tile_store(a, seg, Dx, Dy, Dz, bt, acc);
 }
 
@@ -179,11 +182,10 @@ struct Pair2 {
 
 // Packed field of one source at two Gauss points (lanes), given R0 = x - x1:
 // s <- (sigma b') / c2 per lane, and dd <- squared point-to-segment distance
-// + a^2.  The formula of seg_sigma_b_geom rearranged for fused multiply-adds:
-// c2 is taken out of every coefficient (the caller scales the sums), the
-// moments enter as K2 = 3 J2, K3 = 3 J3, K4 = 3 J4 (which absorbs the 1/3 and
-// the 3 of 3 c2), y = R0.t is carried as ny = -y, and (b x b').Rp is
-// evaluated as b'.(Rp x b).  a2 = a^2, nr = -c1/c2.
+// + a^2.  The formula of seg_sigma_b (FP64, c2 taken out, K_k = 3 J_k,
+// (b x b').Rp as b'.(Rp x b)) in packed FP32, with y = R0.t carried as
+// ny = -y and the negated source vectors of the record, so that every
+// subtraction is a fused multiply-add.  a2 = a^2, nr = -c1/c2.
 __device__ __forceinline__ void seg_sigma_b2(float2 R0x, float2 R0y, float2 R0z, const Src2& S, const float2 bt[3],
                                              const Pair2& P, float2 a2, float2 nr, float2 s[3], float2& dd)
 {
@@ -255,15 +257,16 @@ __device__ __forceinline__ double3 near_field_fp64(const double* __restrict__ po
     const double td[3] = {r64[4], r64[5], r64[6]};
     const double bd[3] = {r64[8], r64[9], r64[10]};
     const double qd[3] = {r64[12], r64[13], r64[14]};
-    PairK<double> kd;
-    pair_constants(td, bd, qd, bt, kd);
+    const double nr = -c1 / c2;
+    PairK kd;
+    pair_constants(td, qd, bt, nr, kd);
     const double xi = gl4_xi(qp);
     const double xq0 = __dadd_rn(xa, __dmul_rn(xi, Dx));
     const double xq1 = __dadd_rn(ya, __dmul_rn(xi, Dy));
     const double xq2 = __dadd_rn(za, __dmul_rn(xi, Dz));
     double vd[3] = {0.0, 0.0, 0.0};
-    seg_sigma_b(xq0 - x1d[0], xq1 - x1d[1], xq2 - x1d[2], td, r64[3], bd, qd, bt, kd, a2, c1, c2, vd);
-    return make_double3(vd[0], vd[1], vd[2]);
+    seg_sigma_b(xq0 - x1d[0], xq1 - x1d[1], xq2 - x1d[2], td, r64[3], bd, qd, bt, kd, a2, nr, vd);
+    return make_double3(c2 * vd[0], c2 * vd[1], c2 * vd[2]);
 }
 
 // Near pairs found by a warp wait in a per-warp queue of (source index,

@@ -35,10 +35,11 @@ namespace ptadd {
 
 // ---------------------------------------------------------------- math
 // Reciprocal and reciprocal square root.  FP32: the hardware approximations
-// (PTX rcp.approx / rsqrt.approx).  FP64: the FP32 approximation as a seed,
-// then two Newton-Raphson steps in FP64 (y <- y + y (1 - x y) for 1/x,
-// y <- y + y (1/2 - x/2 y^2) for 1/sqrt x), which square the ~2^-22 seed
-// error twice.
+// (PTX rcp.approx / rsqrt.approx).  FP64: the FP32 approximation as a seed y,
+// then ONE third-order (Householder) correction: with e = 1 - x y,
+// 1/x = y / (1 - e) ~ y (1 + e + e^2); with e = 1 - x y^2,
+// 1/sqrt x = y (1 - e)^(-1/2) ~ y (1 + e/2 + 3 e^2 / 8).  The ~2^-22 error of
+// the seed becomes ~2^-66, below the final rounding.
 __device__ __forceinline__ float rcp_approx(float x)
 {
     float y;
@@ -53,129 +54,85 @@ __device__ __forceinline__ float rsqrt_approx(float x)
 }
 __device__ __forceinline__ double rcp_nr(double x)
 {
-    double y = (double)rcp_approx(__double2float_rn(x));
-    double e = fma(-x, y, 1.0);
-    y = fma(y, e, y);
-    e = fma(-x, y, 1.0);
-    return fma(y, e, y);
+    const double y = (double)rcp_approx(__double2float_rn(x));
+    const double e = fma(-x, y, 1.0);
+    return fma(y, fma(e, e, e), y);
 }
 __device__ __forceinline__ double rsqrt_nr(double x)
 {
-    double y = (double)rsqrt_approx(__double2float_rn(x));
-    const double hx = 0.5 * x;
-    double e = fma(-hx * y, y, 0.5);
-    y = fma(y, e, y);
-    e = fma(-hx * y, y, 0.5);
-    return fma(y, e, y);
+    const double y = (double)rsqrt_approx(__double2float_rn(x));
+    const double e = fma(-x * y, y, 1.0);
+    return fma(y * e, fma(e, 0.375, 0.5), y);
 }
 
-template <typename T> struct RMath;
-template <> struct RMath<double> {
-    static __device__ __forceinline__ double rcp(double x) { return rcp_nr(x); }
-    static __device__ __forceinline__ double rsqrt(double x) { return rsqrt_nr(x); }
-};
-template <> struct RMath<float> {
-    static __device__ __forceinline__ float rcp(float x) { return rcp_approx(x); }
-    static __device__ __forceinline__ float rsqrt(float x) { return rsqrt_approx(x); }
+// Per-pair constants that depend on the source and the target only:
+// t.b', q.b' and r t.b' with r = -c1/c2.
+struct PairK {
+    double tb, qb, nrtb;
 };
 
-// Per-pair constants that depend on the source and the target only.
-template <typename T> struct PairK {
-    T tb;     // t . b'
-    T qb;     // q . b'
-    T w[3];   // b x b'
-};
-
-template <typename T>
-__device__ __forceinline__ void pair_constants(const T t[3], const T b[3], const T q[3], const T bt[3],
-                                               PairK<T>& k)
+__device__ __forceinline__ void pair_constants(const double t[3], const double q[3], const double bt[3], double nr,
+                                               PairK& k)
 {
-    k.tb = t[0] * bt[0] + t[1] * bt[1] + t[2] * bt[2];
-    k.qb = q[0] * bt[0] + q[1] * bt[1] + q[2] * bt[2];
-    k.w[0] = b[1] * bt[2] - b[2] * bt[1];
-    k.w[1] = b[2] * bt[0] - b[0] * bt[2];
-    k.w[2] = b[0] * bt[1] - b[1] * bt[0];
+    k.tb = fma(t[0], bt[0], fma(t[1], bt[1], t[2] * bt[2]));
+    k.qb = fma(q[0], bt[0], fma(q[1], bt[1], q[2] * bt[2]));
+    k.nrtb = nr * k.tb;
 }
 
-// Geometry of one (field point, source) pair from R0 = x - x1.
-template <typename T> struct PairGeom {
-    T y;             // R0 . t  (u1 = -y)
-    T Rp[3];         // perpendicular part of R0
-    T d2;            // |Rp|^2 + a^2
-    T u2;            // L - y
-    T r1s, r2s;      // rho1^2, rho2^2
-};
-
-template <typename T>
-__device__ __forceinline__ void pair_geom(T R0x, T R0y, T R0z, const T t[3], T L, T a2, PairGeom<T>& g)
+// Accumulate (sigma b') / c2 of one source at one field point, given
+// R0 = x - x1; nr = -c1/c2.  The common factor c2 of the formula is applied
+// once per target by the caller, and the integrals J2, J3, J4 enter as
+// K_k = 3 J_k, which removes the factors 1/3 and 3 of the closed forms:
+//   A0 = a^2 K2 + 2 J0,  A1 = a^2 K3 + 2 J1,
+//   c_Rxb = r t.b' A0,   c_q = r t.b' A1 + J1 t.b' - J0 (Rp.b'),
+//   c_Rp = (q.Rp)(K2 (Rp.b') - K3 t.b') - J0 q.b',
+//   c_t = r (A0 (Rp.(b x b')) + A1 q.b') + J1 q.b' + (q.Rp)(K4 t.b' - K3 (Rp.b')),
+//   c_b = (q.Rp)(A0 - J0),
+// with Rp.(b x b') evaluated as b'.(Rp x b), reusing Rp x b.
+__device__ __forceinline__ void seg_sigma_b(double R0x, double R0y, double R0z, const double t[3], double L,
+                                            const double b[3], const double q[3], const double bt[3],
+                                            const PairK& k, double a2, double nr, double s[3])
 {
-    g.y = R0x * t[0] + R0y * t[1] + R0z * t[2];
-    g.Rp[0] = fma(-g.y, t[0], R0x);
-    g.Rp[1] = fma(-g.y, t[1], R0y);
-    g.Rp[2] = fma(-g.y, t[2], R0z);
-    g.d2 = fma(g.Rp[0], g.Rp[0], fma(g.Rp[1], g.Rp[1], fma(g.Rp[2], g.Rp[2], a2)));
-    g.u2 = L - g.y;
-    g.r1s = fma(g.y, g.y, g.d2);
-    g.r2s = fma(g.u2, g.u2, g.d2);
-}
-
-// Accumulate (sigma b') of one source at one field point from its geometry.
-template <typename T>
-__device__ __forceinline__ void seg_sigma_b_geom(const PairGeom<T>& G, const T t[3], T L, const T b[3],
-                                                 const T q[3], const T bt[3], const PairK<T>& k, T a2, T c1,
-                                                 T c2, T s[3])
-{
-    const T y = G.y, u2 = G.u2, d2 = G.d2, r1s = G.r1s, r2s = G.r2s;
-    const T Rpx = G.Rp[0], Rpy = G.Rp[1], Rpz = G.Rp[2];
-    const T i1 = RMath<T>::rsqrt(r1s), i2 = RMath<T>::rsqrt(r2s);
-    const T m = -y * i1, p = u2 * i2;
-    const bool same = (y <= T(0)) || (y >= L);  // u1 u2 >= 0
-    const T i1s = i1 * i1, i2s = i2 * i2, i12 = i1s * i2s;
-    const T pm = p * m;
-    const T S = fma(p, p, fma(m, m, pm));
-    const T isum = i1 + i2;
-    const T den = same ? (p + m) * (T(1) + pm) : d2;
-    const T rr = RMath<T>::rcp(den * isum);
-    const T rden = rr * isum;  // 1/den
-    const T Lsum = L * (u2 - y);  // L (u1 + u2)
-    const T J1 = Lsum * i12 * (rr * den);
-    const T J3 = J1 * (i1s + fma(i1, i2, i2s)) * T(1.0 / 3.0);
-    const T g = Lsum * i12 * rden;
-    const T J0 = same ? g * (T(1) + pm) : (p - m) * rden;
-    const T Wt = same ? fma((r1s + u2 * u2) * i12 * rden, p + m, i1s + i2s) : (T(3) - S) * rden;
-    const T J2 = J0 * Wt * T(1.0 / 3.0);
-    const T J4 = J0 * S * T(1.0 / 3.0);
-
-    const T A0 = fma(T(3) * a2, J2, T(2) * J0);
-    const T A1 = fma(T(3) * a2, J3, T(2) * J1);
-    const T Rb = Rpx * bt[0] + Rpy * bt[1] + Rpz * bt[2];
-    const T Rw = Rpx * k.w[0] + Rpy * k.w[1] + Rpz * k.w[2];
-    const T qR = Rpx * q[0] + Rpy * q[1] + Rpz * q[2];
-    const T c1tb = c1 * k.tb;
-    const T c3qR = T(3) * c2 * qR;
-    const T cRxb = -c1tb * A0;
-    const T cq = fma(-c1tb, A1, c2 * fma(J1, k.tb, -J0 * Rb));
-    const T cRp = fma(c3qR, fma(J2, Rb, -J3 * k.tb), -c2 * J0 * k.qb);
-    const T ct = fma(-c1, fma(A0, Rw, A1 * k.qb), fma(c2 * J1, k.qb, c3qR * fma(J4, k.tb, -J3 * Rb)));
-    const T cb = c2 * qR * (A0 - J0);
+    const double y = fma(R0x, t[0], fma(R0y, t[1], R0z * t[2]));  // u1 = -y
+    const double Rpx = fma(-y, t[0], R0x), Rpy = fma(-y, t[1], R0y), Rpz = fma(-y, t[2], R0z);
+    const double d2 = fma(Rpx, Rpx, fma(Rpy, Rpy, fma(Rpz, Rpz, a2)));
+    const double u2 = L - y;
+    const double r1s = fma(y, y, d2), r2s = fma(u2, u2, d2);
+    const double i1 = rsqrt_nr(r1s), i2 = rsqrt_nr(r2s);
+    const double m = -y * i1, p = u2 * i2;
+    const bool same = (y <= 0.0) || (y >= L);  // u1 u2 >= 0
+    const double i1s = i1 * i1, i2s = i2 * i2, i12 = i1s * i2s;
+    const double pm = p * m;
+    const double S = fma(p, p, fma(m, m, pm));
+    const double isum = i1 + i2;
+    const double pps = p + m, one_pm = 1.0 + pm;
+    const double den = same ? pps * one_pm : d2;
+    const double rr = rcp_nr(den * isum);
+    const double rden = rr * isum;        // 1/den
+    const double Li = L * (u2 - y) * i12;  // L (u1 + u2) / (rho1^2 rho2^2)
+    const double J1 = Li * (rr * den);
+    const double K3 = J1 * (i1s + fma(i1, i2, i2s));
+    const double J0 = same ? (Li * rden) * one_pm : (p - m) * rden;
+    const double Wt = same ? fma((r1s + u2 * u2) * i12 * rden, pps, i1s + i2s) : (3.0 - S) * rden;
+    const double K2 = J0 * Wt;
+    const double K4 = J0 * S;
+    const double A0 = fma(a2, K2, J0 + J0);
+    const double A1 = fma(a2, K3, J1 + J1);
     // Rp x b
-    const T Xx = Rpy * b[2] - Rpz * b[1];
-    const T Xy = Rpz * b[0] - Rpx * b[2];
-    const T Xz = Rpx * b[1] - Rpy * b[0];
+    const double Xx = fma(Rpy, b[2], -Rpz * b[1]);
+    const double Xy = fma(Rpz, b[0], -Rpx * b[2]);
+    const double Xz = fma(Rpx, b[1], -Rpy * b[0]);
+    const double Rb = fma(Rpx, bt[0], fma(Rpy, bt[1], Rpz * bt[2]));
+    const double Rw = fma(Xx, bt[0], fma(Xy, bt[1], Xz * bt[2]));
+    const double qR = fma(Rpx, q[0], fma(Rpy, q[1], Rpz * q[2]));
+    const double cRxb = k.nrtb * A0;
+    const double cq = fma(k.nrtb, A1, fma(J1, k.tb, -J0 * Rb));
+    const double cRp = fma(qR, fma(K2, Rb, -K3 * k.tb), -J0 * k.qb);
+    const double ct = fma(nr, fma(A0, Rw, A1 * k.qb), fma(J1, k.qb, qR * fma(K4, k.tb, -K3 * Rb)));
+    const double cb = qR * (A0 - J0);
     s[0] = fma(cRxb, Xx, fma(cq, q[0], fma(cRp, Rpx, fma(ct, t[0], fma(cb, bt[0], s[0])))));
     s[1] = fma(cRxb, Xy, fma(cq, q[1], fma(cRp, Rpy, fma(ct, t[1], fma(cb, bt[1], s[1])))));
     s[2] = fma(cRxb, Xz, fma(cq, q[2], fma(cRp, Rpz, fma(ct, t[2], fma(cb, bt[2], s[2])))));
-}
-
-// Accumulate (sigma b') of one source at one field point, given R0 = x - x1.
-template <typename T>
-__device__ __forceinline__ void seg_sigma_b(T R0x, T R0y, T R0z, const T t[3], T L, const T b[3],
-                                            const T q[3], const T bt[3], const PairK<T>& k, T a2, T c1,
-                                            T c2, T s[3])
-{
-    PairGeom<T> G;
-    pair_geom(R0x, R0y, R0z, t, L, a2, G);
-    seg_sigma_b_geom(G, t, L, b, q, bt, k, a2, c1, c2, s);
 }
 
 // Gauss-Legendre rule on [0,1]: the textbook 4-point abscissae z and

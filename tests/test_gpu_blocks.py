@@ -5,8 +5,11 @@ FP64 bursts in one batch, two increments (the first with one block above the
 holding at one block).
 
 The rates are differences of two running averages a fraction of a percent
-apart, so each is held to max(1e-8, 10 x the oracle's own one-ulp floor)
-(the oracle started from positions moved by one ulp), computed here."""
+apart.  The oracle started from positions moved by one ulp gives the effect
+of ONE rounding-sized perturbation at the start (the floor); the GPU and the
+oracle round differently at every DD step, and each of those perturbations
+grows no more than the one at the start, so each record is held to
+max(1e-8, floor x the DD steps run so far), computed here."""
 
 import dataclasses
 
@@ -50,14 +53,16 @@ def test_block_driver_matches_oracle():
     ref_p = _oracle(net, np.nextafter(net.xyz, np.inf), q, incs)
     assert ref[0]["mag"][2] == 1.0 and ref[0]["mag"][0] > 1 and np.all(ref[1]["mag"] > 1)
     assert list(ref[1]["limit"]) == [False, False, True]
+    steps = 0
     for k, (g, r, rp) in enumerate(zip(got, ref, ref_p)):
         assert g["chunks"] == r["chunks"], k
+        steps += sum(r["chunks"]) * p.chunk
         assert np.array_equal(g["limit"], r["limit"])
         assert np.allclose(g["mag"], r["mag"], rtol=1e-13)
         for key in ("R_prev", "R_t", "Lpdot", "Lp"):
             for blk in range(3):
                 floor = _rel(rp[key][blk], r[key][blk]) if np.linalg.norm(r[key][blk]) > 0 else 0.0
-                tol = max(1e-8, 10 * floor)
+                tol = max(1e-8, steps * floor)
                 if np.linalg.norm(r[key][blk]) == 0:
                     assert np.linalg.norm(g[key][blk]) == 0, (k, key, blk)
                 else:
