@@ -317,6 +317,50 @@ ptadd_status ptadd_closure_realisation(const ptadd_material* mat, uint64_t seed,
  * PTADD_ERR_ARG on NULL T/Lp, V without alpha, or non-finite values. */
 ptadd_status ptadd_dissipation_projection(const double T6[6], const double alpha[9], double Lp[9], double V[3]);
 
+/* Junctions and thermally activated breaking in the burst (Sec. 2.2).
+ * Sessile segments are those whose two nodes are pinned.  In every step of
+ * ptadd_advance, before the Euler update, each free node:
+ *   - releases its junction when the DD clock has reached its break time;
+ *   - if it holds none, forms one with the lowest-index sessile segment of
+ *     another loop within capture_radius, except segments of the sessile
+ *     loop it last broke away from; the junction breaks after t_b = f a
+ *     (Eq. 2.2), a = max_break_time, f in [0,1) the top 53 bits of
+ *     SplitMix64 output k+1 of the stream seeded with
+ *     seed ^ (node * 0xD1B54A32D192ED03) for the node's k-th junction;
+ *   - holds still (velocity 0) while it holds a junction.
+ * After the update the clock advances by dt; when some junction is held and
+ * no free node moved more than stuck_disp in the step, the clock instead
+ * jumps to the earliest break time.  Over a jump the network is frozen: Lp
+ * is 0 and rho keeps the step's value, and the averages of ptadd_advance
+ * divide by the steps' time plus the jumps (Eq. 2.5).
+ * p = NULL switches junctions off.  Setting them (again) clears every
+ * junction and sets the clock to 0.  ptadd_set_network switches them off.
+ * The state blob of ptadd_get_state carries the junction state while they
+ * are on.  Single-realisation API only (not the batch).  PTADD_ERR_ARG on
+ * negative or non-finite parameters; PTADD_ERR_STATE without a network. */
+typedef struct {
+    double capture_radius;  /* m */
+    double max_break_time;  /* a, s */
+    double stuck_disp;      /* m per step */
+    uint64_t seed;
+} ptadd_junction_params;
+ptadd_status ptadd_set_junctions(ptadd_ctx* ctx, const ptadd_junction_params* p);
+
+typedef struct {
+    double clock;     /* DD time since ptadd_set_junctions, s */
+    double jumped;    /* time skipped while stuck, s */
+    int64_t held;     /* junctions held now */
+    int64_t formed;   /* junctions formed since ptadd_set_junctions */
+    int64_t broken;
+    int64_t jumps;
+} ptadd_junction_info;
+/* Junction state; the per-node arrays (caller-owned, n_nodes each, any may
+ * be NULL): seg = held sessile segment or -1, last = sessile loop last
+ * broken from or -1, count = junctions formed, break_time (s).
+ * PTADD_ERR_STATE when junctions are off. */
+ptadd_status ptadd_get_junctions(ptadd_ctx* ctx, ptadd_junction_info* info, int32_t* seg, int32_t* last,
+                                 int32_t* count, double* break_time);
+
 /* Block stress average of the coupling (Sec. 4.2, the stress-averaging
  * block; host only, no GPU): <T>_r = sum_{g in r} w_g T_g / sum_{g in r} w_g
  * over the Gauss points g of block r.  T6[6g..]: stress at point g (Voigt

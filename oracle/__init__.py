@@ -19,7 +19,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ptadd_oracle.c")
-_SRCS = [_SRC, os.path.join(_HERE, "mlp_oracle.c")]
+_SRCS = [_SRC, os.path.join(_HERE, "mlp_oracle.c"), os.path.join(_HERE, "junction_oracle.c")]
 _LIBDIR = os.path.join(_HERE, "_lib")
 _LIB = os.path.join(_LIBDIR, "liboracle.so")
 _lib = None
@@ -67,6 +67,17 @@ def _load():
                                   ctypes.c_double, _D, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
                                   _D, _D, _D, _D, _D]
         lib.orc_burst.restype = ctypes.c_int
+        _I32 = ctypes.POINTER(ctypes.c_int32)
+        lib.orc_splitmix64_mix.argtypes = [ctypes.c_uint64]
+        lib.orc_splitmix64_mix.restype = ctypes.c_uint64
+        lib.orc_junction_fraction.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64]
+        lib.orc_junction_fraction.restype = ctypes.c_double
+        lib.orc_point_segment_dist2.argtypes = [_D, _D, _D]
+        lib.orc_point_segment_dist2.restype = ctypes.c_double
+        lib.orc_burst_junctions.argtypes = [_D, ctypes.c_int64, _D, ctypes.c_int64, _I64, _D, _D, _U8,
+                                            ctypes.c_double, _D, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                                            _D, ctypes.c_uint64, _I32, _I32, _I32, _D, _D, _I64, _D, _D, _D, _D]
+        lib.orc_burst_junctions.restype = ctypes.c_int
         lib.orc_num_threads.restype = ctypes.c_int
         lib.orc_gelu.argtypes = [ctypes.c_double]
         lib.orc_gelu.restype = ctypes.c_double
@@ -245,6 +256,61 @@ def burst(mat, net, n_steps, dt, interactions=True, trace=False):
         out["Lp_trace"] = tL[:n_steps].reshape(-1, 3, 3)
         out["rho_trace"] = tr[:n_steps]
     return out
+
+
+# ------------------------------------------------------------ junctions
+def splitmix64_mix(z):
+    return int(_load().orc_splitmix64_mix(ctypes.c_uint64(z & 0xFFFFFFFFFFFFFFFF)))
+
+
+def junction_fraction(seed, node, k):
+    return float(_load().orc_junction_fraction(ctypes.c_uint64(seed), int(node), int(k)))
+
+
+def point_segment_dist2(x, x1, x2):
+    x, px = _d(x)
+    x1, p1 = _d(x1)
+    x2, p2 = _d(x2)
+    return float(_load().orc_point_segment_dist2(px, p1, p2))
+
+
+def junction_state(n_nodes):
+    """Fresh junction state: nothing held, clock 0."""
+    return dict(seg=np.full(n_nodes, -1, np.int32), last=np.full(n_nodes, -1, np.int32),
+                count=np.zeros(n_nodes, np.int32), brk=np.zeros(n_nodes), clock=np.zeros(2),
+                counts=np.zeros(3, np.int64))
+
+
+def burst_junctions(mat, net, n_steps, dt, capture_radius, max_break_time, stuck_disp, seed, state=None,
+                    interactions=True):
+    """n_steps DD steps with junctions and thermally activated breaking
+    (Sec. 2.2, readings in junction_oracle.c).  `state` (from
+    junction_state() or a previous call) is updated in place.  Returns
+    dict(xyz, Lp_avg, rho_avg, S_t, state, status)."""
+    lib = _load()
+    st = junction_state(net.n_nodes) if state is None else state
+    m, mp = _mat(mat)
+    x, px = _d(net.xyz)
+    off, poff = _i(net.loop_off)
+    bv, pb = _d(net.burgers)
+    nv, pn = _d(net.normal)
+    pin, ppin = _u8(net.pinned)
+    sg, ps = _d(net.sig_app)
+    jp, pj = _d([capture_radius, max_break_time, stuck_disp])
+    _I32 = ctypes.POINTER(ctypes.c_int32)
+    for k, dt_ in (("seg", np.int32), ("last", np.int32), ("count", np.int32), ("brk", np.float64),
+                   ("clock", np.float64), ("counts", np.int64)):
+        st[k] = np.ascontiguousarray(st[k], dtype=dt_)
+    xo = np.zeros((net.n_nodes, 3))
+    Lp = np.zeros(9)
+    rho, S_t = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    rc = lib.orc_burst_junctions(mp, net.n_nodes, px, net.n_loops, poff, pb, pn, ppin, float(net.volume), ps,
+                                 int(bool(interactions)), int(n_steps), float(dt), pj, ctypes.c_uint64(seed),
+                                 st["seg"].ctypes.data_as(_I32), st["last"].ctypes.data_as(_I32),
+                                 st["count"].ctypes.data_as(_I32), st["brk"].ctypes.data_as(_D),
+                                 st["clock"].ctypes.data_as(_D), st["counts"].ctypes.data_as(_I64),
+                                 xo.ctypes.data_as(_D), Lp.ctypes.data_as(_D), ctypes.byref(rho), ctypes.byref(S_t))
+    return dict(xyz=xo, Lp_avg=Lp.reshape(3, 3), rho_avg=rho.value, S_t=S_t.value, state=st, status=rc)
 
 
 # ------------------------------------------------------------------ MLP

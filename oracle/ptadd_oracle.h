@@ -110,6 +110,28 @@ void orc_adam_step(int64_t n, double* p, const double* g, double* m, double* v, 
 /* Number of OpenMP threads the oracle uses (for reporting). */
 int orc_num_threads(void);
 
+/* Junctions and thermally activated breaking (Sec. 2.2; junction_oracle.c).
+ * SplitMix64 output mix (Vigna) and the break fraction f of the k-th
+ * junction of a node, in [0, 1). */
+uint64_t orc_splitmix64_mix(uint64_t z);
+double orc_junction_fraction(uint64_t seed, int64_t node, int64_t k);
+/* squared distance from x to the segment x1 -> x2 */
+double orc_point_segment_dist2(const double x[3], const double x1[3], const double x2[3]);
+/* n_steps DD steps with junctions: jpar = {capture radius r_c (m), maximum
+ * breaking time a (s), stuck displacement (m)}.  Junction state per node
+ * (in/out): jseg (held sessile segment or -1), jlast (sessile loop last
+ * broken from or -1), jcount (junctions formed), jbreak (break time, s);
+ * clock = {DD time t, total time jumped} (s, in/out); counts = {formed,
+ * broken, jumps} (in/out).  Lp_avg, rho_avg: Eq. 2.5 over the burst's
+ * S_t = n_steps dt + the jumps (S_t_out).  Returns 0, or -1 on a
+ * non-finite sample. */
+int orc_burst_junctions(const double mat[5], int64_t n_nodes, const double* xyz, int64_t n_loops,
+                        const int64_t* loop_off, const double* burgers, const double* normal,
+                        const uint8_t* pinned, double volume, const double sig_app[6], int interactions,
+                        int64_t n_steps, double dt, const double jpar[3], uint64_t seed, int32_t* jseg,
+                        int32_t* jlast, int32_t* jcount, double* jbreak, double clock[2], int64_t counts[3],
+                        double* xyz_out, double Lp_avg[9], double* rho_avg, double* S_t_out);
+
 #ifdef __cplusplus
 }
 #endif

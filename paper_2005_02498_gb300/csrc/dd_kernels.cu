@@ -279,6 +279,7 @@ __global__ void lp_finish_kernel(int nblk, const double* __restrict__ partial, d
         __syncthreads();
     }
     if (threadIdx.x < 10) acc[threadIdx.x] = fma(red[0][threadIdx.x], dt, acc[threadIdx.x]);
+    if (threadIdx.x == 9) acc[11] = red[0][9];  // the step's line length (junction jumps weight it)
 }
 
 cudaError_t launch_lp_euler(DevNetwork& net, double dt_hat, cudaStream_t st)

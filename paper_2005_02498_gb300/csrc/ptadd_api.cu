@@ -118,6 +118,7 @@ void ptadd_destroy(ptadd_ctx* ctx)
     free_network(ctx->net);
     batch_free(ctx);
     mlp_free(ctx);
+    junctions_free(ctx);
     for (auto& e : ctx->ev_open) {
         cudaEventDestroy(e.first);
         cudaEventDestroy(e.second);
@@ -175,6 +176,7 @@ ptadd_status ptadd_set_network(ptadd_ctx* ctx, int64_t n_nodes, const double* xy
             if (!isfinite(burgers[3 * k + c])) return arg_error("non-finite Burgers vector");
     }
 
+    junctions_free(ctx);
     free_network(ctx->net);
     ctx->have_net = false;
     DevNetwork& net = ctx->net;
@@ -375,21 +377,30 @@ ptadd_status ptadd_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, double Lp
     for (int64_t it = 0; it < n_steps; ++it) {
         ptadd_status st = eval_forces(ctx, net.tgt_burst, net.n_tgt_burst);
         if (st != PTADD_OK) return st;
+        if (ctx->junc) {
+            PTADD_CUDA(launch_junction_update(ctx, s));
+            ctx->kernel_launches += 1;
+        }
         PTADD_CUDA(launch_lp_euler(net, dt_hat, s));
         ctx->kernel_launches += 2;
+        if (ctx->junc) {
+            PTADD_CUDA(launch_junction_event(ctx, dt, dt_hat, s));
+            ctx->kernel_launches += 1;
+        }
     }
-    double acc[10];
+    double acc[13];
     int flag = 0;
-    PTADD_CUDA(cudaMemcpyAsync(acc, net.acc, 10 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PTADD_CUDA(cudaMemcpyAsync(acc, net.acc, 13 * sizeof(double), cudaMemcpyDeviceToHost, s));
     PTADD_CUDA(cudaMemcpyAsync(&flag, net.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     PTADD_CUDA(cudaStreamSynchronize(s));
     {
         ptadd_status st = drain_events(ctx);
         if (st != PTADD_OK) return st;
     }
-    // Eq. 2.5 with internal sums: R = (sum Lambda_hat dt_hat) / (sum dt_hat), then SI scale
+    // Eq. 2.5 with internal sums: R = (sum Lambda_hat dt_hat) / (sum dt_hat), then SI scale; the
+    // time jumped over while stuck (junctions) counts with Lp = 0 and the step's rho
     const double l = ctx->len_unit;
-    const double St = dt_hat * (double)n_steps;
+    const double St = dt_hat * (double)n_steps + (ctx->junc ? acc[12] : 0.0);
     const double lp_scale = l * l * l * ctx->mat.mu / (ctx->mat.B * net.volume);
     const double rho_scale = l / net.volume;
     bool finite = (flag == 0);
@@ -541,8 +552,10 @@ ptadd_status ptadd_get_forces_dev(ptadd_ctx* ctx, double* F_dev)
     return PTADD_OK;
 }
 
-// state blob: magic, n_nodes, then 3n doubles (internal units, SoA)
+// state blob: magic, n_nodes, then 3n doubles (internal units, SoA); with
+// junctions on, a second magic and the junction state follow
 static const uint64_t STATE_MAGIC = 0x5054414444535431ull;  // "PTADDST1"
+static const uint64_t JUNC_MAGIC = 0x5054414444534A31ull;   // "PTADDSJ1"
 
 ptadd_status ptadd_get_state(ptadd_ctx* ctx, void* buf, size_t* bytes)
 {
@@ -553,7 +566,8 @@ ptadd_status ptadd_get_state(ptadd_ctx* ctx, void* buf, size_t* bytes)
     }
     if (!bytes) return arg_error("bytes is NULL");
     const int64_t n = ctx->net.n_nodes;
-    const size_t need = 2 * sizeof(uint64_t) + 3 * n * sizeof(double);
+    const size_t base = 2 * sizeof(uint64_t) + 3 * n * sizeof(double);
+    const size_t need = base + (ctx->junc ? sizeof(uint64_t) + junction_state_bytes(ctx) : 0);
     if (!buf) {
         *bytes = need;
         return PTADD_OK;
@@ -564,6 +578,11 @@ ptadd_status ptadd_get_state(ptadd_ctx* ctx, void* buf, size_t* bytes)
     PTADD_CUDA(cudaMemcpyAsync((char*)buf + sizeof(hdr), ctx->net.pos[ctx->net.cur], 3 * n * sizeof(double),
                                cudaMemcpyDeviceToHost, ctx->stream));
     PTADD_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (ctx->junc) {
+        memcpy((char*)buf + base, &JUNC_MAGIC, sizeof(uint64_t));
+        ptadd_status st = junction_state_get(ctx, (char*)buf + base + sizeof(uint64_t));
+        if (st != PTADD_OK) return st;
+    }
     *bytes = need;
     return PTADD_OK;
 }
@@ -577,14 +596,22 @@ ptadd_status ptadd_set_state(ptadd_ctx* ctx, const void* buf, size_t bytes)
     }
     if (!buf) return arg_error("buf is NULL");
     const int64_t n = ctx->net.n_nodes;
-    const size_t need = 2 * sizeof(uint64_t) + 3 * n * sizeof(double);
+    const size_t base = 2 * sizeof(uint64_t) + 3 * n * sizeof(double);
+    const size_t need = base + (ctx->junc ? sizeof(uint64_t) + junction_state_bytes(ctx) : 0);
     uint64_t hdr[2];
-    if (bytes != need) return arg_error("state size does not match the loaded network");
+    if (bytes != need)
+        return arg_error("state size does not match the loaded network (or junctions are on in one and off in the other)");
     memcpy(hdr, buf, sizeof(hdr));
     if (hdr[0] != STATE_MAGIC || hdr[1] != (uint64_t)n) return arg_error("state blob does not match the network");
+    if (ctx->junc) {
+        uint64_t jm;
+        memcpy(&jm, (const char*)buf + base, sizeof(jm));
+        if (jm != JUNC_MAGIC) return arg_error("state blob holds no junction state");
+    }
     PTADD_CUDA(cudaMemcpyAsync(ctx->net.pos[ctx->net.cur], (const char*)buf + sizeof(hdr), 3 * n * sizeof(double),
                                cudaMemcpyHostToDevice, ctx->stream));
     PTADD_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (ctx->junc) return junction_state_set(ctx, (const char*)buf + base + sizeof(uint64_t));
     return PTADD_OK;
 }
 

@@ -76,7 +76,8 @@ struct DevNetwork {
     double* force = nullptr;       // SoA [3*n] (last evaluated nodal force)
     double* partial = nullptr;     // [max_blocks*10]
     int max_red_blocks = 0;
-    double* acc = nullptr;         // [16]: 0..8 sum Lp dt, 9 sum rho dt, 10 flag
+    double* acc = nullptr;         // [16]: 0..8 sum Lp dt, 9 sum rho dt, 11 line length of the last
+                                   // step, 12 time jumped over while stuck (junctions)
     int* flag = nullptr;           // non-finite flag
     double* staging = nullptr;     // [3*n] AoS SI positions in / out
     double volume = 0;             // m^3
@@ -104,6 +105,20 @@ int choose_chunks(int64_t n_tgt, int64_t n_src, int max_chunks, int precision);
 // peak microbenchmark
 cudaError_t launch_fma_chains(int fp64, int blocks, int threads, long iters, double* sink, cudaStream_t st);
 
+// junctions and thermally activated breaking (junctions.cu)
+struct DevJunctions;
+void junctions_free(ptadd_ctx* ctx);
+// before the Euler stage of a step: release due junctions, form new ones,
+// hold the velocities of held nodes, reduce the stuck test's inputs
+cudaError_t launch_junction_update(ptadd_ctx* ctx, cudaStream_t st);
+// after it: advance the DD clock by dt_s, or to the next break when stuck
+// (adding the frozen interval to the rho and time sums in net.acc)
+cudaError_t launch_junction_event(ptadd_ctx* ctx, double dt_s, double dt_hat, cudaStream_t st);
+// junction part of the state blob
+size_t junction_state_bytes(const ptadd_ctx* ctx);
+ptadd_status junction_state_get(ptadd_ctx* ctx, char* dst);
+ptadd_status junction_state_set(ptadd_ctx* ctx, const char* src);
+
 struct DevBatch;
 void batch_free(ptadd_ctx* ctx);
 struct MlpDev;
@@ -123,6 +138,7 @@ struct ptadd_ctx {
     bool have_net = false;
     ptadd::DevBatch* batch = nullptr;  // batched ensemble (ptadd_batch_*)
     ptadd::MlpDev* mlp = nullptr;      // surrogate (ptadd_mlp_* / ptadd_surrogate_*)
+    ptadd::DevJunctions* junc = nullptr;  // junctions (ptadd_set_junctions), NULL: off
     double sig_app[6] = {0, 0, 0, 0, 0, 0};  // Pa
     // profiling (ptadd_profile_*)
     bool timing = false;

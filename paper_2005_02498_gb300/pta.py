@@ -90,11 +90,16 @@ def _converge(ctx, sigma, p):
     return avg
 
 
-def run(ctx, net, p, slow_steps):
-    """Run `slow_steps` slow steps; returns one record per step."""
+def run(ctx, net, p, slow_steps, junctions=None):
+    """Run `slow_steps` slow steps; returns one record per step.
+    junctions: keyword arguments of Context.set_junctions (junctions and
+    thermally activated breaking in every burst; their state is carried
+    from burst to burst with the positions), or None."""
     pattern = np.asarray(p.pattern, float)
     load = lambda t: p.rate * (t + p.delta) * pattern  # noqa: E731
     ctx.set_network(net)
+    if junctions is not None:
+        ctx.set_junctions(**junctions)
     state = ctx.get_state()
     t, h = 0.0, p.h0
     out = []

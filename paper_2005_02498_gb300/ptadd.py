@@ -32,7 +32,7 @@ EXPORTS = ["ptadd_version", "ptadd_create", "ptadd_destroy", "ptadd_last_error",
            "ptadd_mlp_get_params", "ptadd_mlp_loss_grad", "ptadd_mlp_train", "ptadd_mlp_forward",
            "ptadd_surrogate_fit", "ptadd_surrogate_predict", "ptadd_surrogate_predict_dev",
            "ptadd_closure_sweep", "ptadd_closure_realisation", "ptadd_dissipation_projection",
-           "ptadd_block_average", "ptadd_block_stress_pair",
+           "ptadd_block_average", "ptadd_block_stress_pair", "ptadd_set_junctions", "ptadd_get_junctions",
            "ptadd_surrogate_get_state", "ptadd_surrogate_set_state"]
 NOALLOC_MAX_SEGMENTS = 16384
 
@@ -58,6 +58,16 @@ class BatchInfo(ctypes.Structure):
     _fields_ = [("R", ctypes.c_int32), ("n_nodes", ctypes.c_int64), ("n_loops", ctypes.c_int64),
                 ("n_targets", ctypes.c_int64), ("pairs_per_step", ctypes.c_int64), ("work_items", ctypes.c_int64),
                 ("tile_targets", ctypes.c_int32), ("chunk_sources", ctypes.c_int32), ("tuned", ctypes.c_int32)]
+
+
+class JunctionParams(ctypes.Structure):
+    _fields_ = [("capture_radius", ctypes.c_double), ("max_break_time", ctypes.c_double),
+                ("stuck_disp", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class JunctionInfo(ctypes.Structure):
+    _fields_ = [("clock", ctypes.c_double), ("jumped", ctypes.c_double), ("held", ctypes.c_int64),
+                ("formed", ctypes.c_int64), ("broken", ctypes.c_int64), ("jumps", ctypes.c_int64)]
 
 
 class Info(ctypes.Structure):
@@ -172,6 +182,11 @@ def load(build_if_missing=True):
     lib.ptadd_closure_realisation.restype = st
     lib.ptadd_dissipation_projection.argtypes = [_D, _D, _D, _D]
     lib.ptadd_dissipation_projection.restype = st
+    _I32 = ctypes.POINTER(ctypes.c_int32)
+    lib.ptadd_set_junctions.argtypes = [_VP, ctypes.POINTER(JunctionParams)]
+    lib.ptadd_set_junctions.restype = st
+    lib.ptadd_get_junctions.argtypes = [_VP, ctypes.POINTER(JunctionInfo), _I32, _I32, _I32, _D]
+    lib.ptadd_get_junctions.restype = st
     lib.ptadd_block_average.argtypes = [ctypes.c_int64, _D, _D, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _D]
     lib.ptadd_block_average.restype = st
     lib.ptadd_block_stress_pair.argtypes = [ctypes.c_int32, _D, _D, ctypes.c_double, ctypes.c_double,
@@ -429,6 +444,29 @@ class Context:
     def set_state(self, blob):
         buf = ctypes.create_string_buffer(blob, len(blob))
         _check(self._lib.ptadd_set_state(self._h, ctypes.cast(buf, _VP), len(blob)))
+
+    # ---------------------------------------------------------- junctions
+    def set_junctions(self, capture_radius=None, max_break_time=1e-3, stuck_disp=0.0, seed=0):
+        """ptadd_set_junctions; capture_radius None switches junctions off."""
+        if capture_radius is None:
+            _check(self._lib.ptadd_set_junctions(self._h, None))
+            return
+        p = JunctionParams(float(capture_radius), float(max_break_time), float(stuck_disp), int(seed))
+        _check(self._lib.ptadd_set_junctions(self._h, ctypes.byref(p)))
+
+    def junctions(self):
+        """ptadd_get_junctions: dict(clock, jumped, held, formed, broken,
+        jumps, seg, last, count, break_time)."""
+        n = self.info()["n_nodes"]
+        info = JunctionInfo()
+        seg, last, cnt = (np.zeros(n, np.int32) for _ in range(3))
+        brk = np.zeros(n)
+        i32 = ctypes.POINTER(ctypes.c_int32)
+        _check(self._lib.ptadd_get_junctions(self._h, ctypes.byref(info), seg.ctypes.data_as(i32),
+                                             last.ctypes.data_as(i32), cnt.ctypes.data_as(i32), _dptr(brk)))
+        out = {k: getattr(info, k) for k, _ in JunctionInfo._fields_}
+        out.update(seg=seg, last=last, count=cnt, break_time=brk)
+        return out
 
     # ------------------------------------------------------------ batched
     def batch_set(self, batch):

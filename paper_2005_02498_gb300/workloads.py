@@ -418,3 +418,32 @@ def realisation_for_densities(rng, sig6, rho_m, rho_s, n_loops=32, nodes_per_loo
     xyz, off, bv, nv = _loops_with_systems(rng, systems, edge, nodes_per_loop, r_min, r_max, radius, sense)
     pin = np.repeat((cls >= 12).astype(np.uint8), nodes_per_loop)
     return Network(xyz, off, bv, nv, pin, edge ** 3, np.asarray(sig6, float).copy())
+
+
+# --------------------------------------------------------------------------
+# The paper's microstructure recipe (Sec. 3.2.1) on glide loops: mobile line
+# density shared among the slip systems in proportion to |Schmid factor|,
+# sessile density spread evenly over the 12 systems (rho_s >> rho_m), every
+# loop carrying both line senses (net density 0), sessile loops pinned.
+# --------------------------------------------------------------------------
+def schmid_factors(sig6):
+    """f_i = b_i . (sigma n_i) / |sigma| for the 12 FCC systems (|sigma| the
+    Frobenius norm of the full tensor), Sec. 3.2.1."""
+    s = np.asarray(sig6, float)
+    S = np.array([[s[0], s[5], s[4]], [s[5], s[1], s[3]], [s[4], s[3], s[2]]])
+    bh, nh = fcc_slip_systems()
+    return np.einsum("ki,ij,kj->k", bh, S, nh) / np.linalg.norm(S)
+
+
+def junction_microstructure(seed, sig6, rho_m, rho_s, n_loops=64, nodes_per_loop=32,
+                            r_min=0.05 * MICRON, r_max=0.2 * MICRON):
+    """One realisation of the paper's recipe with n_loops glide loops:
+    mobile density rho_m (1/m^2) per system in proportion to |f_i|, sessile
+    density rho_s evenly over the systems; class counts, radii and senses
+    stratified as in realisation_for_densities."""
+    f = np.abs(schmid_factors(sig6))
+    rho_mi = rho_m * f / f.sum()
+    rho_si = np.full(12, rho_s / 12.0)
+    rng = np.random.default_rng(seed)
+    return realisation_for_densities(rng, sig6, rho_mi, rho_si, n_loops, nodes_per_loop, r_min, r_max,
+                                     stratified=True)
