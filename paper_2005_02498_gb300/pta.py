@@ -139,11 +139,21 @@ def main(argv=None):
     ap.add_argument("--slow-steps", type=int, default=5)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--device", type=int, default=0)
+    ap.add_argument("--orientation", default="crystal", choices=["crystal", "tension", "shear"],
+                    help="crystal: uniaxial [001] in the crystal frame; tension / shear: the paper's uniaxial X "
+                         "tension or XY simple shear in the laboratory frame, rotated into the crystal by the "
+                         "Appendix's C2G matrices")
     a = ap.parse_args(argv)
     prec = ptadd.PTADD_FP64 if a.precision == "fp64" else ptadd.PTADD_MIXED
+    p = PTAParams()
+    if a.orientation == "tension":
+        p.pattern = tuple(W.global_to_crystal_stress((1, 0, 0, 0, 0, 0), W.c2g_matrix(*W.C2G_TENSION)))
+    elif a.orientation == "shear":
+        p.pattern = tuple(W.global_to_crystal_stress((0, 0, 0, 0, 0, 1), W.c2g_matrix(*W.C2G_SHEAR)))
     with ptadd.Context(W.Material().as_tuple(), prec, a.device) as ctx:
-        recs = run(ctx, W.small_loop_network(), PTAParams(), a.slow_steps)
-    print(json.dumps({"workload": "16 loops, 512 segments", "precision": a.precision, "steps": recs}))
+        recs = run(ctx, W.small_loop_network(), p, a.slow_steps)
+    print(json.dumps({"workload": "16 loops, 512 segments", "precision": a.precision,
+                      "orientation": a.orientation, "pattern": list(p.pattern), "steps": recs}))
     return 0
 
 

@@ -447,3 +447,35 @@ def junction_microstructure(seed, sig6, rho_m, rho_s, n_loops=64, nodes_per_loop
     rng = np.random.default_rng(seed)
     return realisation_for_densities(rng, sig6, rho_mi, rho_si, n_loops, nodes_per_loop, r_min, r_max,
                                      stratified=True)
+
+
+# --------------------------------------------------------------------------
+# Crystal-to-global frames (Appendix): A_ki = e_k . e^_i, so that global
+# components are g = A c; its rows are the unit crystallographic directions
+# that lie along the global X, Y and Z = X x Y axes.  The DD box works in the
+# crystal frame, so a stress given in the laboratory frame enters as
+# sigma_crystal = A^T sigma_global A.
+# --------------------------------------------------------------------------
+C2G_TENSION = ((0, -1, 1), (2, 1, 1))   # symmetric double slip, uniaxial tension (Sec. 3.3.1)
+C2G_SHEAR = ((0, 1, 1), (-1, 1, -1))    # simple shear orientation (Sec. 3.3.2)
+
+
+def c2g_matrix(x_dir, y_dir):
+    """C2G matrix with the crystal direction x_dir along global X and y_dir
+    (perpendicular to it) along global Y."""
+    x = np.asarray(x_dir, float)
+    y = np.asarray(y_dir, float)
+    if abs(x @ y) > 1e-12 * np.linalg.norm(x) * np.linalg.norm(y):
+        raise ValueError("the two crystal directions must be perpendicular")
+    x = x / np.linalg.norm(x)
+    y = y / np.linalg.norm(y)
+    return np.array([x, y, np.cross(x, y)])
+
+
+def global_to_crystal_stress(sig6_global, A):
+    """Voigt stress in the laboratory frame -> Voigt stress in the crystal
+    frame of the C2G matrix A."""
+    s = np.asarray(sig6_global, float)
+    S = np.array([[s[0], s[5], s[4]], [s[5], s[1], s[3]], [s[4], s[3], s[2]]])
+    C = A.T @ S @ A
+    return np.array([C[0, 0], C[1, 1], C[2, 2], C[1, 2], C[0, 2], C[0, 1]])

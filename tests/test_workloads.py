@@ -1,5 +1,7 @@
 """Host-side checks of the seeded input generators (no GPU, no oracle)."""
 
+import math
+
 import numpy as np
 
 from paper_2005_02498_gb300 import workloads as W
@@ -205,3 +207,36 @@ def test_native_closure_realisation_rejects_bad_arguments():
         ptadd.closure_realisation(mat, 1, good, 0)
     with pytest.raises(ptadd.PtaddError):
         ptadd.closure_realisation((48e9, 0.34, 0.0, 2.556e-10, 1e-4), 1, good, 8)  # b = 0
+
+
+def _golden_matrix(key):
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_magnitudes.json")))
+    return np.array([[eval(e, {"sqrt": math.sqrt}) for e in r] for r in gold[key]["rows"]])
+
+
+def test_c2g_matrices_are_the_papers_and_rotate_the_load_into_the_crystal():
+    for dirs, key in ((W.C2G_TENSION, "c2g_tension"), (W.C2G_SHEAR, "c2g_shear")):
+        A = W.c2g_matrix(*dirs)
+        assert np.allclose(A, _golden_matrix(key), rtol=0, atol=1e-15)
+        assert np.allclose(A @ A.T, np.eye(3), atol=1e-15) and abs(np.linalg.det(A) - 1) < 1e-15
+    # uniaxial tension along global X: in the crystal, sigma (c1 x c1) with c1 = [0 -1 1]/sqrt(2);
+    # the symmetric double slip orientation loads 4 systems on two {111} planes at 1/sqrt(6)
+    A = W.c2g_matrix(*W.C2G_TENSION)
+    sc = W.global_to_crystal_stress([100e6, 0, 0, 0, 0, 0], A)
+    c1 = np.array([0, -1, 1]) / math.sqrt(2)
+    full = np.array([[sc[0], sc[5], sc[4]], [sc[5], sc[1], sc[3]], [sc[4], sc[3], sc[2]]])
+    assert np.allclose(full, 100e6 * np.outer(c1, c1), rtol=0, atol=1e-7)
+    f = W.schmid_factors(sc)
+    on = np.isclose(np.abs(f), 1 / math.sqrt(6), rtol=1e-12)
+    assert on.sum() == 4 and np.allclose(f[~on], 0, atol=1e-15)
+    bh, nh = W.fcc_slip_systems()
+    assert len({tuple(np.round(n * math.sqrt(3)).astype(int)) for n in nh[on]}) == 2
+    # simple shear in the global XY plane: all of it on the one system with b along X and n along Y
+    B = W.c2g_matrix(*W.C2G_SHEAR)
+    f = W.schmid_factors(W.global_to_crystal_stress([0, 0, 0, 0, 0, 50e6], B))
+    k = int(np.argmax(np.abs(f)))
+    assert math.isclose(abs(f[k]), 1 / math.sqrt(2), rel_tol=1e-12)
+    assert np.sum(np.abs(f) > 0.7) == 1
+    assert abs(abs(bh[k] @ B[0]) - 1) < 1e-12 and abs(abs(nh[k] @ B[1]) - 1) < 1e-12
