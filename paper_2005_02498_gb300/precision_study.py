@@ -8,7 +8,7 @@ FP64, mixed (FP32 far field, FP64 near field and integration), and FP64 from
 positions moved by one ulp.  The last one measures how far the trajectory
 itself amplifies rounding: at 1e-11 s explicit Euler is unstable for the
 smaller loops, so two FP64 runs differing by one ulp already disagree, and
-the mixed path can only be judged against that floor.  Reported per dt:
+the mixed path can only be measured against that floor.  Reported per dt:
 the relative (Frobenius) difference of the averaged Lp and the relative
 max-norm difference of the final displacements, mixed vs FP64 and perturbed
 FP64 vs FP64, and the pair evaluations per second of each precision

@@ -10,7 +10,7 @@ class counts, radii and line senses balanced, total density exact), computed
 by batched mixed-precision DD bursts (`--dt`, `--steps`).  Realisations with
 the same input differ, so a single closure is noisy: the network is trained
 on one realisation per training point (it regresses to the conditional
-mean) and judged on `--eval` hold-out points against the mean of
+mean) and scored on `--eval` hold-out points against the mean of
 `--members` realisations.  The spread of single realisations around those
 means gives the noise floor of that reference, and the model error with the
 floor removed is reported beside the raw figure.  Training uses every
@@ -208,7 +208,7 @@ def main(argv=None):
     p.add_argument("--fp64-check", type=int, default=32, help="hold-out points relabelled with FP64 DD")
     p.add_argument("--members", type=int, default=16, help="realisations per hold-out ensemble mean")
     p.add_argument("--loops", type=int, default=128, help="loops per realisation")
-    p.add_argument("--eval", type=int, default=400, help="hold-out points judged against ensemble means")
+    p.add_argument("--eval", type=int, default=400, help="hold-out points scored against ensemble means")
     p.add_argument("--load-data", default=None, help="reuse a labelled set written by --save-data")
     p.add_argument("--infer", type=int, default=1 << 20)
     p.add_argument("--device", type=int, default=0)
@@ -230,7 +230,7 @@ def main(argv=None):
             out["labels_from"] = a.load_data
             out["dd_closures_per_s"] = float(d["dd_closures_per_s"])
         else:
-            # training labels: one realisation per point; the judged hold-out
+            # training labels: one realisation per point; the scored hold-out
             # points: ensemble means and one independent single realisation
             Ytr, t_gen, pairs = generate(ctx, X[:ntr], 1, a.seed + 1, a.steps, a.dt, a.loops)
             Yho, t_ho, _ = generate(ctx, X[ntr:ntr + nev], a.members, a.seed + 2, a.steps, a.dt, a.loops)
