@@ -306,6 +306,20 @@ ptadd_status ptadd_closure_realisation(const ptadd_material* mat, uint64_t seed,
                                        int32_t n_loops, double* xyz, double* burgers, double* normal,
                                        uint8_t* pinned, double* volume);
 
+/* Line density per slip system of one realisation (host only, no GPU): the
+ * observable the closure inputs are made of (mobile and sessile density per
+ * FCC {111}<110> system, Sec. 3.2.1, Sec. 2.4).  rho24[i] (i < 12) =
+ * (1/V) x length of the segments of loops on system i with at least one
+ * free node; rho24[12 + i] the same for segments whose two nodes are
+ * pinned.  Systems in the order of ptadd_closure_realisation; a loop's
+ * system is the one whose Burgers direction and plane normal are parallel
+ * (to 1e-9) to its Burgers vector and glide normal.  Network arrays as in
+ * ptadd_set_network (host, m).  PTADD_ERR_ARG on bad sizes, NULL arrays, a
+ * non-positive volume, non-finite positions or a loop on no FCC system. */
+ptadd_status ptadd_system_densities(int64_t n_nodes, const double* xyz, int64_t n_loops, const int64_t* loop_off,
+                                    const double* burgers, const double* normal, const uint8_t* pinned, double volume,
+                                    double* rho24);
+
 /* Non-negative dissipation at a material point (Sec. 4, "Ensuring
  * non-negative dissipation"; host only, no GPU).  T6: Cauchy stress in
  * Voigt order xx, yy, zz, yz, xz, xy (any unit); Lp[9]: plastic distortion rate, row-major, corrected in

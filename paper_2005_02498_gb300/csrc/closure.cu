@@ -264,4 +264,47 @@ ptadd_status ptadd_closure_sweep(ptadd_ctx* ctx, int64_t n_pts, const double* si
     return PTADD_OK;
 }
 
+ptadd_status ptadd_system_densities(int64_t n_nodes, const double* xyz, int64_t n_loops, const int64_t* loop_off,
+                                    const double* burgers, const double* normal, const uint8_t* pinned, double volume,
+                                    double* rho24)
+{
+    if (n_nodes < 0 || n_loops < 1 || !xyz || !loop_off || !burgers || !normal || !rho24 ||
+        !(volume > 0.0) || !isfinite(volume))
+        return carg("ptadd_system_densities: bad sizes, NULL array or non-positive volume");
+    if (loop_off[0] != 0 || loop_off[n_loops] != n_nodes)
+        return carg("ptadd_system_densities: loop_off must start at 0 and end at n_nodes");
+    double bh[12][3], nh[12][3];
+    fcc_systems(bh, nh);
+    double acc[24] = {0};
+    for (int64_t k = 0; k < n_loops; ++k) {
+        const int64_t s = loop_off[k], e = loop_off[k + 1];
+        if (e - s < 2) return carg("ptadd_system_densities: every loop needs >= 2 nodes");
+        const double* b = burgers + 3 * k;
+        const double* nv = normal + 3 * k;
+        const double bn = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+        const double nn = sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+        int sys = -1;
+        for (int i = 0; i < 12 && bn > 0.0 && nn > 0.0; ++i) {
+            const double cb = fabs(b[0] * bh[i][0] + b[1] * bh[i][1] + b[2] * bh[i][2]) / bn;
+            const double cn = fabs(nv[0] * nh[i][0] + nv[1] * nh[i][1] + nv[2] * nh[i][2]) / nn;
+            if (cb > 1.0 - 1e-9 && cn > 1.0 - 1e-9) sys = i;
+        }
+        if (sys < 0) {
+            set_error("ptadd_system_densities: loop %lld is not on an FCC {111}<110> system", (long long)k);
+            return PTADD_ERR_ARG;
+        }
+        for (int64_t a = s; a < e; ++a) {
+            const int64_t c = (a + 1 < e) ? a + 1 : s;
+            const double dx = xyz[3 * c] - xyz[3 * a], dy = xyz[3 * c + 1] - xyz[3 * a + 1],
+                         dz = xyz[3 * c + 2] - xyz[3 * a + 2];
+            const double L = sqrt(dx * dx + dy * dy + dz * dz);
+            if (!isfinite(L)) return carg("ptadd_system_densities: non-finite node position");
+            const bool sessile = pinned && pinned[a] && pinned[c];
+            acc[(sessile ? 12 : 0) + sys] += L;
+        }
+    }
+    for (int m = 0; m < 24; ++m) rho24[m] = acc[m] / volume;
+    return PTADD_OK;
+}
+
 }  // extern "C"

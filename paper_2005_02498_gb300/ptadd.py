@@ -32,7 +32,7 @@ EXPORTS = ["ptadd_version", "ptadd_create", "ptadd_destroy", "ptadd_last_error",
            "ptadd_mlp_get_params", "ptadd_mlp_loss_grad", "ptadd_mlp_train", "ptadd_mlp_forward",
            "ptadd_surrogate_fit", "ptadd_surrogate_predict", "ptadd_surrogate_predict_dev",
            "ptadd_closure_sweep", "ptadd_closure_realisation", "ptadd_dissipation_projection",
-           "ptadd_block_average", "ptadd_block_stress_pair", "ptadd_set_junctions", "ptadd_get_junctions",
+           "ptadd_block_average", "ptadd_block_stress_pair", "ptadd_set_junctions", "ptadd_get_junctions", "ptadd_system_densities",
            "ptadd_surrogate_get_state", "ptadd_surrogate_set_state"]
 NOALLOC_MAX_SEGMENTS = 16384
 
@@ -187,6 +187,8 @@ def load(build_if_missing=True):
     lib.ptadd_set_junctions.restype = st
     lib.ptadd_get_junctions.argtypes = [_VP, ctypes.POINTER(JunctionInfo), _I32, _I32, _I32, _D]
     lib.ptadd_get_junctions.restype = st
+    lib.ptadd_system_densities.argtypes = [ctypes.c_int64, _D, ctypes.c_int64, _I64, _D, _D, _U8, ctypes.c_double, _D]
+    lib.ptadd_system_densities.restype = st
     lib.ptadd_block_average.argtypes = [ctypes.c_int64, _D, _D, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _D]
     lib.ptadd_block_average.restype = st
     lib.ptadd_block_stress_pair.argtypes = [ctypes.c_int32, _D, _D, ctypes.c_double, ctypes.c_double,
@@ -277,6 +279,22 @@ def dissipation_projection(T6, Lp, V=None, alpha=None):
     _check(lib.ptadd_dissipation_projection(_dptr(t), _dptr(a) if a is not None else None, _dptr(L),
                                             _dptr(v) if v is not None else None))
     return L.reshape(3, 3), v
+
+
+def system_densities(net, xyz=None):
+    """ptadd_system_densities (host only): [24] line densities (1/m^2),
+    12 mobile then 12 sessile, of `net` (positions `xyz` if given)."""
+    lib = load()
+    x = _c(net.xyz if xyz is None else xyz, np.float64)
+    off = _c(net.loop_off, np.int64)
+    bv = _c(net.burgers, np.float64)
+    nv = _c(net.normal, np.float64)
+    pin = _c(net.pinned, np.uint8) if net.pinned is not None else None
+    out = np.zeros(24)
+    _check(lib.ptadd_system_densities(x.shape[0], _dptr(x), off.shape[0] - 1, off.ctypes.data_as(_I64), _dptr(bv),
+                                      _dptr(nv), pin.ctypes.data_as(_U8) if pin is not None else None,
+                                      float(net.volume), _dptr(out)))
+    return out
 
 
 def block_average(T6, w, block, n_blocks):

@@ -240,3 +240,36 @@ def test_c2g_matrices_are_the_papers_and_rotate_the_load_into_the_crystal():
     assert math.isclose(abs(f[k]), 1 / math.sqrt(2), rel_tol=1e-12)
     assert np.sum(np.abs(f) > 0.7) == 1
     assert abs(abs(bh[k] @ B[0]) - 1) < 1e-12 and abs(abs(nh[k] @ B[1]) - 1) < 1e-12
+
+
+def test_native_system_densities_closed_form_and_features():
+    """ptadd_system_densities: regular 32-gon loops have perimeter
+    64 R sin(pi/32) exactly, so each system's density is known in closed
+    form; on a closure realisation it equals the generator's features."""
+    from paper_2005_02498_gb300 import ptadd
+    rng = np.random.default_rng(4)
+    systems = np.array([0, 0, 5, 11, 7])
+    radius = np.array([50e-9, 80e-9, 60e-9, 100e-9, 70e-9])
+    xyz, off, bv, nv = W._loops_with_systems(rng, systems, 1e-6, 32, radius=radius)
+    pin = np.repeat(np.array([0, 0, 0, 1, 1], np.uint8), 32)
+    net = W.Network(xyz, off, bv, nv, pin, 1e-18, np.zeros(6))
+    rho = ptadd.system_densities(net)
+    want = np.zeros(24)
+    for s_, r_, p_ in zip(systems, radius, [0, 0, 0, 1, 1]):
+        want[12 * p_ + s_] += 64 * r_ * math.sin(math.pi / 32) / 1e-18
+    assert np.allclose(rho, want, rtol=1e-12, atol=0)
+    batch, feats = W.closure_ensemble(9, 3)
+    for r in range(3):
+        n0, n1 = int(batch.node_off[r]), int(batch.node_off[r + 1])
+        l0, l1 = int(batch.loop_base[r]), int(batch.loop_base[r + 1])
+        one = W.Network(batch.xyz[n0:n1], batch.loop_off[l0:l1 + 1] - batch.loop_off[l0], batch.burgers[l0:l1],
+                        batch.normal[l0:l1], batch.pinned[n0:n1], float(batch.volume[r]), batch.sig6[r])
+        assert np.allclose(ptadd.system_densities(one), feats[r, 6:], rtol=1e-12, atol=0)
+    bad = net.copy()
+    bad.burgers = bad.burgers.copy()
+    bad.burgers[0] = [1e-10, 2e-10, 0.0]
+    try:
+        ptadd.system_densities(bad)
+        raise AssertionError("a loop off the FCC systems must be rejected")
+    except ptadd.PtaddError:
+        pass
