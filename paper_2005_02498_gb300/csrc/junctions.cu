@@ -16,8 +16,9 @@
 // after the Euler stage:
 //   junction_event_kernel (one thread): t <- t + dt, or, if some junction is
 //     held and no free node moved more than the stuck displacement, t <- the
-//     earliest break time; the frozen interval adds the step's line length
-//     times its length to the rho sum (Lp adds nothing) and to the time sum.
+//     earliest break time; the frozen interval adds (the step's line length)
+//     x (the interval) to the rho sum, nothing to the Lp sum, and the
+//     interval to the time sum.
 // Distances and times are formed with explicit round-to-nearest operations,
 // no contraction, so a decision depends only on the positions and the clock.
 #include <cuda_runtime.h>
@@ -311,14 +312,21 @@ extern "C" ptadd_status ptadd_set_junctions(ptadd_ctx* ctx, const ptadd_junction
     }
     const unsigned long long red0[6] = {0ull, INF_BITS, 0ull, 0ull, 0ull, 0ull};
     const double clock0[2] = {0.0, 0.0};
-    if (!sess.empty())
-        PTADD_CUDA(cudaMemcpy(j->sess, sess.data(), sess.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    PTADD_CUDA(cudaMemset(j->seg, 0xFF, n * sizeof(int32_t)));  // -1
-    PTADD_CUDA(cudaMemset(j->last, 0xFF, n * sizeof(int32_t)));
-    PTADD_CUDA(cudaMemset(j->count, 0, n * sizeof(int32_t)));
-    PTADD_CUDA(cudaMemset(j->brk, 0, n * sizeof(double)));
-    PTADD_CUDA(cudaMemcpy(j->clock, clock0, sizeof(clock0), cudaMemcpyHostToDevice));
-    PTADD_CUDA(cudaMemcpy(j->red, red0, sizeof(red0), cudaMemcpyHostToDevice));
+    auto chk = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
+    };
+    if (!sess.empty()) chk(cudaMemcpy(j->sess, sess.data(), sess.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    chk(cudaMemset(j->seg, 0xFF, n * sizeof(int32_t)));  // -1
+    chk(cudaMemset(j->last, 0xFF, n * sizeof(int32_t)));
+    chk(cudaMemset(j->count, 0, n * sizeof(int32_t)));
+    chk(cudaMemset(j->brk, 0, n * sizeof(double)));
+    chk(cudaMemcpy(j->clock, clock0, sizeof(clock0), cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(j->red, red0, sizeof(red0), cudaMemcpyHostToDevice));
+    if (e != cudaSuccess) {  // leave junctions off rather than half set
+        set_error("ptadd_set_junctions: initialising the junction state failed: %s", cudaGetErrorString(e));
+        junctions_free(ctx);
+        return PTADD_ERR_CUDA;
+    }
     return PTADD_OK;
 }
 
