@@ -348,7 +348,9 @@ ptadd_status ptadd_dissipation_projection(const double T6[6], const double alpha
  * is 0 and rho keeps the step's value, and the averages of ptadd_advance
  * divide by the steps' time plus the jumps (Eq. 2.5).
  * p = NULL switches junctions off.  Setting them (again) clears every
- * junction and sets the clock to 0.  ptadd_set_network switches them off.
+ * junction and sets the clock to 0.  ptadd_set_network switches them off;
+ * ptadd_set_nodes moves nodes and leaves the junctions as they are (a held
+ * node stays held where it was put).
  * The state blob of ptadd_get_state carries the junction state while they
  * are on.  Single-realisation API only (not the batch).  PTADD_ERR_ARG on
  * negative or non-finite parameters; PTADD_ERR_STATE without a network. */
