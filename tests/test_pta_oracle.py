@@ -69,3 +69,43 @@ def test_pta_first_step_is_two_plain_bursts_when_one_chunk_is_allowed():
     n2.sig_app = np.array(p.pattern) * p.rate * p.delta
     r2 = O.burst(MAT, n2, p.chunk, p.dt)
     assert np.array_equal(rec["Lp_prev"], r1["Lp_avg"]) and np.array_equal(rec["Lp"], r2["Lp_avg"])
+
+
+class _StandInContext:
+    """The single-realisation calls pta.run makes, answered by the oracle's
+    burst on the host, so that the product's PTA driver is checked on the CPU
+    against the oracle's independent loop."""
+
+    def set_network(self, net):
+        self.net, self.xyz, self.sig = net, net.xyz.copy(), net.sig_app.copy()
+
+    def set_applied_stress(self, sig6):
+        self.sig = np.asarray(sig6, float).copy()
+
+    def get_state(self):
+        return self.xyz.copy()
+
+    def set_state(self, blob):
+        self.xyz = blob.copy()
+
+    def advance(self, n, dt):
+        m = self.net.copy()
+        m.xyz, m.sig_app = self.xyz, self.sig
+        r = O.burst(MAT, m, n, dt)
+        self.xyz = r["xyz"]
+        return r["Lp_avg"], r["rho_avg"]
+
+
+def test_product_pta_driver_follows_the_oracle_loop():
+    from paper_2005_02498_gb300 import pta
+    for lpdot_max, steps in ((1e30, 3), (0.0, 1)):
+        p = P(lpdot_max=lpdot_max, max_chunks=3, extend_chunks=2)
+        net = W.small_loop_network()
+        got = pta.run(_StandInContext(), net, p, steps)
+        want = OP.run(MAT, net, p, steps)
+        for g, r in zip(got, want):
+            assert (g["jumps"], g["chunks"], g["extended"]) == (r["jumps"], r["chunks"], r["extended"])
+            assert g["t"] == r["t"]
+            for key in ("Lp", "Lp_prev", "Lpdot"):
+                assert np.allclose(g[key], r[key], rtol=1e-12, atol=0), key
+            assert np.isclose(g["rhodot"], r["rhodot"], rtol=1e-9)
