@@ -207,6 +207,23 @@ ptadd_status ptadd_batch_get_info(ptadd_ctx* ctx, ptadd_batch_info* info);
  * the batch's size class.  A cached entry is reused unless force != 0.
  * ptadd_batch_set applies a cached entry when one exists. */
 ptadd_status ptadd_batch_autotune(ptadd_ctx* ctx, const char* cache_path, int force);
+/* Set the pair-stage configuration by hand: tile_targets (threads per
+ * block) 64 or 128, chunk_sources a multiple of 128 in [1024, 2^24].  A
+ * realisation of N nodes is then split into ceil(N / chunk_sources) source
+ * chunks, each a separate work item whose nodal-force parts the node stage
+ * sums in chunk order.  Results equal those of any other configuration up to
+ * the summation order.  Marks the batch untuned (info.tuned = 0).
+ * PTADD_ERR_ARG outside those values, PTADD_ERR_STATE without a batch. */
+ptadd_status ptadd_batch_configure(ptadd_ctx* ctx, int32_t tile_targets, int32_t chunk_sources);
+/* Nodal forces F[n_nodes*3] (N) of every realisation at the current
+ * positions, as the burst's step would evaluate them (Sec. 2.1: the
+ * Peach-Koehler force of the nonsingular stress of all segments of the
+ * realisation plus its applied stress, integrated against the linear shape
+ * functions with the 4-point Gauss rule), in the context's precision.  The
+ * burst does not evaluate segments whose nodes are all pinned (sessile
+ * obstacles, sources only), so the entries of pinned nodes are 0; the
+ * entries of every other node are complete.  Positions are not changed. */
+ptadd_status ptadd_batch_get_forces(ptadd_ctx* ctx, double* F);
 /* ptadd_batch_set followed by ptadd_batch_advance. */
 ptadd_status ptadd_batch_run(ptadd_ctx* ctx, int32_t R, const int64_t* node_off, int64_t n_loops,
                              const int64_t* loop_off, const double* xyz, const double* burgers,
@@ -223,6 +240,16 @@ ptadd_status ptadd_batch_run(ptadd_ctx* ctx, int32_t R, const int64_t* node_off,
  * if a bounded wait for the tensor core gave up. */
 ptadd_status ptadd_gemm_bf16(int device, int64_t M, int32_t N, int32_t K, const uint16_t* A, const uint16_t* B,
                              float* C);
+/* Self-test of the bounded tensor-core waits; it has no counterpart in the
+ * paper.  Runs the GEMM kernel above once (M = 128, N = K = 64, zero
+ * operands) with the MMAs and their commit withheld, so the mbarrier phase
+ * that every thread waits on never completes: each wait gives up after its
+ * iteration limit (about 2 s of SM clocks), the kernel sets its error word,
+ * frees its tensor memory and returns, and the call reports
+ * PTADD_ERR_TIMEOUT -- the expected result.  PTADD_OK would mean a wait
+ * completed without its arrival.  The device and the library stay usable
+ * afterwards. */
+ptadd_status ptadd_gemm_timeout_selftest(int device);
 
 /* -------------------------------------------------------------- surrogate */
 /* A learned stand-in for the PTA closure (not in the paper): an MLP
@@ -451,22 +478,37 @@ ptadd_status ptadd_fma_peak(int device, int fp64, double seconds, double* flops)
  * Inputs and output are caller-owned DEVICE arrays:
  *   xyz_dev[n*3]      node positions, m
  *   nxt_dev[n]        index of the node after node i on its loop (segment i
- *                     runs i -> nxt[i]); prv_dev[n] the node before i
+ *                     runs i -> nxt[i]); prv_dev[n] the node before i.
+ *                     Required: 0 <= nxt[i], prv[i] < n_nodes and
+ *                     prv[nxt[i]] == nxt[prv[i]] == i for every i.  The
+ *                     tables are checked on the device before any kernel
+ *                     indexes with them; if an entry breaks the rule, no
+ *                     out-of-range access happens and every output force
+ *                     is NaN (the status, returned before the GPU ran, is
+ *                     still PTADD_OK).
  *   burgers_dev[n*3]  Burgers vector of segment i, m
  *   sig_app[6]        HOST array, applied stress, Pa (Voigt order)
  *   F_dev[n*3]        output nodal forces, N
  *   stream            cudaStream_t as void* (NULL = legacy default stream)
  * 2 <= n_nodes <= PTADD_NOALLOC_MAX_SEGMENTS, else PTADD_ERR_ARG.
+ * Call it with the device that owns `stream` and the arrays current
+ * (cudaSetDevice): the scratch used is that device's.
  *
- * Scratch: one fixed array of about 7 MB in the library's device memory
- * (held by every GPU that loads the library until the process exits).  The
- * first call on a device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call before
- * any stream capture.  Every call on a device shares the array: calls whose
- * work overlaps on the GPU (other streams, other host threads) race and
- * corrupt each other's results -- serialise them.  The call writes every
- * scratch entry it reads, so nothing carries over from the previous call.
- * Work is enqueued on `stream`; the call returns without synchronising. */
+ * Scratch: one fixed array of about 7 MB in the library's device memory.
+ * With lazy module loading (the CUDA default) the library's module, and with
+ * it the array, is loaded on a device at the first call there: that first
+ * call allocates device memory outside the caller's pool and may
+ * synchronise the device, so make one warm-up call on each device before
+ * entering a pool-managed region or a stream capture.  The array then stays
+ * until the process exits.  Outside stream capture every call looks up the
+ * array's device address (cudaGetSymbolAddress) afresh; a call under
+ * capture reuses the address of the last uncaptured call on that device
+ * (PTADD_ERR_STATE if there was none).  Every call on a device shares the
+ * array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race and corrupt each other's results -- serialise them.  The
+ * call writes every scratch entry it reads, so nothing carries over from the
+ * previous call.  Work is enqueued on `stream`; the call returns without
+ * synchronising. */
 ptadd_status ptadd_forces_noalloc(const ptadd_material* mat, int64_t n_nodes, const double* xyz_dev,
                                   const int32_t* nxt_dev, const int32_t* prv_dev, const double* burgers_dev,
                                   const double sig_app[6], double* F_dev, void* stream);

@@ -2,11 +2,11 @@
 on top of the oracle's FP64 burst.
 
 TEST INFRASTRUCTURE, like the rest of this package: only the test suite may
-use it.  It shares no code with the product's PTA driver; it follows the
-steps of the paper's single-box algorithm in their order, with the same
-readings (load l(t) = c1 (t + Delta) along a unit pattern; a running average
-converges when one more chunk of DD steps moves it by less than the
-tolerance; Frobenius norms; next slow step 0.002 / |R^Lp_t|, at most h_max).
+use it.  It shares no code with the product's PTA driver; it runs the
+single-box slow-time loop of Sec. 3.1 with the same readings (load
+l(t) = c1 (t + Delta) along a unit pattern; a running average converges when
+one more chunk of DD steps moves it by less than the tolerance; Frobenius
+norms; next slow step 0.002 / |R^Lp_t|, at most h_max).
 
 `p` is any object with the attributes rate, pattern, delta, h0, h_max, dt,
 chunk, tol_lp, tol_rho, max_chunks, extend_chunks, lpdot_max, max_jumps,
@@ -60,19 +60,19 @@ def run(mat, net, p, slow_steps):
     for _ in range(slow_steps):
         jumps = 0
         while True:
-            # step 1: running averages at l(t - Delta) from the carried microstructure
+            # converged averages at l(t - Delta) from the carried microstructure
             sL1, sr1, n1, x1 = _average_until_converged(mat, net, xyz, _stress(p, t - p.delta), p)
-            # step 2: from where step 1 ended, at l(t)
+            # then at l(t), from where that burst stopped
             sL2, sr2, n2, x2 = _average_until_converged(mat, net, x1, _stress(p, t), p)
-            # step 3
+            # difference quotient of the two averages
             lpdot = (sL2 / n2 - sL1 / n1) / p.delta
-            # step 4: a jump restarts from the state step 2 ended in
+            # a jump restarts the pair from the state the l(t) burst ended in
             if np.linalg.norm(lpdot) > p.lpdot_max and jumps < p.max_jumps:
                 xyz = x2
                 jumps += 1
                 continue
             break
-        # step 5: extend the t - Delta average while it exceeds the t average
+        # extend the t - Delta average while it exceeds the t average
         ext = 0
         xe = x1
         while np.linalg.norm(sL1 / n1) > np.linalg.norm(sL2 / n2) and ext < p.extend_chunks:
@@ -85,7 +85,7 @@ def run(mat, net, p, slow_steps):
         records.append({"t": t, "load": float(p.rate * (t + p.delta)), "Lp": sL2 / n2, "rho": sr2 / n2,
                         "Lp_prev": sL1 / n1, "Lpdot": lpdot, "rhodot": rhodot, "jumps": jumps,
                         "chunks": [n1 - ext, n2], "extended": ext})
-        # step 6: slow time step control
+        # slow time step from the strain-step bound
         h = min(p.h_max, p.strain_step / max(np.linalg.norm(sL2 / n2), 1e-300))
         xyz = x2
         t += h

@@ -327,6 +327,16 @@ __global__ void batch_soa_to_aos(int64_t n, const double* __restrict__ soa, doub
     aos[i] = soa[(i % 3) * n + i / 3] * scale;
 }
 
+// Forces SoA -> AoS in SI, zero at pinned nodes (their segments may be skipped).
+__global__ void batch_forces_out(int64_t n, const double* __restrict__ force, const uint8_t* __restrict__ pinned,
+                                 double scale, double* __restrict__ aos)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    const int64_t a = i / 3;
+    aos[i] = pinned[a] ? 0.0 : force[(i % 3) * n + a] * scale;
+}
+
 __global__ void batch_aos_to_soa(int64_t n, const double* __restrict__ aos, double scale, double* __restrict__ soa)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -932,6 +942,55 @@ ptadd_status ptadd_batch_set_nodes(ptadd_ctx* ctx, const double* xyz)
     batch_aos_to_soa<<<(unsigned)((3 * B.n + 255) / 256), 256, 0, s>>>(B.n, B.staging, 1.0 / ctx->len_unit,
                                                                          B.pos[B.cur]);
     PTADD_CUDA(cudaGetLastError());
+    PTADD_CUDA(cudaStreamSynchronize(s));
+    return PTADD_OK;
+}
+
+ptadd_status ptadd_batch_configure(ptadd_ctx* ctx, int32_t tile_targets, int32_t chunk_sources)
+{
+    if (!ctx || !ctx->batch) {
+        set_error("no batch loaded");
+        return PTADD_ERR_STATE;
+    }
+    if (tile_targets != 64 && tile_targets != 128) return barg("tile_targets must be 64 or 128");
+    if (chunk_sources < 1024 || chunk_sources > (1 << 24) || chunk_sources % 128 != 0)
+        return barg("chunk_sources must be a multiple of 128 in [1024, 2^24]");
+    PTADD_CUDA(cudaSetDevice(ctx->device));
+    PTADD_CUDA(cudaStreamSynchronize(ctx->stream));
+    BatchConfig cfg;
+    cfg.tpb = tile_targets;
+    cfg.chunk_len = chunk_sources;
+    ptadd_status st = apply_config(*ctx->batch, cfg, ctx->own_stream);
+    if (st == PTADD_OK) ctx->batch->tuned = 0;
+    return st;
+}
+
+ptadd_status ptadd_batch_get_forces(ptadd_ctx* ctx, double* F)
+{
+    if (!ctx || !ctx->batch) {
+        set_error("no batch loaded");
+        return PTADD_ERR_STATE;
+    }
+    if (!F) return barg("F is NULL");
+    PTADD_CUDA(cudaSetDevice(ctx->device));
+    DevBatch& B = *ctx->batch;
+    cudaStream_t s = ctx->own_stream;
+    PTADD_CUDA(cudaStreamSynchronize(ctx->stream));
+    const Consts c = batch_consts(ctx);
+    const unsigned nb = (unsigned)((B.n + 255) / 256);
+    batch_prep_kernel<<<nb, 256, 0, s>>>(B.n, B.pos[B.cur], B.nxt, B.loop_of, B.real_of, B.loop_b, B.d_origin, B.src,
+                                         B.src32);
+    PTADD_CUDA(cudaGetLastError());
+    PTADD_CUDA(cudaMemsetAsync(B.counter, 0, sizeof(unsigned), s));
+    if (B.n_items > 0) PTADD_CUDA(launch_batch_pair(B, (int)ctx->prec, c, s));
+    batch_node_kernel<<<nb, 256, 0, s>>>(B.n, B.pos[B.cur], B.nxt, B.prv, B.loop_of, B.real_of, B.loop_n, B.pinned,
+                                         B.d_node_off, B.d_fp_base, B.d_chunks, B.fpart, B.force, B.vel);
+    PTADD_CUDA(cudaGetLastError());
+    batch_forces_out<<<(unsigned)((3 * B.n + 255) / 256), 256, 0, s>>>(
+        B.n, B.force, B.pinned, ctx->mat.mu * ctx->len_unit * ctx->len_unit, B.staging);
+    PTADD_CUDA(cudaGetLastError());
+    ctx->kernel_launches += 4;
+    PTADD_CUDA(cudaMemcpyAsync(F, B.staging, 3 * B.n * sizeof(double), cudaMemcpyDeviceToHost, s));
     PTADD_CUDA(cudaStreamSynchronize(s));
     return PTADD_OK;
 }

@@ -3,6 +3,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "ptadd_internal.cuh"
 #include "tc_gemm.cuh"
 
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(GEMM_THREADS) tc_gemm_kernel(GemmArgs g)
         gemm_wait1();  // chunk k has landed (the newest group is chunk k + 1)
         fence_async_smem();
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && !g.withhold_mma) {
             tc_fence_after();
             const uint32_t a0 = ubase + (uint32_t)(k & 1) * GEMM_STAGE, b0 = a0 + GEMM_A_BYTES;
             const int kc = min(GEMM_KC, g.K - k * GEMM_KC);
@@ -172,8 +174,8 @@ cudaError_t launch_tc_gemm(const GemmArgs& g, cudaStream_t s)
 
 using namespace ptadd;
 
-extern "C" ptadd_status ptadd_gemm_bf16(int device, int64_t M, int32_t N, int32_t K, const uint16_t* A,
-                                        const uint16_t* B, float* C)
+static ptadd_status gemm_bf16(int device, int64_t M, int32_t N, int32_t K, const uint16_t* A, const uint16_t* B,
+                              float* C, int withhold_mma)
 {
     if (!A || !B || !C) {
         set_error("ptadd_gemm_bf16: null array");
@@ -221,6 +223,7 @@ extern "C" ptadd_status ptadd_gemm_bf16(int device, int64_t M, int32_t N, int32_
         g.out_f32 = dC;
         g.ld_out = N;
         g.err = derr;
+        g.withhold_mma = withhold_mma;
         e = launch_tc_gemm(g, s);
         if (e != cudaSuccess) fail(e, "launch");
     }
@@ -241,4 +244,17 @@ extern "C" ptadd_status ptadd_gemm_bf16(int device, int64_t M, int32_t N, int32_
     cudaFree(dC);
     cudaFree(derr);
     return st;
+}
+
+extern "C" ptadd_status ptadd_gemm_bf16(int device, int64_t M, int32_t N, int32_t K, const uint16_t* A,
+                                        const uint16_t* B, float* C)
+{
+    return gemm_bf16(device, M, N, K, A, B, C, 0);
+}
+
+extern "C" ptadd_status ptadd_gemm_timeout_selftest(int device)
+{
+    std::vector<uint16_t> zeros(128 * 64, 0);
+    std::vector<float> out(128 * 64, 0.0f);
+    return gemm_bf16(device, 128, 64, 64, zeros.data(), zeros.data(), out.data(), 1);
 }

@@ -140,6 +140,7 @@ struct GemmArgs {
     const float* zin;
     int64_t ld_z;
     int* err;  // set to 1 if an MMA wait gave up
+    int withhold_mma;  // self-test of the bounded waits: issue no MMA and no commit
 };
 
 constexpr int GEMM_THREADS = 128;

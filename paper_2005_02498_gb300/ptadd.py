@@ -28,7 +28,8 @@ EXPORTS = ["ptadd_version", "ptadd_create", "ptadd_destroy", "ptadd_last_error",
            "ptadd_profile_reset", "ptadd_profile_read", "ptadd_forces_noalloc",
            "ptadd_batch_set", "ptadd_batch_set_stress", "ptadd_batch_advance", "ptadd_batch_get_nodes",
            "ptadd_batch_set_nodes", "ptadd_batch_get_info", "ptadd_batch_autotune", "ptadd_batch_run",
-           "ptadd_gemm_bf16", "ptadd_mlp_param_count", "ptadd_mlp_init", "ptadd_mlp_set_params",
+           "ptadd_batch_configure", "ptadd_batch_get_forces",
+           "ptadd_gemm_bf16", "ptadd_gemm_timeout_selftest", "ptadd_mlp_param_count", "ptadd_mlp_init", "ptadd_mlp_set_params",
            "ptadd_mlp_get_params", "ptadd_mlp_loss_grad", "ptadd_mlp_train", "ptadd_mlp_forward",
            "ptadd_surrogate_fit", "ptadd_surrogate_predict", "ptadd_surrogate_predict_dev",
            "ptadd_closure_sweep", "ptadd_closure_realisation", "ptadd_dissipation_projection",
@@ -147,11 +148,17 @@ def load(build_if_missing=True):
     lib.ptadd_batch_get_info.restype = st
     lib.ptadd_batch_autotune.argtypes = [_VP, ctypes.c_char_p, ctypes.c_int]
     lib.ptadd_batch_autotune.restype = st
+    lib.ptadd_batch_configure.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32]
+    lib.ptadd_batch_configure.restype = st
+    lib.ptadd_batch_get_forces.argtypes = [_VP, _D]
+    lib.ptadd_batch_get_forces.restype = st
     lib.ptadd_batch_run.argtypes = [_VP, ctypes.c_int32, _I64, ctypes.c_int64, _I64, _D, _D, _D, _U8, _D, _D,
                                     ctypes.c_int64, ctypes.c_double, _D, _D]
     lib.ptadd_batch_run.restype = st
     lib.ptadd_gemm_bf16.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _VP, _VP, _VP]
     lib.ptadd_gemm_bf16.restype = st
+    lib.ptadd_gemm_timeout_selftest.argtypes = [ctypes.c_int]
+    lib.ptadd_gemm_timeout_selftest.restype = st
     _F = ctypes.POINTER(ctypes.c_float)
     lib.ptadd_mlp_param_count.restype = ctypes.c_int64
     lib.ptadd_mlp_init.argtypes = [_VP, ctypes.c_uint64]
@@ -341,6 +348,11 @@ def gemm_bf16(A_bits, B_bits, device=0):
     return C
 
 
+def gemm_timeout_selftest(device=0):
+    """Status of ptadd_gemm_timeout_selftest (PTADD_ERR_TIMEOUT = 4 expected)."""
+    return int(load().ptadd_gemm_timeout_selftest(int(device)))
+
+
 def to_bf16_bits(x):
     """Round-to-nearest-even FP32 -> BF16 bit patterns (uint16)."""
     u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
@@ -525,6 +537,15 @@ class Context:
         i = BatchInfo()
         _check(self._lib.ptadd_batch_get_info(self._h, ctypes.byref(i)))
         return {k: getattr(i, k) for k, _ in BatchInfo._fields_}
+
+    def batch_configure(self, tile_targets, chunk_sources):
+        _check(self._lib.ptadd_batch_configure(self._h, int(tile_targets), int(chunk_sources)))
+
+    def batch_get_forces(self):
+        """Nodal forces [n_nodes, 3] (N) at the current positions; 0 at pinned nodes."""
+        out = np.zeros((self.batch_n, 3))
+        _check(self._lib.ptadd_batch_get_forces(self._h, _dptr(out)))
+        return out
 
     def batch_autotune(self, cache_path=None, force=False):
         _check(self._lib.ptadd_batch_autotune(self._h, cache_path.encode() if cache_path else None,

@@ -56,8 +56,8 @@ def test_pta_jump_rule_restarts_until_the_cap():
 
 
 def test_pta_first_step_is_two_plain_bursts_when_one_chunk_is_allowed():
-    """With one chunk per average and no extension, step 1 is one burst at
-    l(-Delta) = 0 and step 2 one burst at l(0) from where step 1 ended."""
+    """With one chunk per average and no extension, the first slow step is one
+    burst at l(-Delta) = 0 and one burst at l(0) from where that one ended."""
     p = P(max_chunks=1, extend_chunks=0)
     net = W.small_loop_network()
     rec = OP.run(MAT, net, p, 1)[0]

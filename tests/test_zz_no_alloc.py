@@ -84,3 +84,34 @@ def test_noalloc_rejects_networks_beyond_its_scratch():
                              idx.data_ptr(), small.data_ptr(), np.zeros(6), small.data_ptr())
     assert e.value.status == 1
     assert "scratch" in str(e.value)
+
+
+def test_noalloc_rejects_broken_loop_tables_without_touching_memory_outside_them():
+    # The tables are checked on the device before any kernel indexes with
+    # them: an entry outside [0, n) or one that breaks prv[nxt[i]] == i is
+    # never used as an index, and the call writes NaN to every output force.
+    # A valid call afterwards is unaffected.
+    import torch
+    dev = torch.device("cuda", 0)
+    net = W.small_loop_network()
+    nxt, prv, bseg = ring_tables(net)
+    x = torch.from_numpy(np.ascontiguousarray(net.xyz)).to(dev)
+    tb = torch.from_numpy(bseg).to(dev)
+    stream = torch.cuda.current_stream()
+    for bad_nxt, bad_prv in [(7, None), (None, 2), (None, None)]:
+        n2, p2 = nxt.copy(), prv.copy()
+        if bad_nxt is not None:
+            n2[bad_nxt] = net.n_nodes + 1000  # out of range
+        if bad_prv is not None:
+            p2[bad_prv] = -5  # out of range
+        if bad_nxt is None and bad_prv is None:
+            n2[3], n2[4] = n2[4], n2[3]  # in range, but prv[nxt[i]] != i
+        tn = torch.from_numpy(n2).to(dev)
+        tp = torch.from_numpy(p2).to(dev)
+        F = torch.zeros((net.n_nodes, 3), dtype=torch.float64, device=dev)
+        ptadd.forces_noalloc(MAT, net.n_nodes, x.data_ptr(), tn.data_ptr(), tp.data_ptr(), tb.data_ptr(),
+                             net.sig_app, F.data_ptr(), stream.cuda_stream)
+        torch.cuda.synchronize()
+        assert torch.isnan(F).all()
+    F_ok = forces_noalloc(net)
+    assert relmax(F_ok, forces_context(net)) <= 1e-11
