@@ -78,9 +78,7 @@ constexpr int PAIR_TPB = 128;
 constexpr int PAIR_TILE = 128;
 constexpr int MIX_TPB = 128;
 constexpr int MIX_TILE = 128;
-#ifndef PTADD_MIX_MINB
-#define PTADD_MIX_MINB 2  // resident blocks per SM the register budget is sized for
-#endif
+constexpr int MIX_MINB = 3;  // resident blocks per SM the register budget is sized for
 
 __global__ void __launch_bounds__(PAIR_TPB) pair_fp64_kernel(TileArgs base, int64_t n_tgt, int64_t chunk_len,
                                                              Consts c)
@@ -96,7 +94,7 @@ __global__ void __launch_bounds__(PAIR_TPB) pair_fp64_kernel(TileArgs base, int6
     pair_tile_fp64<PAIR_TILE>(a, c, tile);
 }
 
-__global__ void __launch_bounds__(MIX_TPB, PTADD_MIX_MINB) pair_mixed_kernel(TileArgs base, int64_t n_tgt, int64_t chunk_len,
+__global__ void __launch_bounds__(MIX_TPB, MIX_MINB) pair_mixed_kernel(TileArgs base, int64_t n_tgt, int64_t chunk_len,
                                                              Consts c, float near2)
 {
     __shared__ MixSmem<MIX_TILE, MIX_TPB> sm;
@@ -124,11 +122,12 @@ int choose_chunks(int64_t n_tgt, int64_t n_src, int max_chunks, int precision)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_fp64_kernel, PAIR_TPB, 0);
     if (per_sm < 1) per_sm = 1;
     const int64_t tiles_t = (n_tgt + PAIR_TPB - 1) / PAIR_TPB;
+    int64_t cap = n_src / (2 * PAIR_TILE);
+    if (cap > max_chunks) cap = max_chunks;
+    if (cap < 1) cap = 1;
     const int64_t want_blocks = (int64_t)sms * per_sm * 16;
     int64_t ch = (want_blocks + tiles_t - 1) / (tiles_t > 0 ? tiles_t : 1);
-    const int64_t max_by_src = n_src / (2 * PAIR_TILE);
-    if (ch > max_by_src) ch = max_by_src;
-    if (ch > max_chunks) ch = max_chunks;
+    if (ch > cap) ch = cap;
     if (ch < 1) ch = 1;
     return (int)ch;
 }

@@ -128,13 +128,15 @@ __device__ __forceinline__ void pair_tile_fp64(const TileArgs& a, const Consts& 
 }
 
 // ----------------------------------------------------------------- mixed
-// Every (Gauss point, source) pair is first located in FP32 from hi/lo-split
-// coordinates; if the point lies within 10 a of the source segment the pair
-// is evaluated in FP64 from the FP64 records, otherwise in FP32.  Per Gauss
-// point the FP32 contributions are summed in three levels: plainly over
-// groups of SUM_GROUP sources, with Kahan compensation over the groups of one
-// shared-memory tile, and in FP64 over the tiles (where the FP64 near-field
-// values also go); the FP64 sums feed the PK force and the nodal assembly.
+// Every (Gauss point, source) pair is first located in FP32 (coordinates
+// relative to an integer origin near the target, so that R0 = x - x1 keeps
+// FP32 resolution anywhere in the box); if the point lies within 10 a of the
+// source segment the pair is evaluated in FP64 from the FP64 records,
+// otherwise in FP32.  Per Gauss point the FP32 contributions are summed in
+// three levels: plainly over groups of SUM_GROUP sources, with Kahan
+// compensation over the groups of the work item's source range, and in FP64
+// over work items (where the FP64 near-field values also go); the FP64 sums
+// feed the PK force and the nodal assembly.
 //
 // The FP32 work is packed: Gauss points (0,1) and (2,3) travel as the two
 // lanes of a float2, so every add, multiply and fused multiply-add of the
@@ -145,6 +147,8 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 // a - b, rounded once
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+// -a (a sign flip the compiler may fold into the instruction that uses it)
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float2 f2(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float2 sel2(bool cx, bool cy, float2 a, float2 b)
 {
@@ -159,85 +163,126 @@ __device__ __forceinline__ void kahan_add2(float2& s, float2& c, float2 v)
     s = t;
 }
 // sources summed plainly before a compensated add
-constexpr int SUM_GROUP = 16;
+constexpr int SUM_GROUP = 32;
+// sources of one group handled per loop iteration (two independent chains)
+constexpr int MIX_UNROLL = 2;
 // keep a register value opaque, so the compiler holds it instead of
 // recomputing it from its (FP64) inputs inside the loop
 __device__ __forceinline__ void opaque(float& x) { asm volatile("" : "+f"(x)); }
 
 // Shared-memory record of one source for the packed loop (float2 units, every
 // scalar in both lanes): x1 hi (0-2), x1 lo (3-5), L (6), t (7-9), b (10-12),
-// q = b x t (13-15), -t (16-18), -b (19-21).  The negated copies let the
-// field formula use plain fused multiply-adds where it subtracts.
-constexpr int MIX_REC = 22;
+// q = b x t (13-15), -t (16-18), -b (19-21), L^2 (22), 2L (23).  The negated
+// copies let the field formula use plain fused multiply-adds where it
+// subtracts.
+constexpr int MIX_REC = 24;
 
 struct Src2 {
-    float2 t[3], nt[3], L, b[3], nb[3], q[3];
+    float2 t[3], nt[3], L, b[3], nb[3], q[3], LL, L2;
 };
 
 // Quantities of one (source, target) pair shared by the four Gauss points:
-// t.b', -t.b', q.b', -q.b' and -(c1/c2) t.b'.
+// t.b', -t.b', q.b', -q.b'.
 struct Pair2 {
-    float2 tb, ntb, qb, nqb, nrtb;
+    float2 tb, ntb, qb, nqb;
 };
 
-// Packed field of one source at two Gauss points (lanes), given R0 = x - x1:
-// s <- (sigma b') / c2 per lane, and dd <- squared point-to-segment distance
-// + a^2.  The formula of seg_sigma_b (FP64, c2 taken out, K_k = 3 J_k,
-// (b x b').Rp as b'.(Rp x b)) in packed FP32, with y = R0.t carried as
-// ny = -y and the negated source vectors of the record, so that every
-// subtraction is a fused multiply-add.  a2 = a^2, nr = -c1/c2.
-__device__ __forceinline__ void seg_sigma_b2(float2 R0x, float2 R0y, float2 R0z, const Src2& S, const float2 bt[3],
-                                             const Pair2& P, float2 a2, float2 nr, float2 s[3], float2& dd)
+// Geometry of a (Gauss-point pair, source), given R0 = x - x1: ny = -y with
+// y = R0.t, Rp = R0 - y t (the part of R0 normal to the source), d2 =
+// |Rp|^2 + a^2, u2 = L - y, rho1^2 = y^2 + d2, rho2^2 = u2^2 + d2.
+struct Geo2 {
+    float2 ny, Rp[3], d2, u2, r1s, r2s;
+};
+
+__device__ __forceinline__ void seg_geo2(const float2 R0[3], const Src2& S, float2 a2, Geo2& G)
 {
-    const float2 ny = fma2(R0x, S.nt[0], fma2(R0y, S.nt[1], mul2(R0z, S.nt[2])));
-    const float2 Rpx = fma2(ny, S.t[0], R0x), Rpy = fma2(ny, S.t[1], R0y), Rpz = fma2(ny, S.t[2], R0z);
-    const float2 d2 = fma2(Rpx, Rpx, fma2(Rpy, Rpy, fma2(Rpz, Rpz, a2)));
-    const float2 u2 = add2(S.L, ny);
-    const float2 r1s = fma2(ny, ny, d2), r2s = fma2(u2, u2, d2);
-    // y < 0: nearest to x1; y > L: nearest to x2; else to the line
-    dd = sel2(ny.x > 0.0f, ny.y > 0.0f, r1s, sel2(u2.x < 0.0f, u2.y < 0.0f, r2s, d2));
+    G.ny = fma2(R0[0], S.nt[0], fma2(R0[1], S.nt[1], mul2(R0[2], S.nt[2])));
+#pragma unroll
+    for (int e = 0; e < 3; ++e) G.Rp[e] = fma2(G.ny, S.t[e], R0[e]);
+    G.d2 = fma2(G.Rp[0], G.Rp[0], fma2(G.Rp[1], G.Rp[1], fma2(G.Rp[2], G.Rp[2], a2)));
+    G.u2 = add2(S.L, G.ny);
+    G.r1s = fma2(G.ny, G.ny, G.d2);
+    G.r2s = fma2(G.u2, G.u2, G.d2);
+}
+
+// The packed field of one source at two Gauss points (lanes) in coefficient
+// form:
+//   (sigma b') / c2 = cRxb (Rp x b) + cq q + cRp Rp + ct t + cb b',
+// the formula of seg_sigma_b (FP64: c2 taken out, K_k = 3 J_k, (b x b').Rp
+// as b'.(Rp x b)) regrouped so that each coefficient costs few operations:
+//   B0 = a^2 K2 + J0 (= A0 - J0),  C1 = r A1 + J1,
+//   cRxb = (r A0) t.b',  cq = C1 t.b' - J0 (Rp.b'),
+//   ct = (r A0) Rw + C1 q.b' + (q.Rp)(K4 t.b' - K3 (Rp.b')),
+//   cRp = (q.Rp)(K2 (Rp.b') - K3 t.b') - J0 q.b',  cb = (q.Rp) B0,
+// with r = -c1/c2 (nr) and Rw = b'.(Rp x b).  L (u1 + u2) = L (L + 2 ny)
+// comes from L^2 and 2L of the record.  The reciprocal of a lane flagged near
+// is replaced by 0; every coefficient carries it as a factor (all other
+// factors are finite, rho >= a > 0), so such a lane contributes exactly 0 and
+// the caller adds the terms unconditionally.  SAME = 1: every lane of the
+// warp has both ends of the source on one side of the foot of the
+// perpendicular (u1 u2 >= 0), so the straddling forms are not evaluated.
+struct Coef2 {
+    float2 cRxb, cq, cRp, ct, cb;
+    float2 X[3];  // Rp x b
+};
+
+template <int SAME>
+__device__ __forceinline__ void seg_coef2(const Geo2& G, const Src2& S, const float2 bt[3], const Pair2& P,
+                                          float2 a2, float2 nr, bool nearx, bool neary, Coef2& C)
+{
+    const float2 ny = G.ny, d2 = G.d2, u2 = G.u2, r1s = G.r1s, r2s = G.r2s;
+    const float2 Rpx = G.Rp[0], Rpy = G.Rp[1], Rpz = G.Rp[2];
     const float2 i1 = make_float2(rsqrt_approx(r1s.x), rsqrt_approx(r1s.y));
     const float2 i2 = make_float2(rsqrt_approx(r2s.x), rsqrt_approx(r2s.y));
     const float2 m = mul2(ny, i1), p = mul2(u2, i2);
-    // u1 u2 >= 0 (y <= 0 or y >= L)
-    const bool samex = (ny.x >= 0.0f) || (u2.x <= 0.0f), samey = (ny.y >= 0.0f) || (u2.y <= 0.0f);
     const float2 i1s = mul2(i1, i1), i2s = mul2(i2, i2), i12 = mul2(i1s, i2s);
+    const float2 ssum = add2(i1s, i2s);
     const float2 pm = mul2(p, m);
     const float2 S2 = fma2(p, p, fma2(m, m, pm));
     const float2 isum = add2(i1, i2);
     const float2 pps = add2(p, m), one_pm = add2(f2(1.0f), pm);
-    const float2 den = sel2(samex, samey, mul2(pps, one_pm), d2);
+    bool samex = true, samey = true;
+    if (!SAME) {
+        samex = (ny.x >= 0.0f) || (u2.x <= 0.0f);
+        samey = (ny.y >= 0.0f) || (u2.y <= 0.0f);
+    }
+    const float2 den = SAME ? mul2(pps, one_pm) : sel2(samex, samey, mul2(pps, one_pm), d2);
     const float2 dis = mul2(den, isum);
-    const float2 rr = make_float2(rcp_approx(dis.x), rcp_approx(dis.y));
+    const float2 rr = sel2(nearx, neary, f2(0.0f), make_float2(rcp_approx(dis.x), rcp_approx(dis.y)));
     const float2 rden = mul2(rr, isum);
-    const float2 Lsum = mul2(S.L, add2(u2, ny));
-    const float2 Li = mul2(Lsum, i12);
+    const float2 Li = mul2(fma2(ny, S.L2, S.LL), i12);  // L (u1 + u2) / (rho1^2 rho2^2)
     const float2 J1 = mul2(Li, mul2(rr, den));
-    const float2 K3 = mul2(J1, add2(i1s, fma2(i1, i2, i2s)));
+    const float2 K3 = mul2(J1, fma2(i1, i2, ssum));
     const float2 g = mul2(Li, rden);
-    const float2 J0 = sel2(samex, samey, mul2(g, one_pm), mul2(sub2(p, m), rden));
-    const float2 Wt = sel2(samex, samey, fma2(mul2(mul2(add2(r1s, mul2(u2, u2)), i12), rden), pps, add2(i1s, i2s)),
-                           mul2(sub2(f2(3.0f), S2), rden));
+    // one-side form of (3 - p^2 - pm - m^2)/d^2: (u1^2 + u2^2 + d^2)/(rho1^2 rho2^2 (1 + pm)) + 1/rho1^2 + 1/rho2^2
+    const float2 Wsame = fma2(mul2(mul2(fma2(ny, ny, r2s), i12), rden), pps, ssum);
+    float2 J0, Wt;
+    if (SAME) {
+        J0 = mul2(g, one_pm);
+        Wt = Wsame;
+    } else {
+        J0 = sel2(samex, samey, mul2(g, one_pm), mul2(sub2(p, m), rden));
+        Wt = sel2(samex, samey, Wsame, mul2(sub2(f2(3.0f), S2), rden));
+    }
     const float2 K2 = mul2(J0, Wt);
     const float2 K4 = mul2(J0, S2);
-    const float2 A0 = fma2(a2, K2, add2(J0, J0));
+    const float2 B0 = fma2(a2, K2, J0);
+    const float2 A0 = add2(B0, J0);
     const float2 A1 = fma2(a2, K3, add2(J1, J1));
-    // Rp x b
-    const float2 Xx = fma2(Rpy, S.b[2], mul2(Rpz, S.nb[1]));
-    const float2 Xy = fma2(Rpz, S.b[0], mul2(Rpx, S.nb[2]));
-    const float2 Xz = fma2(Rpx, S.b[1], mul2(Rpy, S.nb[0]));
+    const float2 C1 = fma2(nr, A1, J1);
+    const float2 nrA0 = mul2(nr, A0);
+    C.X[0] = fma2(Rpy, S.b[2], mul2(Rpz, S.nb[1]));
+    C.X[1] = fma2(Rpz, S.b[0], mul2(Rpx, S.nb[2]));
+    C.X[2] = fma2(Rpx, S.b[1], mul2(Rpy, S.nb[0]));
     const float2 Rb = fma2(Rpx, bt[0], fma2(Rpy, bt[1], mul2(Rpz, bt[2])));
-    const float2 nRb = mul2(Rb, f2(-1.0f));
-    const float2 Rw = fma2(Xx, bt[0], fma2(Xy, bt[1], mul2(Xz, bt[2])));
+    const float2 nRb = neg2(Rb);
+    const float2 Rw = fma2(C.X[0], bt[0], fma2(C.X[1], bt[1], mul2(C.X[2], bt[2])));
     const float2 qR = fma2(Rpx, S.q[0], fma2(Rpy, S.q[1], mul2(Rpz, S.q[2])));
-    const float2 cRxb = mul2(P.nrtb, A0);
-    const float2 cq = fma2(P.nrtb, A1, fma2(J1, P.tb, mul2(J0, nRb)));
-    const float2 cRp = fma2(qR, fma2(K3, P.ntb, mul2(K2, Rb)), mul2(J0, P.nqb));
-    const float2 ct = fma2(nr, fma2(A0, Rw, mul2(A1, P.qb)), fma2(J1, P.qb, mul2(qR, fma2(K3, nRb, mul2(K4, P.tb)))));
-    const float2 cb = mul2(qR, sub2(A0, J0));
-    s[0] = fma2(cRxb, Xx, fma2(cq, S.q[0], fma2(cRp, Rpx, fma2(ct, S.t[0], mul2(cb, bt[0])))));
-    s[1] = fma2(cRxb, Xy, fma2(cq, S.q[1], fma2(cRp, Rpy, fma2(ct, S.t[1], mul2(cb, bt[1])))));
-    s[2] = fma2(cRxb, Xz, fma2(cq, S.q[2], fma2(cRp, Rpz, fma2(ct, S.t[2], mul2(cb, bt[2])))));
+    C.cRxb = mul2(nrA0, P.tb);
+    C.cq = fma2(P.tb, C1, mul2(J0, nRb));
+    C.ct = fma2(nrA0, Rw, fma2(C1, P.qb, mul2(qR, fma2(K3, nRb, mul2(K4, P.tb)))));
+    C.cRp = fma2(qR, fma2(K3, P.ntb, mul2(K2, Rb)), mul2(J0, P.nqb));
+    C.cb = mul2(qR, B0);
 }
 
 // One near-field (Gauss point, source) pair in FP64: (sigma b') of source js
@@ -280,7 +325,7 @@ template <int TILE, int TPB>
 struct MixSmem {
     float2 tile[TILE * MIX_REC];  // source records (MIX_REC float2 each)
     double nacc[12 * TPB];             // FP64 sums: [qp * 3 + e][thread]
-    float2 ksum[12 * TPB];             // Kahan sums of a tile: [p * 3 + e][thread], then compensations
+    float2 ksum[12 * TPB];             // Kahan sums of the work item: [p * 3 + e][thread], then compensations
     uint2 queue[TPB / 32][NEAR_Q];
 };
 
@@ -340,32 +385,45 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
     opaque(btf[1]);
     opaque(btf[2]);
     const float2 bt2[3] = {f2(btf[0]), f2(btf[1]), f2(btf[2])};
-    // Gauss points, hi/lo split about the origin; pair p holds points 2p, 2p+1
-    float2 XH[2][3], XL[2][3];
+    // Gauss points relative to an integer origin Ot near this target (its
+    // first Gauss point, rounded, in the frame of the split origin): within a
+    // segment length of Ot, so FP32 holds them to ~1e-7 of that length.  A
+    // source start x1 = h1 + l1 (integer hi part, |lo| <= 1/2) then moves to
+    // this frame as (h1 - Ot) + l1: the integer parts subtract exactly and the
+    // fraction rounds once, i.e. to ~1 ulp of |x1 - Ot| ~ |R0| + L.
+    // Pair p holds Gauss points 2p, 2p+1.
+    float2 XT[2][3];
+    float nOt[3];
+    {
+        double Ot[3];
 #pragma unroll
-    for (int qp = 0; qp < 4; ++qp) {
-        const double xi = gl4_xi(qp);
-        const double qd[3] = {__dadd_rn(xa, __dmul_rn(xi, Dx)) - a.origin[0],
-                              __dadd_rn(ya, __dmul_rn(xi, Dy)) - a.origin[1],
-                              __dadd_rn(za, __dmul_rn(xi, Dz)) - a.origin[2]};
+        for (int qp = 0; qp < 4; ++qp) {
+            const double xi = gl4_xi(qp);
+            const double qd[3] = {__dadd_rn(xa, __dmul_rn(xi, Dx)) - a.origin[0],
+                                  __dadd_rn(ya, __dmul_rn(xi, Dy)) - a.origin[1],
+                                  __dadd_rn(za, __dmul_rn(xi, Dz)) - a.origin[2]};
 #pragma unroll
-        for (int e = 0; e < 3; ++e) {
-            const double h = rint(qd[e]);
-            float hf = (float)h, lf = (float)(qd[e] - h);
-            opaque(hf);
-            opaque(lf);
-            if (qp & 1) {
-                XH[qp >> 1][e].y = hf;
-                XL[qp >> 1][e].y = lf;
-            } else {
-                XH[qp >> 1][e].x = hf;
-                XL[qp >> 1][e].x = lf;
+            for (int e = 0; e < 3; ++e) {
+                if (qp == 0) {
+                    Ot[e] = rint(qd[e]);
+                    nOt[e] = (float)(-Ot[e]);
+                    opaque(nOt[e]);
+                }
+                float xf = (float)(qd[e] - Ot[e]);
+                opaque(xf);
+                if (qp & 1)
+                    XT[qp >> 1][e].y = xf;
+                else
+                    XT[qp >> 1][e].x = xf;
             }
         }
     }
-    // FP64 sums per Gauss point (far-field tile sums and near-field values)
+    // FP64 sums per Gauss point (far-field sums of the work item and
+    // near-field values); Kahan sums of the work item and their compensations
 #pragma unroll
     for (int k = 0; k < 12; ++k) sm.nacc[k * TPB + threadIdx.x] = 0.0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) sm.ksum[k * TPB + threadIdx.x] = f2(0.0f);
     // loop-invariant constants held in registers (not re-derived from FP64 inputs in the loop)
     float kc[2] = {(float)c.a2, (float)(-c.c1 / c.c2)};
     opaque(kc[0]);
@@ -397,24 +455,22 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
             d[8] = make_float4(-v[7], -v[7], -v[8], -v[8]);
             d[9] = make_float4(-v[9], -v[9], -v[10], -v[10]);
             d[10] = make_float4(-v[11], -v[11], -v[12], -v[12]);
+            d[11] = make_float4(v[6] * v[6], v[6] * v[6], v[6] + v[6], v[6] + v[6]);
         }
         __syncthreads();
-        // plain sums of the current group of SUM_GROUP sources (/ c2); the
-        // Kahan sums of the tile and their compensations wait in shared memory
+        // plain sums of the current group of SUM_GROUP sources (/ c2)
         float2 SG[2][3];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) sm.ksum[k * TPB + threadIdx.x] = f2(0.0f);
         for (int g0 = 0; g0 < cnt; g0 += SUM_GROUP) {
             const int g1 = min(cnt, g0 + SUM_GROUP);
 #pragma unroll
             for (int p = 0; p < 2; ++p)
 #pragma unroll
                 for (int e = 0; e < 3; ++e) SG[p][e] = f2(0.0f);
+#pragma unroll MIX_UNROLL
             for (int jj = g0; jj < g1; ++jj) {
                 const float2* r = sm.tile + jj * MIX_REC;
                 if (!(r[6].x > 0.0f)) continue;  // zero-length source (uniform branch)
                 Src2 S;
-                const float2 h1[3] = {r[0], r[1], r[2]}, l1[3] = {r[3], r[4], r[5]};
                 S.L = r[6];
 #pragma unroll
                 for (int e = 0; e < 3; ++e) {
@@ -424,30 +480,48 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
                     S.nt[e] = r[16 + e];
                     S.nb[e] = r[19 + e];
                 }
+                S.LL = r[22];
+                S.L2 = r[23];
                 Pair2 P;
                 P.tb = fma2(S.t[0], bt2[0], fma2(S.t[1], bt2[1], mul2(S.t[2], bt2[2])));
                 P.qb = fma2(S.q[0], bt2[0], fma2(S.q[1], bt2[1], mul2(S.q[2], bt2[2])));
-                P.ntb = mul2(P.tb, f2(-1.0f));
-                P.nqb = mul2(P.qb, f2(-1.0f));
-                P.nrtb = mul2(nr, P.tb);
-                // both Gauss-point pairs first (two independent chains), then the sums
-                float2 v[2][3], dd[2];
+                P.ntb = neg2(P.tb);
+                P.nqb = neg2(P.qb);
+                // the source start in this thread's frame
+                float x1t[3];
 #pragma unroll
-                for (int p = 0; p < 2; ++p) {
-                    const float2 R0x = add2(sub2(XH[p][0], h1[0]), sub2(XL[p][0], l1[0]));
-                    const float2 R0y = add2(sub2(XH[p][1], h1[1]), sub2(XL[p][1], l1[1]));
-                    const float2 R0z = add2(sub2(XH[p][2], h1[2]), sub2(XL[p][2], l1[2]));
-                    seg_sigma_b2(R0x, R0y, R0z, S, bt2, P, a2, nr, v[p], dd[p]);
-                }
+                for (int e = 0; e < 3; ++e) x1t[e] = (r[e].x + nOt[e]) + r[3 + e].x;
+                // near test of both Gauss-point pairs first (point-to-segment
+                // distance), then the coefficients (near lanes give 0)
+                Geo2 G[2];
                 bool nrq[2][2];
+                bool same_all = true;
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {
-                    nrq[p][0] = active && dd[p].x < near2;
-                    nrq[p][1] = active && dd[p].y < near2;
-                    // far lanes go to the FP32 group sums; near lanes to the FP64 queue
+                    float2 R0[3];
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) R0[e] = sub2(XT[p][e], f2(x1t[e]));
+                    seg_geo2(R0, S, a2, G[p]);
+                    const float2 ny = G[p].ny, u2 = G[p].u2;
+                    // y < 0: nearest to x1; y > L: nearest to x2; else to the line
+                    const float2 dd = sel2(ny.x > 0.0f, ny.y > 0.0f, G[p].r1s,
+                                           sel2(u2.x < 0.0f, u2.y < 0.0f, G[p].r2s, G[p].d2));
+                    nrq[p][0] = active && dd.x < near2;
+                    nrq[p][1] = active && dd.y < near2;
+                    same_all = same_all && (ny.x >= 0.0f || u2.x <= 0.0f) && (ny.y >= 0.0f || u2.y <= 0.0f);
+                }
+                const bool uni = __all_sync(0xffffffffu, same_all);
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    Coef2 C;
+                    if (uni)
+                        seg_coef2<1>(G[p], S, bt2, P, a2, nr, nrq[p][0], nrq[p][1], C);
+                    else
+                        seg_coef2<0>(G[p], S, bt2, P, a2, nr, nrq[p][0], nrq[p][1], C);
 #pragma unroll
                     for (int e = 0; e < 3; ++e)
-                        SG[p][e] = add2(SG[p][e], sel2(nrq[p][0], nrq[p][1], f2(0.0f), v[p][e]));
+                        SG[p][e] = fma2(C.cRxb, C.X[e], fma2(C.cq, S.q[e], fma2(C.cRp, G[p].Rp[e],
+                                        fma2(C.ct, S.t[e], fma2(C.cb, bt2[e], SG[p][e])))));
                 }
                 if (__any_sync(0xffffffffu, nrq[0][0] || nrq[0][1] || nrq[1][0] || nrq[1][1])) {
                     const unsigned js = (unsigned)(j0 + jj);
@@ -476,18 +550,18 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
                 sm.ksum[(6 + k) * TPB + threadIdx.x] = ck;
             }
         }
-        // compensated tile sums to FP64, restoring the factor c2
-#pragma unroll
-        for (int p = 0; p < 2; ++p)
-#pragma unroll
-            for (int e = 0; e < 3; ++e) {
-                const float2 sk = sm.ksum[(3 * p + e) * TPB + threadIdx.x];
-                const float2 ck = sm.ksum[(6 + 3 * p + e) * TPB + threadIdx.x];
-                double* acc = sm.nacc + (6 * p + e) * TPB + threadIdx.x;
-                acc[0] = fma(c.c2, (double)sk.x - (double)ck.x, acc[0]);
-                acc[3 * TPB] = fma(c.c2, (double)sk.y - (double)ck.y, acc[3 * TPB]);
-            }
     }
+    // compensated sums of the work item's sources to FP64, restoring the factor c2
+#pragma unroll
+    for (int p = 0; p < 2; ++p)
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const float2 sk = sm.ksum[(3 * p + e) * TPB + threadIdx.x];
+            const float2 ck = sm.ksum[(6 + 3 * p + e) * TPB + threadIdx.x];
+            double* acc = sm.nacc + (6 * p + e) * TPB + threadIdx.x;
+            acc[0] = fma(c.c2, (double)sk.x - (double)ck.x, acc[0]);
+            acc[3 * TPB] = fma(c.c2, (double)sk.y - (double)ck.y, acc[3 * TPB]);
+        }
     if (qn > 0) {
         __syncwarp();
         near_flush(a.pos, n, a.nxt, a.src, a.k64, seg, wq, qn, sm.nacc, TPB);

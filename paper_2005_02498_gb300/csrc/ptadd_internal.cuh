@@ -44,8 +44,9 @@ constexpr int SRC_STRIDE = 16;
 // FP32 record of the mixed path (16 floats):
 //   [0..2] x1_hi  [3..5] x1_lo  [6] L  [7..9] t  [10..12] b  [13..15] q
 // with x1 - origin = x1_hi + x1_lo, x1_hi integer-valued (exact in FP32 for
-// |x1 - origin| < 2^24 l), so R0 = (x_hi - x1_hi) + (x_lo - x1_lo) keeps ~1 ulp
-// relative accuracy for every pair.
+// |x1 - origin| < 2^24 l), so that a target can move x1 into a frame of its
+// own (integer origin Ot nearby) as (x1_hi - Ot) + x1_lo with one rounding,
+// and R0 = x - x1 keeps ~1e-7 relative accuracy for every pair.
 constexpr int SRC32_STRIDE = 16;
 // Near field of the mixed path: point-to-segment distance below 10 a, with a
 // 1 % margin in favour of FP64 on the FP32 estimate of that distance.
