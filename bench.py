@@ -49,6 +49,18 @@ from paper_2005_02498_gb300 import workloads as W  # noqa: E402
 # reciprocal square root as 1: 4 x 165 per field point + 19 per pair.
 FLOPS_PER_PAIR = 4 * 165 + 19
 L2_FLUSH_BYTES = 256 << 20
+
+
+def _bf16_peak():
+    """Dense BF16 tensor peak for a kernel timed alone (burst figure)."""
+    try:
+        return (float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]),
+                "measured: MEASURED_PEAKS.json bf16_tflops (cuBLAS burst)")
+    except (OSError, ValueError, KeyError):
+        return 1900.0, "fallback: one earlier burst measurement of a GB300"
+
+
+BF16_PEAK_TFLOPS, BF16_PEAK_SOURCE = _bf16_peak()
 WORKLOAD = ("1024 circular FCC glide loops x 32 segments = 32768 segments, 5 um cube, "
             "mu 48 GPa, nu 0.34, b 0.2556 nm, a = b, B 1e-4 Pa s, 50 MPa [001], dt 1e-11 s")
 
@@ -66,6 +78,13 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target length of the CPU-baseline sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-closures", action="store_true", help="skip the PTA-closure legs (batched ensemble, sweep)")
+    p.add_argument("--c3-steps", type=int, default=10, help="timed DD steps of the 256-realisation batch")
+    p.add_argument("--c3-fp64-R", type=int, default=16, help="realisations of the plain FP64 batch subsample")
+    p.add_argument("--sur-train", type=int, default=8000, help="DD-labelled closures the surrogate is fitted on")
+    p.add_argument("--sweep-steps", type=int, default=3, help="load steps of the 100-step sweep that are run")
+    p.add_argument("--ref-points", type=int, default=8, help="(point, step) pairs checked against FP64 DD")
+    p.add_argument("--ref-members", type=int, default=16, help="FP64 DD realisations per reference mean")
     return p.parse_args()
 
 
@@ -201,6 +220,144 @@ def arm_config(args, n_segments, world):
             "pairs_per_step": n_segments * n_segments * args.dd_steps, "segments": n_segments,
             "l2": "flushed between timed steps (256 MB device write)",
             "parallelism": "one independent realisation per GPU" if world > 1 else "single GPU"}
+
+
+# ------------------------------------------------------ closure legs
+BATCH_WORKLOAD = ("256 independent realisations, N_r ~ U{1024..16384} segments in loops of 32, every stress "
+                  "component ~ U(-200, 200) MPa, sessile loop fraction ~ U(0.1, 0.9), 16 loops per um^3, "
+                  "dt 1e-11 s, 2000-step bursts, seed 1003")
+SWEEP_WORKLOAD = ("16^3 material points, 100 load steps of smooth random stress fields up to 200 MPa and density "
+                  "fields of the training marginals (seed 1005); surrogate inside its trust region, 64-realisation "
+                  "DD ensembles of 4096-segment closures (128 loops, 100 steps at dt 5e-13 s) outside it")
+
+
+def closure_legs(args, device):
+    """PTA closures/s on the batched workloads, against plain FP64 DD on the
+    same GPU: (1) the 256-realisation ensemble, mixed precision, timed steps
+    extrapolated to its 2000-step bursts, with plain FP64 on a subsample
+    extrapolated per segment pair; (2) the closure sweep: a surrogate fitted
+    here on DD-labelled closures answers inside its trust region, DD
+    ensembles outside it, on evenly spaced load steps of the 100-step load
+    path (extrapolated), its answers checked against FP64 DD ensemble means
+    on a sample of (point, step) pairs.  Wall-clock timing of synchronous
+    calls (each call ends with a device-to-host copy of its results)."""
+    import torch
+
+    from paper_2005_02498_gb300 import closure_sweep as CS
+    from paper_2005_02498_gb300 import ptadd
+    from paper_2005_02498_gb300 import surrogate as SU
+
+    mat = W.Material().as_tuple()
+    out = {}
+    # (1) batched ensemble
+    batch = W.batch_ensemble(1003, R=256)
+    dt3, burst = 1e-11, 2000
+    with ptadd.Context(mat, ptadd.PTADD_MIXED, device) as c:
+        c.batch_set(batch)
+        c.batch_autotune()
+        info = c.batch_info()
+        c.batch_advance(2, dt3)  # warm-up: captures the two-step graph
+        c.batch_set_nodes(batch.xyz)
+        t0 = time.perf_counter()
+        c.batch_advance(args.c3_steps, dt3)
+        el = time.perf_counter() - t0
+    ms = 1e3 * el / args.c3_steps
+    sub = W.batch_from_networks([batch.realisation(r) for r in range(args.c3_fp64_R)])
+    with ptadd.Context(mat, ptadd.PTADD_FP64, device) as c:
+        c.batch_set(sub)
+        pairs_sub = c.batch_info()["pairs_per_step"]
+        c.batch_advance(1, dt3)
+        c.batch_set_nodes(sub.xyz)
+        t0 = time.perf_counter()
+        c.batch_advance(2, dt3)
+        el64 = time.perf_counter() - t0
+    rate64 = pairs_sub * 2 / el64
+    cps = batch.R / (ms * 1e-3 * burst)
+    cps64 = batch.R / (info["pairs_per_step"] / rate64 * burst)
+    out["batched_ensemble"] = {
+        "workload": BATCH_WORKLOAD, "segments": int(batch.xyz.shape[0]), "pairs_per_step": info["pairs_per_step"],
+        "tile_targets": info["tile_targets"], "chunk_sources": info["chunk_sources"],
+        "timed_steps": args.c3_steps, "ms_per_step": ms, "pair_evals_per_s": info["pairs_per_step"] / (ms * 1e-3),
+        "closures_per_s": cps, "closures_per_s_note": "timed steps extrapolated to the 2000-step bursts",
+        "fp64_dd": {"realisations": args.c3_fp64_R, "steps": 2, "pair_evals_per_s": rate64,
+                    "closures_per_s": cps64, "note": "plain FP64 on the first realisations, extrapolated per "
+                                                     "segment pair to the whole batch"},
+        "speedup_vs_fp64_dd": cps / cps64}
+
+    # (2) surrogate fitted on DD closures, then the sweep slice
+    steps, dt, loops, members = 100, 5e-13, 128, 64
+    rng = np.random.default_rng(1004)
+    nval = max(64, args.sur_train // 10)
+    X = SU.feature_points(rng, args.sur_train + nval)
+    pts, S, rho = CS.material_points(1005, 16)
+    K = 100
+    ks_run = CS.load_steps_run(K, args.sweep_steps)
+    with ptadd.Context(mat, ptadd.PTADD_MIXED, device) as c:
+        Y, t_lab, _ = SU.generate(c, X, 1, 1005, steps, dt, loops)
+        t0 = time.perf_counter()
+        val_err, curve, nfit = SU.fit_early_stopping(c, X[:args.sur_train], Y[:args.sur_train],
+                                                     X[args.sur_train:], Y[args.sur_train:], epochs=40, seed=1004)
+        t_fit = time.perf_counter() - t0
+        # fused inference on 1M device-resident points resampled from the training inputs
+        feats = torch.from_numpy(X[rng.integers(0, X.shape[0], size=1 << 20)]).cuda(device)
+        yd = torch.empty((1 << 20, 6), dtype=torch.float64, device=feats.device)
+        rd = torch.empty(1 << 20, dtype=torch.uint8, device=feats.device)
+        st = torch.cuda.Stream(device=feats.device)
+        torch.cuda.synchronize()
+        c.set_stream(st.cuda_stream)
+        c.surrogate_predict_dev(1 << 20, feats.data_ptr(), yd.data_ptr(), rd.data_ptr())
+        st.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(10):
+            c.surrogate_predict_dev(1 << 20, feats.data_ptr(), yd.data_ptr(), rd.data_ptr())
+        e1.record(st)
+        st.synchronize()
+        inf_ms = e0.elapsed_time(e1) / 10
+        c.set_stream(None)
+        del feats, yd, rd
+        r = CS.sweep(c, S, rho, K, ks_run, members, steps, dt, loops, 1005, True, device)
+    # FP64 DD reference means on a random sample of (point, step) pairs of the run steps
+    n = S.shape[0]
+    rs = np.random.default_rng(1006)
+    kr = np.asarray(ks_run) - 1
+    pick = rs.choice(len(kr) * n, size=min(args.ref_points, len(kr) * n), replace=False)
+    ks, ps = kr[pick // n], pick % n
+    fref = np.hstack([S[ps] * ((ks + 1) / K)[:, None], rho[ps]])
+    singles = np.zeros((pick.size, args.ref_members, 6))
+    with ptadd.Context(mat, ptadd.PTADD_FP64, device) as c:
+        t0 = time.perf_counter()
+        ref, _, _ = SU.generate(c, fref, args.ref_members, 1007, steps, dt, loops, singles=singles)
+        t_ref = time.perf_counter() - t0
+    got = r["answers"][ks, ps]
+    # noise of the reference means: spread of single realisations / sqrt(members)
+    M = args.ref_members
+    spread = float(np.linalg.norm(singles - ref[:, None, :]) / np.sqrt(M - 1) / np.linalg.norm(ref) / np.sqrt(M))
+    fp64_real_per_s = pick.size * args.ref_members / t_ref
+    total = r["wall_s"] * K / len(ks_run)
+    sweep_cps = n * K / total
+    fp64_cps = fp64_real_per_s / members  # an all-DD sweep answers each point with a 64-member ensemble
+    run = np.asarray(ks_run) - 1
+    flops = 2.0 * (30 * 256 + 256 * 256 * 2 + 256 * 6) * (1 << 20)
+    out["surrogate"] = {
+        "training_closures": args.sur_train, "validation_closures": nval, "fit_samples_with_images": nfit,
+        "dd_label_closures_per_s_mixed": (args.sur_train + nval) / t_lab, "fit_s": t_fit,
+        "validation_rel_err": val_err,
+        "inference": {"points": 1 << 20, "ms": inf_ms, "closures_per_s": (1 << 20) / (inf_ms * 1e-3),
+                      "tflops_algorithmic": flops / (inf_ms * 1e-3) / 1e12,
+                      "frac_of_bf16_peak": flops / (inf_ms * 1e-3) / 1e12 / BF16_PEAK_TFLOPS,
+                      "bf16_peak_tflops": BF16_PEAK_TFLOPS, "peak_source": BF16_PEAK_SOURCE}}
+    out["closure_sweep"] = {
+        "workload": SWEEP_WORKLOAD, "load_steps_run": len(ks_run), "closures": n * K,
+        "closures_per_s": sweep_cps, "closures_per_s_note": "run load steps extrapolated to all 100",
+        "fallback_fraction": float(r["used_dd"][run].mean()), "fallback_closures": int(r["fallback_closures"]),
+        "rel_err_vs_fp64_dd": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+        "reference": {"pairs": int(pick.size), "members": args.ref_members, "precision": "fp64",
+                      "noise_floor_rel": spread},
+        "fp64_dd_closures_per_s": fp64_cps,
+        "speedup_vs_fp64_dd": sweep_cps / fp64_cps}
+    return out
 
 
 # --------------------------------------------------------- reference arm
@@ -377,7 +534,11 @@ def run_ours(args):
            "near_field_point_pairs_per_step": prof.get("near_point_pairs", 0) / max(1, args.steps),
            "clocks": clk}
     ctx.close()
+    del flush
+    torch.cuda.empty_cache()
 
+    if rank == 0 and world == 1 and not args.no_closures:
+        out["closures"] = closure_legs(args, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, k, secs = cpu_sample(net, args.cpu_seconds, mat.as_tuple())
         out["cpu_baseline"] = {"value": v, "unit": "pair-evals/s", "cores": cores, "kind": "oracle",

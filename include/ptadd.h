@@ -146,6 +146,18 @@ ptadd_status ptadd_advance(ptadd_ctx* ctx, int64_t n_steps, double dt,
                            double Lp_avg[9], double* rho_avg);
 
 /* Current node positions (m) into host xyz[n_nodes*3]. */
+/* Polar dislocation velocity of the last burst (Sec. 2.4, Eq. 2.11; Eq. 2.5
+ * for its running average): the volume-averaged dislocation velocity
+ *   V = (1/|B|) sum_s vbar_s l_s A_s,
+ * with vbar_s the velocity of segment s (the mean of its two nodal
+ * velocities, the one that gives Lp = alpha x V segment by segment), l_s its
+ * length, |B| the network's volume and A_s = core_area (m^2) the core
+ * cross-section of every segment, which the paper takes as |b|^2 up to a
+ * constant and leaves to the caller.  The burst sums l_s vbar_s in the same
+ * reduction as Lp and rho, so the call only scales them: V_avg[3] (m/s).
+ * PTADD_ERR_STATE before the first ptadd_advance after ptadd_set_network;
+ * PTADD_ERR_ARG for a non-positive core_area. */
+ptadd_status ptadd_get_polar_velocity(ptadd_ctx* ctx, double core_area, double V_avg[3]);
 ptadd_status ptadd_get_nodes(ptadd_ctx* ctx, double* xyz);
 
 /* Replace the positions of the loaded network (host xyz[n_nodes*3], m; same
@@ -197,6 +209,9 @@ ptadd_status ptadd_batch_set_stress(ptadd_ctx* ctx, const double* sig6);
 /* Burst of n_steps for every realisation: Lp_avg[R*9] (row-major, 1/s) and
  * rho_avg[R] (1/m^2), the averages of Eq. 2.5; either may be NULL. */
 ptadd_status ptadd_batch_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, double* Lp_avg, double* rho_avg);
+/* R^V of the last batch burst per realisation (as ptadd_get_polar_velocity,
+ * with each realisation's own volume): V_avg[R*3] (m/s). */
+ptadd_status ptadd_batch_get_polar_velocity(ptadd_ctx* ctx, double core_area, double* V_avg);
 ptadd_status ptadd_batch_get_nodes(ptadd_ctx* ctx, double* xyz);
 ptadd_status ptadd_batch_set_nodes(ptadd_ctx* ctx, const double* xyz);
 ptadd_status ptadd_batch_get_info(ptadd_ctx* ctx, ptadd_batch_info* info);
@@ -357,6 +372,17 @@ ptadd_status ptadd_system_densities(int64_t n_nodes, const double* xyz, int64_t 
  * (X A)_i = e_ijk A_jk.  Zero T (or zero X(T alpha)) leaves the input as is.
  * PTADD_ERR_ARG on NULL T/Lp, V without alpha, or non-finite values. */
 ptadd_status ptadd_dissipation_projection(const double T6[6], const double alpha[9], double Lp[9], double V[3]);
+/* The same correction at n_points material points on the device (the Gauss
+ * points of a mesh, the realisations of a batch), one thread per point.
+ * Caller-owned DEVICE arrays: T6_dev[n*6], Lp_dev[n*9] (corrected in place),
+ * alpha_dev[n*9] and V_dev[n*3] (both NULL, or both given; V corrected in
+ * place).  A point with a non-finite value is left unchanged and counted in
+ * *n_bad_dev (a device int the call zeroes first; NULL to skip the count).
+ * Work is enqueued on `stream` (cudaStream_t as void*, NULL = legacy default
+ * stream) without synchronising; allocates nothing.  PTADD_ERR_ARG on
+ * n_points < 0 or a missing array. */
+ptadd_status ptadd_dissipation_projection_dev(int64_t n_points, const double* T6_dev, const double* alpha_dev,
+                                              double* Lp_dev, double* V_dev, int* n_bad_dev, void* stream);
 
 /* Junctions and thermally activated breaking in the burst (Sec. 2.2).
  * Sessile segments are those whose two nodes are pinned.  In every step of

@@ -65,7 +65,9 @@ def _load():
                                    ctypes.c_double, _D, _D]
         lib.orc_burst.argtypes = [_D, ctypes.c_int64, _D, ctypes.c_int64, _I64, _D, _D, _U8,
                                   ctypes.c_double, _D, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
-                                  _D, _D, _D, _D, _D]
+                                  _D, _D, _D, _D, _D, ctypes.c_double, _D]
+        lib.orc_polar_velocity.argtypes = [ctypes.c_int64, _D, ctypes.c_int64, _I64, _D, ctypes.c_double,
+                                           ctypes.c_double, _D]
         lib.orc_burst.restype = ctypes.c_int
         _I32 = ctypes.POINTER(ctypes.c_int32)
         lib.orc_splitmix64_mix.argtypes = [ctypes.c_uint64]
@@ -231,8 +233,20 @@ def lp_rho(net, v, xyz=None):
     return Lp.reshape(3, 3), rho.value
 
 
-def burst(mat, net, n_steps, dt, interactions=True, trace=False):
-    """Run n_steps Euler steps; returns dict(xyz, Lp_avg (3x3), rho_avg[, Lp_trace, rho_trace])."""
+def polar_velocity(net, v, core_area, xyz=None):
+    """V = (core_area / |B|) sum_s L_s vbar_s (Eq. 2.11), from nodal velocities v [n, 3]."""
+    lib = _load()
+    x, px = _d(net.xyz if xyz is None else xyz)
+    off, poff = _i(net.loop_off)
+    vv, pv = _d(v)
+    V = np.zeros(3)
+    lib.orc_polar_velocity(net.n_nodes, px, net.n_loops, poff, pv, float(net.volume), float(core_area),
+                           V.ctypes.data_as(_D))
+    return V
+
+
+def burst(mat, net, n_steps, dt, interactions=True, trace=False, core_area=None):
+    """Run n_steps Euler steps; returns dict(xyz, Lp_avg (3x3), rho_avg[, Lp_trace, rho_trace][, V_avg])."""
     lib = _load()
     m, mp = _mat(mat)
     x, px = _d(net.xyz)
@@ -246,12 +260,16 @@ def burst(mat, net, n_steps, dt, interactions=True, trace=False):
     rho = ctypes.c_double(0.0)
     tL = np.zeros((max(n_steps, 1), 9)) if trace else None
     tr = np.zeros(max(n_steps, 1)) if trace else None
+    V = np.zeros(3)
     rc = lib.orc_burst(mp, net.n_nodes, px, net.n_loops, poff, pb, pn, ppin, float(net.volume), ps,
                        int(bool(interactions)), int(n_steps), float(dt), xo.ctypes.data_as(_D),
                        Lp.ctypes.data_as(_D), ctypes.byref(rho),
                        tL.ctypes.data_as(_D) if trace else None,
-                       tr.ctypes.data_as(_D) if trace else None)
+                       tr.ctypes.data_as(_D) if trace else None,
+                       float(core_area or 0.0), V.ctypes.data_as(_D) if core_area is not None else None)
     out = dict(xyz=xo, Lp_avg=Lp.reshape(3, 3), rho_avg=rho.value, status=rc)
+    if core_area is not None:
+        out["V_avg"] = V
     if trace:
         out["Lp_trace"] = tL[:n_steps].reshape(-1, 3, 3)
         out["rho_trace"] = tr[:n_steps]

@@ -456,19 +456,38 @@ void orc_lp_rho(int64_t n_nodes, const double* xyz, int64_t n_loops,
     (void)n_nodes;
 }
 
+void orc_polar_velocity(int64_t n_nodes, const double* xyz, int64_t n_loops,
+                        const int64_t* loop_off, const double* v, double volume,
+                        double core_area, double V[3])
+{
+    double acc[3] = {0.0, 0.0, 0.0};
+    for (int64_t k = 0; k < n_loops; ++k) {
+        const int64_t b = loop_off[k], e = loop_off[k + 1];
+        for (int64_t i = b; i < e; ++i) {
+            const int64_t j = (i + 1 < e) ? i + 1 : b;
+            double dx[3];
+            for (int m = 0; m < 3; ++m) dx[m] = xyz[3 * j + m] - xyz[3 * i + m];
+            const double L = sqrt(dot3(dx, dx));
+            for (int m = 0; m < 3; ++m) acc[m] += L * 0.5 * (v[3 * i + m] + v[3 * j + m]);
+        }
+    }
+    for (int m = 0; m < 3; ++m) V[m] = core_area * acc[m] / volume;
+    (void)n_nodes;
+}
+
 int orc_burst(const double mat[5], int64_t n_nodes, const double* xyz,
               int64_t n_loops, const int64_t* loop_off, const double* burgers,
               const double* normal, const uint8_t* pinned, double volume,
               const double sig_app[6], int interactions, int64_t n_steps, double dt,
               double* xyz_out, double Lp_avg[9], double* rho_avg,
-              double* Lp_trace, double* rho_trace)
+              double* Lp_trace, double* rho_trace, double core_area, double* V_avg)
 {
     const size_t n3 = (size_t)(3 * (n_nodes > 0 ? n_nodes : 1));
     double* x = (double*)malloc(sizeof(double) * n3);
     double* F = (double*)malloc(sizeof(double) * n3);
     double* v = (double*)malloc(sizeof(double) * n3);
     memcpy(x, xyz, sizeof(double) * (size_t)(3 * n_nodes));
-    double S_Lp[9] = {0}, S_rho = 0.0, S_t = 0.0;
+    double S_Lp[9] = {0}, S_rho = 0.0, S_t = 0.0, S_V[3] = {0.0, 0.0, 0.0};
     int status = 0;
     for (int64_t s = 0; s < n_steps; ++s) {
         orc_nodal_forces(mat, n_nodes, x, n_loops, loop_off, burgers, pinned, sig_app,
@@ -479,6 +498,11 @@ int orc_burst(const double mat[5], int64_t n_nodes, const double* xyz,
         for (int m = 0; m < 9; ++m) S_Lp[m] += Lp[m] * dt;
         S_rho += rho * dt;
         S_t += dt;
+        if (V_avg) {
+            double V[3];
+            orc_polar_velocity(n_nodes, x, n_loops, loop_off, v, volume, core_area, V);
+            for (int m = 0; m < 3; ++m) S_V[m] += V[m] * dt;
+        }
         if (Lp_trace) memcpy(Lp_trace + 9 * s, Lp, sizeof(Lp));
         if (rho_trace) rho_trace[s] = rho;
         for (int m = 0; m < 9; ++m)
@@ -487,6 +511,8 @@ int orc_burst(const double mat[5], int64_t n_nodes, const double* xyz,
     }
     for (int m = 0; m < 9; ++m) Lp_avg[m] = (S_t > 0.0) ? S_Lp[m] / S_t : 0.0;
     *rho_avg = (S_t > 0.0) ? S_rho / S_t : 0.0;
+    if (V_avg)
+        for (int m = 0; m < 3; ++m) V_avg[m] = (S_t > 0.0) ? S_V[m] / S_t : 0.0;
     if (xyz_out) memcpy(xyz_out, x, sizeof(double) * (size_t)(3 * n_nodes));
     free(x);
     free(F);

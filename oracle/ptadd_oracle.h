@@ -83,17 +83,27 @@ void orc_lp_rho(int64_t n_nodes, const double* xyz, int64_t n_loops,
                 const int64_t* loop_off, const double* burgers, const double* v,
                 double volume, double Lp[9], double* rho);
 
+/* Polar dislocation velocity (Sec. 2.4, Eq. 2.11): the volume-averaged
+ * dislocation velocity V = (1/|B|) sum_s vbar_s L_s A_s, with vbar_s the
+ * segment's velocity (the mean of its nodal velocities, the same one that
+ * gives Lp = alpha x V segment by segment) and one core area A_s = core_area
+ * for every segment.  V[3]. */
+void orc_polar_velocity(int64_t n_nodes, const double* xyz, int64_t n_loops,
+                        const int64_t* loop_off, const double* v, double volume,
+                        double core_area, double V[3]);
+
 /* A burst of n_steps explicit Euler steps at fixed dt (Sec. 2.1), returning the
- * running averages R^Lp and R^rho of Eq. 2.5 over the step-start states.
- * xyz_out (may alias nothing) receives the final positions; Lp_trace and
- * rho_trace (or NULL) receive the per-step samples.  Returns 0, or -1 if a
- * non-finite value appeared. */
+ * running averages R^Lp and R^rho of Eq. 2.5 over the step-start states,
+ * and, if V_avg is not NULL, R^V of the polar velocity (Eq. 2.11, core area
+ * core_area).  xyz_out (may alias nothing) receives the final positions;
+ * Lp_trace and rho_trace (or NULL) receive the per-step samples.  Returns 0,
+ * or -1 if a non-finite value appeared. */
 int orc_burst(const double mat[5], int64_t n_nodes, const double* xyz,
               int64_t n_loops, const int64_t* loop_off, const double* burgers,
               const double* normal, const uint8_t* pinned, double volume,
               const double sig_app[6], int interactions, int64_t n_steps, double dt,
               double* xyz_out, double Lp_avg[9], double* rho_avg,
-              double* Lp_trace, double* rho_trace);
+              double* Lp_trace, double* rho_trace, double core_area, double* V_avg);
 
 /* ---- MLP (mlp_oracle.c): dims[0] -> ... -> dims[L], GELU on hidden layers,
  * linear output, parameters packed per layer as W (dims[l+1] x dims[l],

@@ -70,6 +70,68 @@ def material_points(seed, grid, stress_max=200e6, rho_min=2e12, rho_max=2e13):
     return pts, S, rho
 
 
+def sweep(ctx, S, rho, K, ks_run, members, steps, dt, loops, seed, symmetrise=True, device=0,
+          max_fallback_s=600.0):
+    """Answer every material point at the load steps ks_run (of K): the
+    surrogate (on the device, averaged over the 48 symmetric images with
+    `symmetrise`) inside its trust region, the mean of `members` batched DD
+    realisations outside it.  Returns dict(answers [K, n, 6], used_dd [K, n],
+    surrogate_s, fallback_s, fallback_closures, wall_s)."""
+    import torch
+
+    n = S.shape[0]
+    answers = np.zeros((K, n, 6))
+    used_dd = np.zeros((K, n), bool)
+    t_sur = t_dd = 0.0
+    dd_closures = 0
+    st = torch.cuda.Stream(device=device)
+    ctx.set_stream(st.cuda_stream)
+    G = len(closure_symmetries()) if symmetrise else 1
+    feat_d = torch.empty((G * n, 30), dtype=torch.float64, device="cuda:%d" % device)
+    lp_d = torch.empty((G * n, 6), dtype=torch.float64, device=feat_d.device)
+    reg_d = torch.empty(G * n, dtype=torch.uint8, device=feat_d.device)
+    t_all = time.perf_counter()
+    for k in ks_run:
+        feats = np.hstack([S * (k / K), rho])
+        t0 = time.perf_counter()
+        xs = symmetrised_inputs(feats) if G > 1 else feats
+        feat_d.copy_(torch.from_numpy(xs))
+        ctx.surrogate_predict_dev(G * n, feat_d.data_ptr(), lp_d.data_ptr(), reg_d.data_ptr())
+        st.synchronize()
+        ys = lp_d.cpu().numpy()
+        if G > 1:
+            lp, g0 = symmetrised_answers(ys, n)
+            inr = reg_d[g0 * n:(g0 + 1) * n].cpu().numpy().astype(bool)
+        else:
+            lp = ys
+            inr = reg_d.cpu().numpy().astype(bool)
+        t_sur += time.perf_counter() - t0
+        miss = np.flatnonzero(~inr)
+        if miss.size and dd_closures and t_dd / dd_closures * (dd_closures + miss.size) > max_fallback_s:
+            raise SystemExit("fallback work would exceed max_fallback_s; %d misses at load step %d" % (miss.size, k))
+        if miss.size:
+            t0 = time.perf_counter()
+            ctx.set_stream(None)
+            y, _, _ = generate(ctx, feats[miss], members, seed + 100 + k, steps, dt, loops)
+            ctx.set_stream(st.cuda_stream)
+            lp[miss] = y
+            t_dd += time.perf_counter() - t0
+            dd_closures += miss.size
+        answers[k - 1] = lp
+        used_dd[k - 1] = ~inr
+    wall = time.perf_counter() - t_all
+    ctx.set_stream(None)
+    return {"answers": answers, "used_dd": used_dd, "surrogate_s": t_sur, "fallback_s": t_dd,
+            "fallback_closures": dd_closures, "wall_s": wall}
+
+
+def load_steps_run(K, eval_steps):
+    """The load steps a run evaluates: all K, or eval_steps evenly spaced ones."""
+    if eval_steps and eval_steps < K:
+        return sorted(set(int(round(x)) for x in np.linspace(1, K, eval_steps)))
+    return list(range(1, K + 1))
+
+
 def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--state", required=True, help="fitted surrogate state (surrogate.py --save)")
@@ -91,62 +153,19 @@ def main(argv=None):
     p.add_argument("--device", type=int, default=0)
     a = p.parse_args(argv)
 
-    import torch
-
     pts, S, rho = material_points(a.seed, a.grid)
     n = pts.shape[0]
     K = a.load_steps
     rng = np.random.default_rng(a.seed + 1)
-    answers = np.zeros((K, n, 6))
-    used_dd = np.zeros((K, n), bool)
-    t_sur = t_dd = 0.0
-    dd_closures = 0
     mat = W.Material().as_tuple()
+    ks_run = load_steps_run(K, a.eval_steps)
     with ptadd.Context(mat, ptadd.PTADD_MIXED, a.device) as ctx:
         ctx.surrogate_set_state(open(a.state, "rb").read())
-        st = torch.cuda.Stream(device=a.device)
-        ctx.set_stream(st.cuda_stream)
-        G = len(closure_symmetries()) if a.symmetrise else 1
-        feat_d = torch.empty((G * n, 30), dtype=torch.float64, device="cuda:%d" % a.device)
-        lp_d = torch.empty((G * n, 6), dtype=torch.float64, device=feat_d.device)
-        reg_d = torch.empty(G * n, dtype=torch.uint8, device=feat_d.device)
-        t_all = time.perf_counter()
-        ks_run = list(range(1, K + 1))
-        if a.eval_steps and a.eval_steps < K:
-            ks_run = sorted(set(int(round(x)) for x in np.linspace(1, K, a.eval_steps)))
-        n_run = 0
-        for k in ks_run:
-            n_run += 1
-            feats = np.hstack([S * (k / K), rho])
-            t0 = time.perf_counter()
-            xs = symmetrised_inputs(feats) if G > 1 else feats
-            feat_d.copy_(torch.from_numpy(xs))
-            ctx.surrogate_predict_dev(G * n, feat_d.data_ptr(), lp_d.data_ptr(), reg_d.data_ptr())
-            st.synchronize()
-            ys = lp_d.cpu().numpy()
-            if G > 1:
-                lp, g0 = symmetrised_answers(ys, n)
-                inr = reg_d[g0 * n:(g0 + 1) * n].cpu().numpy().astype(bool)
-            else:
-                lp = ys
-                inr = reg_d.cpu().numpy().astype(bool)
-            t_sur += time.perf_counter() - t0
-            miss = np.flatnonzero(~inr)
-            if miss.size and dd_closures and t_dd / dd_closures * (dd_closures + miss.size) > a.max_fallback_s:
-                raise SystemExit("fallback work would exceed --max-fallback-s; %d misses at load step %d"
-                                 % (miss.size, k))
-            if miss.size:
-                t0 = time.perf_counter()
-                ctx.set_stream(None)
-                y, _, _ = generate(ctx, feats[miss], a.members, a.seed + 100 + k, a.steps, a.dt, a.loops)
-                ctx.set_stream(st.cuda_stream)
-                lp[miss] = y
-                t_dd += time.perf_counter() - t0
-                dd_closures += miss.size
-            answers[k - 1] = lp
-            used_dd[k - 1] = ~inr
-        total = (time.perf_counter() - t_all) * (len(ks_run) and K / len(ks_run))
-        ctx.set_stream(None)
+        r = sweep(ctx, S, rho, K, ks_run, a.members, a.steps, a.dt, a.loops, a.seed, a.symmetrise, a.device,
+                  a.max_fallback_s)
+        answers, used_dd, t_sur, t_dd, dd_closures = (r["answers"], r["used_dd"], r["surrogate_s"],
+                                                      r["fallback_s"], r["fallback_closures"])
+        total = r["wall_s"] * K / len(ks_run)
         # all-DD reference on a random sample of (step, point) pairs of the run steps
         kr = np.asarray(ks_run) - 1
         pick = rng.choice(len(kr) * n, size=min(a.check, len(kr) * n), replace=False)

@@ -63,6 +63,7 @@ struct DevBatch {
     double* src = nullptr;
     float* src32 = nullptr;
     double *fpart = nullptr, *vel = nullptr, *force = nullptr, *partial = nullptr, *acc = nullptr;
+    std::vector<double> last_LV;  // [3R] (1/|B|) sum L vbar of the last burst, time-averaged, SI
     int64_t fpart_cap = 0;  // doubles
     // per realisation (device)
     int64_t* d_node_off = nullptr;
@@ -245,19 +246,22 @@ __global__ void batch_node_kernel(int64_t n, const double* __restrict__ pos, con
     vel[a] = v[0]; vel[n + a] = v[1]; vel[2 * n + a] = v[2];
 }
 
+// per-segment sums of the step-start state: L b (x) (t x vbar) (9), L (1), L vbar (3)
+constexpr int BSUM = 13;
+
 __global__ void __launch_bounds__(BRED) batch_lp_euler_kernel(
     int64_t n, const double* __restrict__ pos, double* __restrict__ pos_next, const int32_t* __restrict__ nxt,
     const int32_t* __restrict__ loop_of, const double* __restrict__ loop_b, const double* __restrict__ vel,
     const int32_t* __restrict__ blk_real, const int64_t* __restrict__ blk_start,
     const int64_t* __restrict__ node_off, double dt, double* __restrict__ partial, int* __restrict__ flag)
 {
-    __shared__ double red[BRED / 32][10];
+    __shared__ double red[BRED / 32][BSUM];
     const int r = blk_real[blockIdx.x];
     const int64_t i = blk_start[blockIdx.x] + threadIdx.x;
     const bool in = i < node_off[r + 1];
-    double v10[10];
+    double v13[BSUM];
 #pragma unroll
-    for (int m = 0; m < 10; ++m) v10[m] = 0.0;
+    for (int m = 0; m < BSUM; ++m) v13[m] = 0.0;
     if (in) {
         const int64_t j = nxt[i];
         const double dx = pos[j] - pos[i], dy = pos[n + j] - pos[n + i], dz = pos[2 * n + j] - pos[2 * n + i];
@@ -267,10 +271,12 @@ __global__ void __launch_bounds__(BRED) batch_lp_euler_kernel(
         const double cx = dy * vz - dz * vy, cy = dz * vx - dx * vz, cz = dx * vy - dy * vx;
         const int k = loop_of[i];
         const double b0 = loop_b[3 * k], b1 = loop_b[3 * k + 1], b2 = loop_b[3 * k + 2];
-        v10[0] = b0 * cx; v10[1] = b0 * cy; v10[2] = b0 * cz;
-        v10[3] = b1 * cx; v10[4] = b1 * cy; v10[5] = b1 * cz;
-        v10[6] = b2 * cx; v10[7] = b2 * cy; v10[8] = b2 * cz;
-        v10[9] = sqrt(dx * dx + dy * dy + dz * dz);
+        const double L = sqrt(dx * dx + dy * dy + dz * dz);
+        v13[0] = b0 * cx; v13[1] = b0 * cy; v13[2] = b0 * cz;
+        v13[3] = b1 * cx; v13[4] = b1 * cy; v13[5] = b1 * cz;
+        v13[6] = b2 * cx; v13[7] = b2 * cy; v13[8] = b2 * cz;
+        v13[9] = L;
+        v13[10] = L * vx; v13[11] = L * vy; v13[12] = L * vz;
         const double nxp = __dadd_rn(pos[i], __dmul_rn(vel[i], dt));
         const double nyp = __dadd_rn(pos[n + i], __dmul_rn(vel[n + i], dt));
         const double nzp = __dadd_rn(pos[2 * n + i], __dmul_rn(vel[2 * n + i], dt));
@@ -280,44 +286,48 @@ __global__ void __launch_bounds__(BRED) batch_lp_euler_kernel(
         if (!isfinite(nxp) || !isfinite(nyp) || !isfinite(nzp)) atomicOr(flag, 1);
     }
 #pragma unroll
-    for (int m = 0; m < 10; ++m) {
-        double v = v10[m];
+    for (int m = 0; m < BSUM; ++m) {
+        double v = v13[m];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][m] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 10) {
+    if (threadIdx.x < BSUM) {
         double s = 0.0;
 #pragma unroll
         for (int w = 0; w < BRED / 32; ++w) s += red[w][threadIdx.x];
-        partial[(int64_t)blockIdx.x * 10 + threadIdx.x] = s;
+        partial[(int64_t)blockIdx.x * BSUM + threadIdx.x] = s;
     }
 }
 
-// One block per realisation: its partials in order, weighted by dt.
+// One block per realisation: its partials in order, weighted by dt, into
+// acc[16 r + 0..9] (Lp, rho) and acc[16 r + 13..15] (polar velocity).
 __global__ void batch_finish_kernel(const int32_t* __restrict__ real_blk, const double* __restrict__ partial,
                                     double dt, double* __restrict__ acc)
 {
-    __shared__ double red[128][10];
+    __shared__ double red[128][BSUM];
     const int r = blockIdx.x;
     const int b0 = real_blk[r], b1 = real_blk[r + 1];
-    double s[10];
+    double s[BSUM];
 #pragma unroll
-    for (int m = 0; m < 10; ++m) s[m] = 0.0;
+    for (int m = 0; m < BSUM; ++m) s[m] = 0.0;
     for (int b = b0 + threadIdx.x; b < b1; b += 128)
 #pragma unroll
-        for (int m = 0; m < 10; ++m) s[m] += partial[(int64_t)b * 10 + m];
+        for (int m = 0; m < BSUM; ++m) s[m] += partial[(int64_t)b * BSUM + m];
 #pragma unroll
-    for (int m = 0; m < 10; ++m) red[threadIdx.x][m] = s[m];
+    for (int m = 0; m < BSUM; ++m) red[threadIdx.x][m] = s[m];
     __syncthreads();
     for (int h = 64; h > 0; h >>= 1) {
         if (threadIdx.x < h)
 #pragma unroll
-            for (int m = 0; m < 10; ++m) red[threadIdx.x][m] += red[threadIdx.x + h][m];
+            for (int m = 0; m < BSUM; ++m) red[threadIdx.x][m] += red[threadIdx.x + h][m];
         __syncthreads();
     }
-    if (threadIdx.x < 10) acc[16 * r + threadIdx.x] = fma(red[0][threadIdx.x], dt, acc[16 * r + threadIdx.x]);
+    if (threadIdx.x < BSUM) {
+        const int slot = threadIdx.x < 10 ? threadIdx.x : threadIdx.x + 3;
+        acc[16 * r + slot] = fma(red[0][threadIdx.x], dt, acc[16 * r + slot]);
+    }
 }
 
 __global__ void batch_soa_to_aos(int64_t n, const double* __restrict__ soa, double scale, double* __restrict__ aos)
@@ -744,7 +754,7 @@ ptadd_status ptadd_batch_set(ptadd_ctx* ctx, int32_t R, const int64_t* node_off,
     BALLOC(B.fpart, B.fpart_cap);
     BALLOC(B.vel, 3 * n);
     BALLOC(B.force, 3 * n);
-    BALLOC(B.partial, 10 * (int64_t)B.nblk);
+    BALLOC(B.partial, (int64_t)BSUM * B.nblk);
     BALLOC(B.acc, 16 * (int64_t)R);
     BALLOC(B.d_node_off, R + 1);
     BALLOC(B.d_fp_base, R);
@@ -881,10 +891,16 @@ ptadd_status ptadd_batch_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, dou
     const double l = ctx->len_unit;
     const double St = dt_hat * (double)n_steps;
     bool finite = flag == 0;
+    B.last_LV.assign(3 * (size_t)B.R, 0.0);
     for (int r = 0; r < B.R; ++r) {
         const double lp_scale = l * l * l * ctx->mat.mu / (ctx->mat.B * B.volume[r]);
         const double rho_scale = l / B.volume[r];
+        const double v_scale = l * l * ctx->mat.mu / (ctx->mat.B * B.volume[r]);
         for (int m = 0; m < 10; ++m) finite = finite && isfinite(acc[16 * r + m]);
+        for (int m = 0; m < 3; ++m) {
+            finite = finite && isfinite(acc[16 * r + 13 + m]);
+            B.last_LV[3 * r + m] = n_steps > 0 ? acc[16 * r + 13 + m] / St * v_scale : 0.0;
+        }
         if (Lp_avg)
             for (int m = 0; m < 9; ++m) Lp_avg[9 * r + m] = n_steps > 0 ? acc[16 * r + m] / St * lp_scale : 0.0;
         if (rho_avg) rho_avg[r] = n_steps > 0 ? acc[16 * r + 9] / St * rho_scale : 0.0;
@@ -893,6 +909,23 @@ ptadd_status ptadd_batch_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, dou
         set_error("batch burst produced a non-finite position or average");
         return PTADD_ERR_NONFINITE;
     }
+    return PTADD_OK;
+}
+
+ptadd_status ptadd_batch_get_polar_velocity(ptadd_ctx* ctx, double core_area, double* V_avg)
+{
+    if (!ctx || !ctx->batch) {
+        set_error("no batch loaded");
+        return PTADD_ERR_STATE;
+    }
+    if (!V_avg) return barg("V_avg is NULL");
+    if (!(core_area > 0) || !isfinite(core_area)) return barg("core_area must be positive and finite");
+    const DevBatch& B = *ctx->batch;
+    if (B.last_LV.size() != 3 * (size_t)B.R) {
+        set_error("no batch burst has run since the batch was set");
+        return PTADD_ERR_STATE;
+    }
+    for (size_t k = 0; k < B.last_LV.size(); ++k) V_avg[k] = core_area * B.last_LV[k];
     return PTADD_OK;
 }
 

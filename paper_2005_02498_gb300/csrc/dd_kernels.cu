@@ -209,17 +209,20 @@ cudaError_t launch_node_velocity(const DevNetwork& net, int chunks, cudaStream_t
 
 // ------------------------------------------------------------ lp_euler
 constexpr int RED_TPB = 256;
+// per-segment sums of the step-start state: L b (x) (t x vbar) (9), L (1),
+// L vbar (3, the polar-velocity sum of Eq. 2.11 without A / |B|)
+constexpr int NSUM = 13;
 
 __global__ void __launch_bounds__(RED_TPB) lp_euler_kernel(
     int64_t n, const double* __restrict__ pos, double* __restrict__ pos_next, const int32_t* __restrict__ nxt,
     const int32_t* __restrict__ loop_of, const double* __restrict__ loop_b, const double* __restrict__ vel,
     double dt, double* __restrict__ partial, int* __restrict__ flag)
 {
-    __shared__ double red[RED_TPB / 32][10];
+    __shared__ double red[RED_TPB / 32][NSUM];
     const int64_t i = blockIdx.x * (int64_t)RED_TPB + threadIdx.x;
-    double v10[10];
+    double v13[NSUM];
 #pragma unroll
-    for (int m = 0; m < 10; ++m) v10[m] = 0.0;
+    for (int m = 0; m < NSUM; ++m) v13[m] = 0.0;
     if (i < n) {
         const int64_t j = nxt[i];
         const double dx = pos[j] - pos[i], dy = pos[n + j] - pos[n + i], dz = pos[2 * n + j] - pos[2 * n + i];
@@ -229,10 +232,12 @@ __global__ void __launch_bounds__(RED_TPB) lp_euler_kernel(
         const double cx = dy * vz - dz * vy, cy = dz * vx - dx * vz, cz = dx * vy - dy * vx;  // L t x vbar
         const int k = loop_of[i];
         const double b0 = loop_b[3 * k], b1 = loop_b[3 * k + 1], b2 = loop_b[3 * k + 2];
-        v10[0] = b0 * cx; v10[1] = b0 * cy; v10[2] = b0 * cz;
-        v10[3] = b1 * cx; v10[4] = b1 * cy; v10[5] = b1 * cz;
-        v10[6] = b2 * cx; v10[7] = b2 * cy; v10[8] = b2 * cz;
-        v10[9] = sqrt(dx * dx + dy * dy + dz * dz);
+        const double L = sqrt(dx * dx + dy * dy + dz * dz);
+        v13[0] = b0 * cx; v13[1] = b0 * cy; v13[2] = b0 * cz;
+        v13[3] = b1 * cx; v13[4] = b1 * cy; v13[5] = b1 * cz;
+        v13[6] = b2 * cx; v13[7] = b2 * cy; v13[8] = b2 * cz;
+        v13[9] = L;
+        v13[10] = L * vx; v13[11] = L * vy; v13[12] = L * vz;
         // explicit Euler (all nodes from the step-start state)
         const double nxp = __dadd_rn(pos[i], __dmul_rn(vel[i], dt));
         const double nyp = __dadd_rn(pos[n + i], __dmul_rn(vel[n + i], dt));
@@ -243,41 +248,44 @@ __global__ void __launch_bounds__(RED_TPB) lp_euler_kernel(
         if (!isfinite(nxp) || !isfinite(nyp) || !isfinite(nzp)) atomicOr(flag, 1);
     }
 #pragma unroll
-    for (int m = 0; m < 10; ++m) {
-        double v = v10[m];
+    for (int m = 0; m < NSUM; ++m) {
+        double v = v13[m];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][m] = v;
     }
     __syncthreads();
-    if (threadIdx.x < 10) {
+    if (threadIdx.x < NSUM) {
         double s = 0.0;
 #pragma unroll
         for (int w = 0; w < RED_TPB / 32; ++w) s += red[w][threadIdx.x];
-        partial[blockIdx.x * 10 + threadIdx.x] = s;
+        partial[blockIdx.x * NSUM + threadIdx.x] = s;
     }
 }
 
-// One block: sum the per-block partials in a fixed order, add dt-weighted.
+// One block: sum the per-block partials in a fixed order, add dt-weighted
+// into acc[0..9] (Lp, rho) and acc[13..15] (polar velocity).
 __global__ void lp_finish_kernel(int nblk, const double* __restrict__ partial, double dt, double* __restrict__ acc)
 {
-    __shared__ double red[256][10];
-    double s[10];
+    __shared__ double red[256][NSUM];
+    double s[NSUM];
 #pragma unroll
-    for (int m = 0; m < 10; ++m) s[m] = 0.0;
+    for (int m = 0; m < NSUM; ++m) s[m] = 0.0;
     for (int b = threadIdx.x; b < nblk; b += 256)
 #pragma unroll
-        for (int m = 0; m < 10; ++m) s[m] += partial[b * 10 + m];
+        for (int m = 0; m < NSUM; ++m) s[m] += partial[b * NSUM + m];
 #pragma unroll
-    for (int m = 0; m < 10; ++m) red[threadIdx.x][m] = s[m];
+    for (int m = 0; m < NSUM; ++m) red[threadIdx.x][m] = s[m];
     __syncthreads();
     for (int h = 128; h > 0; h >>= 1) {
         if (threadIdx.x < h)
 #pragma unroll
-            for (int m = 0; m < 10; ++m) red[threadIdx.x][m] += red[threadIdx.x + h][m];
+            for (int m = 0; m < NSUM; ++m) red[threadIdx.x][m] += red[threadIdx.x + h][m];
         __syncthreads();
     }
     if (threadIdx.x < 10) acc[threadIdx.x] = fma(red[0][threadIdx.x], dt, acc[threadIdx.x]);
+    if (threadIdx.x >= 10 && threadIdx.x < NSUM)
+        acc[threadIdx.x + 3] = fma(red[0][threadIdx.x], dt, acc[threadIdx.x + 3]);
     if (threadIdx.x == 9) acc[11] = red[0][9];  // the step's line length (junction jumps weight it)
 }
 

@@ -2,17 +2,24 @@
 // thermally activated breaking (Sec. 2.2), inside the burst of
 // ptadd_advance.
 //
-// Per step, between the velocity stage and the Euler stage:
-//   junction_update_kernel (one thread per node, sessile segments staged
-//     through shared memory in index order): release the node's junction if
-//     its break time has come, else look for the lowest-index sessile
-//     segment of another loop within the capture radius (not of the sessile
-//     loop the node last broke away from) and form a junction breaking
-//     after f a; hold the velocity of a held node at 0.  The largest squared
-//     speed of the free nodes, the number of held junctions and the earliest
-//     break time are reduced with 64-bit atomics on the bit patterns of
-//     non-negative doubles, whose integer order is their numeric order, so
-//     the result does not depend on the order of the atomics.
+// Per step, between the velocity stage and the Euler stage, three kernels:
+//   junction_release_kernel (one thread per node): a held node whose break
+//     time has come lets go (and remembers the sessile loop it left); every
+//     free node that holds nothing goes on the list of nodes looking for a
+//     junction, with its best candidate reset;
+//   junction_search_kernel (one warp per (looking node, 32 sessile
+//     segments), spread over every SM): each lane tests one sessile segment
+//     of another loop (not the one the node last left) against the capture
+//     radius; the warp's lowest passing position in the sessile list goes
+//     into the node's candidate with an atomic minimum, so the lowest-index
+//     segment wins whatever the order of the warps;
+//   junction_hold_kernel (one thread per node): forms the junction found
+//     (breaking after f a), holds the velocity of a held node at 0, and
+//     reduces the largest squared speed of the free nodes, the number of
+//     held junctions and the earliest break time with 64-bit atomics on the
+//     bit patterns of non-negative doubles, whose integer order is their
+//     numeric order, so the result does not depend on the order of the
+//     atomics.
 // after the Euler stage:
 //   junction_event_kernel (one thread): t <- t + dt, or, if some junction is
 //     held and no free node moved more than the stuck displacement, t <- the
@@ -23,6 +30,7 @@
 // no contraction, so a decision depends only on the positions and the clock.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <vector>
@@ -45,6 +53,10 @@ struct DevJunctions {
     double* clock = nullptr;     // [0] DD time, [1] time jumped (s)
     unsigned long long* red = nullptr;  // [0] max v^2 bits, [1] min break bits, [2] held,
                                         // [3] formed, [4] broken, [5] jumps
+    int64_t n_free = 0;          // unpinned nodes (the most that can look in one step)
+    int32_t* look = nullptr;     // nodes looking for a junction this step (any order)
+    unsigned* look_n = nullptr;  // their number (reset by the event kernel)
+    int32_t* found = nullptr;    // per node: lowest passing position in sess, or INT32_MAX
 };
 
 namespace {
@@ -84,70 +96,72 @@ __device__ __forceinline__ double seg_dist2(double x, double y, double z, const 
     return __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
 }
 
-__global__ void __launch_bounds__(JT) junction_update_kernel(
-    int64_t n, const double* __restrict__ pos, const int32_t* __restrict__ nxt, const int32_t* __restrict__ loop_of,
-    const uint8_t* __restrict__ pinned, double* __restrict__ vel, const int32_t* __restrict__ sess, int64_t n_sess,
-    int32_t* __restrict__ jseg, int32_t* __restrict__ jlast, int32_t* __restrict__ jcount, double* __restrict__ jbrk,
-    const double* __restrict__ clock, double rc2, double a, uint64_t seed, unsigned long long* __restrict__ red)
+__global__ void __launch_bounds__(JT) junction_release_kernel(
+    int64_t n, const int32_t* __restrict__ loop_of, const uint8_t* __restrict__ pinned, int32_t* __restrict__ jseg,
+    int32_t* __restrict__ jlast, const double* __restrict__ jbrk, const double* __restrict__ clock,
+    int32_t* __restrict__ look, unsigned* __restrict__ look_n, int32_t* __restrict__ found,
+    unsigned long long* __restrict__ red)
 {
-    __shared__ double sp[JT][6];
-    __shared__ int32_t sidx[JT], sloop[JT];
     const int64_t p = blockIdx.x * (int64_t)JT + threadIdx.x;
-    const bool mine = p < n && !pinned[p];
-    const double t = clock[0];
-    int32_t js = -1, jl = -1, myloop = -2;
-    double x = 0, y = 0, z = 0;
-    if (mine) {
-        js = jseg[p];
-        jl = jlast[p];
-        myloop = loop_of[p];
-        x = pos[p];
-        y = pos[n + p];
-        z = pos[2 * n + p];
-        if (js >= 0 && jbrk[p] <= t) {
-            jl = loop_of[js];
-            js = -1;
-            atomicAdd(&red[4], 1ull);
+    if (p >= n || pinned[p]) return;
+    int32_t js = jseg[p];
+    if (js >= 0 && jbrk[p] <= clock[0]) {
+        jlast[p] = loop_of[js];
+        jseg[p] = -1;
+        js = -1;
+        atomicAdd(&red[4], 1ull);
+    }
+    if (js < 0) {
+        found[p] = INT32_MAX;
+        look[atomicAdd(look_n, 1u)] = (int32_t)p;
+    }
+}
+
+// Block: JSW warps; warp w of block (x, y) tests look[x JSW + w] against the
+// sessile positions 32 y .. 32 y + 31, one per lane.
+constexpr int JSW = 8;
+
+__global__ void __launch_bounds__(32 * JSW) junction_search_kernel(
+    int64_t n, const double* __restrict__ pos, const int32_t* __restrict__ nxt, const int32_t* __restrict__ loop_of,
+    const int32_t* __restrict__ sess, int64_t n_sess, const int32_t* __restrict__ jlast,
+    const int32_t* __restrict__ look, const unsigned* __restrict__ look_n, int32_t* __restrict__ found, double rc2)
+{
+    const int li = blockIdx.x * JSW + (threadIdx.x >> 5);
+    if (li >= (int)*look_n) return;  // warp-uniform
+    const int64_t k = (int64_t)blockIdx.y * 32 + (threadIdx.x & 31);
+    const int32_t p = look[li];
+    bool hit = false;
+    if (k < n_sess) {
+        const int32_t sg = sess[k];
+        const int32_t sl = loop_of[sg];
+        if (sl != loop_of[p] && sl != jlast[p]) {
+            const int32_t e = nxt[sg];
+            const double sp[6] = {pos[sg], pos[n + sg], pos[2 * n + sg], pos[e], pos[n + e], pos[2 * n + e]};
+            hit = seg_dist2(pos[p], pos[n + p], pos[2 * n + p], sp) < rc2;
         }
     }
-    bool look = mine && js < 0;
-    bool formed = false;
-    for (int64_t base = 0; base < n_sess; base += JT) {
-        if (!__syncthreads_or(look)) break;  // block-uniform
-        const int cnt = (int)min((int64_t)JT, n_sess - base);
-        if (threadIdx.x < cnt) {
-            const int32_t s = sess[base + threadIdx.x];
-            const int32_t e = nxt[s];
-            sp[threadIdx.x][0] = pos[s];
-            sp[threadIdx.x][1] = pos[n + s];
-            sp[threadIdx.x][2] = pos[2 * n + s];
-            sp[threadIdx.x][3] = pos[e];
-            sp[threadIdx.x][4] = pos[n + e];
-            sp[threadIdx.x][5] = pos[2 * n + e];
-            sidx[threadIdx.x] = s;
-            sloop[threadIdx.x] = loop_of[s];
-        }
-        __syncthreads();
-        if (look)
-            for (int k = 0; k < cnt; ++k) {
-                if (sloop[k] == myloop || sloop[k] == jl) continue;
-                if (seg_dist2(x, y, z, sp[k]) < rc2) {
-                    js = sidx[k];
-                    look = false;
-                    formed = true;
-                    break;
-                }
-            }
-    }
-    if (!mine) return;
-    if (formed) {
+    const unsigned cand = hit ? (unsigned)k : 0xFFFFFFFFu;
+    const unsigned best = __reduce_min_sync(0xffffffffu, cand);
+    if ((threadIdx.x & 31) == 0 && best != 0xFFFFFFFFu) atomicMin(&found[p], (int32_t)best);
+}
+
+__global__ void __launch_bounds__(JT) junction_hold_kernel(
+    int64_t n, const uint8_t* __restrict__ pinned, double* __restrict__ vel, const int32_t* __restrict__ sess,
+    int32_t* __restrict__ jseg, int32_t* __restrict__ jcount, double* __restrict__ jbrk,
+    const int32_t* __restrict__ found, const double* __restrict__ clock, double a, uint64_t seed,
+    unsigned long long* __restrict__ red)
+{
+    const int64_t p = blockIdx.x * (int64_t)JT + threadIdx.x;
+    if (p >= n || pinned[p]) return;
+    int32_t js = jseg[p];
+    if (js < 0 && found[p] != INT32_MAX) {
+        js = sess[found[p]];
         const int32_t k = jcount[p];
-        jbrk[p] = __dadd_rn(t, __dmul_rn(a, break_fraction(seed, p, k)));
+        jbrk[p] = __dadd_rn(clock[0], __dmul_rn(a, break_fraction(seed, p, k)));
         jcount[p] = k + 1;
+        jseg[p] = js;
         atomicAdd(&red[3], 1ull);
     }
-    jseg[p] = js;
-    jlast[p] = jl;
     if (js >= 0) {
         vel[p] = 0.0;
         vel[n + p] = 0.0;
@@ -161,10 +175,11 @@ __global__ void __launch_bounds__(JT) junction_update_kernel(
 }
 
 __global__ void junction_event_kernel(double* __restrict__ clock, unsigned long long* __restrict__ red,
-                                      double* __restrict__ acc, double dt_s, double dt_hat, double stuck_hat,
-                                      double time_scale)
+                                      double* __restrict__ acc, unsigned* __restrict__ look_n, double dt_s,
+                                      double dt_hat, double stuck_hat, double time_scale)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    *look_n = 0u;
     const double t1 = __dadd_rn(clock[0], dt_s);
     const double vmax = sqrt(__longlong_as_double((long long)red[0]));
     const double tmin = __longlong_as_double((long long)red[1]);
@@ -190,7 +205,7 @@ void junctions_free(ptadd_ctx* ctx)
 {
     DevJunctions* j = ctx->junc;
     if (!j) return;
-    void* ptrs[] = {j->sess, j->seg, j->last, j->count, j->brk, j->clock, j->red};
+    void* ptrs[] = {j->sess, j->seg, j->last, j->count, j->brk, j->clock, j->red, j->look, j->look_n, j->found};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     delete j;
@@ -202,16 +217,27 @@ cudaError_t launch_junction_update(ptadd_ctx* ctx, cudaStream_t st)
     DevJunctions* j = ctx->junc;
     const DevNetwork& net = ctx->net;
     const int64_t n = net.n_nodes;
-    junction_update_kernel<<<(unsigned)((n + JT - 1) / JT), JT, 0, st>>>(
-        n, net.pos[net.cur], net.nxt, net.loop_of, net.pinned, net.vel, j->sess, j->n_sess, j->seg, j->last,
-        j->count, j->brk, j->clock, j->rc2, j->a, j->seed, j->red);
+    const unsigned nb = (unsigned)((n + JT - 1) / JT);
+    junction_release_kernel<<<nb, JT, 0, st>>>(n, net.loop_of, net.pinned, j->seg, j->last, j->brk, j->clock,
+                                               j->look, j->look_n, j->found, j->red);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (j->n_free > 0 && j->n_sess > 0) {
+        const dim3 grid((unsigned)((j->n_free + JSW - 1) / JSW), (unsigned)((j->n_sess + 31) / 32));
+        junction_search_kernel<<<grid, 32 * JSW, 0, st>>>(n, net.pos[net.cur], net.nxt, net.loop_of, j->sess,
+                                                          j->n_sess, j->last, j->look, j->look_n, j->found, j->rc2);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    junction_hold_kernel<<<nb, JT, 0, st>>>(n, net.pinned, net.vel, j->sess, j->seg, j->count, j->brk, j->found,
+                                            j->clock, j->a, j->seed, j->red);
     return cudaGetLastError();
 }
 
 cudaError_t launch_junction_event(ptadd_ctx* ctx, double dt_s, double dt_hat, cudaStream_t st)
 {
     DevJunctions* j = ctx->junc;
-    junction_event_kernel<<<1, 32, 0, st>>>(j->clock, j->red, ctx->net.acc, dt_s, dt_hat, j->stuck_hat,
+    junction_event_kernel<<<1, 32, 0, st>>>(j->clock, j->red, ctx->net.acc, j->look_n, dt_s, dt_hat, j->stuck_hat,
                                              ctx->mat.mu / ctx->mat.B);
     return cudaGetLastError();
 }
@@ -283,8 +309,11 @@ extern "C" ptadd_status ptadd_set_junctions(ptadd_ctx* ctx, const ptadd_junction
     PTADD_CUDA(cudaMemcpy(pin.data(), net.pinned, n, cudaMemcpyDeviceToHost));
     PTADD_CUDA(cudaMemcpy(nxt.data(), net.nxt, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
     std::vector<int32_t> sess;
-    for (int64_t i = 0; i < n; ++i)
+    int64_t n_free = 0;
+    for (int64_t i = 0; i < n; ++i) {
         if (pin[i] && pin[nxt[i]]) sess.push_back((int32_t)i);
+        n_free += pin[i] ? 0 : 1;
+    }
 
     DevJunctions* j = new DevJunctions;
     ctx->junc = j;
@@ -294,6 +323,7 @@ extern "C" ptadd_status ptadd_set_junctions(ptadd_ctx* ctx, const ptadd_junction
     j->stuck_hat = p->stuck_disp / l;
     j->seed = p->seed;
     j->n_sess = (int64_t)sess.size();
+    j->n_free = n_free;
     cudaError_t e = cudaSuccess;
     auto al = [&](void** q, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(q, bytes > 0 ? bytes : 1);
@@ -305,6 +335,9 @@ extern "C" ptadd_status ptadd_set_junctions(ptadd_ctx* ctx, const ptadd_junction
     al((void**)&j->brk, n * sizeof(double));
     al((void**)&j->clock, 2 * sizeof(double));
     al((void**)&j->red, 6 * sizeof(unsigned long long));
+    al((void**)&j->look, (size_t)n * sizeof(int32_t));
+    al((void**)&j->look_n, sizeof(unsigned));
+    al((void**)&j->found, (size_t)n * sizeof(int32_t));
     if (e != cudaSuccess) {
         set_error("ptadd_set_junctions: cudaMalloc failed: %s", cudaGetErrorString(e));
         junctions_free(ctx);
@@ -322,6 +355,7 @@ extern "C" ptadd_status ptadd_set_junctions(ptadd_ctx* ctx, const ptadd_junction
     chk(cudaMemset(j->brk, 0, n * sizeof(double)));
     chk(cudaMemcpy(j->clock, clock0, sizeof(clock0), cudaMemcpyHostToDevice));
     chk(cudaMemcpy(j->red, red0, sizeof(red0), cudaMemcpyHostToDevice));
+    chk(cudaMemset(j->look_n, 0, sizeof(unsigned)));
     if (e != cudaSuccess) {  // leave junctions off rather than half set
         set_error("ptadd_set_junctions: initialising the junction state failed: %s", cudaGetErrorString(e));
         junctions_free(ctx);

@@ -233,7 +233,7 @@ ptadd_status ptadd_set_network(ptadd_ctx* ctx, int64_t n_nodes, const double* xy
     ALLOC(net.fpart, (size_t)net.max_chunks * 6 * n);
     ALLOC(net.vel, 3 * n);
     ALLOC(net.force, 3 * n);
-    ALLOC(net.partial, (size_t)net.max_red_blocks * 10);
+    ALLOC(net.partial, (size_t)net.max_red_blocks * 13);
     ALLOC(net.acc, 16);
     ALLOC(net.flag, 1);
     ALLOC(net.staging, 3 * n);
@@ -270,6 +270,7 @@ ptadd_status ptadd_set_network(ptadd_ctx* ctx, int64_t n_nodes, const double* xy
     PTADD_CUDA(cudaStreamSynchronize(s));
     for (int c = 0; c < 6; ++c) ctx->sig_app[c] = 0.0;
     ctx->have_net = true;
+    ctx->have_LV = false;
     return PTADD_OK;
 }
 
@@ -379,7 +380,7 @@ ptadd_status ptadd_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, double Lp
         if (st != PTADD_OK) return st;
         if (ctx->junc) {
             PTADD_CUDA(launch_junction_update(ctx, s));
-            ctx->kernel_launches += 1;
+            ctx->kernel_launches += 3;
         }
         PTADD_CUDA(launch_lp_euler(net, dt_hat, s));
         ctx->kernel_launches += 2;
@@ -388,9 +389,9 @@ ptadd_status ptadd_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, double Lp
             ctx->kernel_launches += 1;
         }
     }
-    double acc[13];
+    double acc[16];
     int flag = 0;
-    PTADD_CUDA(cudaMemcpyAsync(acc, net.acc, 13 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PTADD_CUDA(cudaMemcpyAsync(acc, net.acc, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
     PTADD_CUDA(cudaMemcpyAsync(&flag, net.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     PTADD_CUDA(cudaStreamSynchronize(s));
     {
@@ -408,10 +409,29 @@ ptadd_status ptadd_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, double Lp
     if (Lp_avg)
         for (int m = 0; m < 9; ++m) Lp_avg[m] = n_steps > 0 ? acc[m] / St * lp_scale : 0.0;
     if (rho_avg) *rho_avg = n_steps > 0 ? acc[9] / St * rho_scale : 0.0;
+    // R^V of Eq. 2.11 without the factor A (applied by ptadd_get_polar_velocity):
+    // (1/|B|) sum L vbar, in SI (L in l, v in l mu / B)
+    const double v_scale = l * l * ctx->mat.mu / (ctx->mat.B * net.volume);
+    for (int m = 0; m < 3; ++m) ctx->last_LV[m] = n_steps > 0 ? acc[13 + m] / St * v_scale : 0.0;
+    ctx->have_LV = true;
+    for (int m = 13; m < 16; ++m) finite = finite && isfinite(acc[m]);
     if (!finite) {
         set_error("burst produced a non-finite position or average");
         return PTADD_ERR_NONFINITE;
     }
+    return PTADD_OK;
+}
+
+ptadd_status ptadd_get_polar_velocity(ptadd_ctx* ctx, double core_area, double V_avg[3])
+{
+    if (!ctx) return arg_error("null context");
+    if (!V_avg) return arg_error("V_avg is NULL");
+    if (!(core_area > 0) || !isfinite(core_area)) return arg_error("core_area must be positive and finite");
+    if (!ctx->have_LV) {
+        set_error("no burst has run since the network was set");
+        return PTADD_ERR_STATE;
+    }
+    for (int m = 0; m < 3; ++m) V_avg[m] = core_area * ctx->last_LV[m];
     return PTADD_OK;
 }
 

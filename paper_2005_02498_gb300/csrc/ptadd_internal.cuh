@@ -75,10 +75,11 @@ struct DevNetwork {
     int max_chunks = 0;
     double* vel = nullptr;         // SoA [3*n]
     double* force = nullptr;       // SoA [3*n] (last evaluated nodal force)
-    double* partial = nullptr;     // [max_blocks*10]
+    double* partial = nullptr;     // [max_blocks*13]
     int max_red_blocks = 0;
     double* acc = nullptr;         // [16]: 0..8 sum Lp dt, 9 sum rho dt, 11 line length of the last
-                                   // step, 12 time jumped over while stuck (junctions)
+                                   // step, 12 time jumped over while stuck (junctions), 13..15 sum
+                                   // (sum_s L vbar) dt (polar velocity)
     int* flag = nullptr;           // non-finite flag
     double* staging = nullptr;     // [3*n] AoS SI positions in / out
     double volume = 0;             // m^3
@@ -141,6 +142,10 @@ struct ptadd_ctx {
     ptadd::MlpDev* mlp = nullptr;      // surrogate (ptadd_mlp_* / ptadd_surrogate_*)
     ptadd::DevJunctions* junc = nullptr;  // junctions (ptadd_set_junctions), NULL: off
     double sig_app[6] = {0, 0, 0, 0, 0, 0};  // Pa
+    // (1/|B|) sum_s L vbar of the last burst, time-averaged, SI (the polar velocity
+    // of Eq. 2.11 divided by the core area)
+    double last_LV[3] = {0, 0, 0};
+    bool have_LV = false;
     // profiling (ptadd_profile_*)
     bool timing = false;
     int64_t kernel_launches = 0, pair_launches = 0, pair_evals = 0;

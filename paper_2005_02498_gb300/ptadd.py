@@ -28,11 +28,13 @@ EXPORTS = ["ptadd_version", "ptadd_create", "ptadd_destroy", "ptadd_last_error",
            "ptadd_profile_reset", "ptadd_profile_read", "ptadd_forces_noalloc",
            "ptadd_batch_set", "ptadd_batch_set_stress", "ptadd_batch_advance", "ptadd_batch_get_nodes",
            "ptadd_batch_set_nodes", "ptadd_batch_get_info", "ptadd_batch_autotune", "ptadd_batch_run",
-           "ptadd_batch_configure", "ptadd_batch_get_forces",
+           "ptadd_batch_configure", "ptadd_batch_get_forces", "ptadd_get_polar_velocity",
+           "ptadd_batch_get_polar_velocity",
            "ptadd_gemm_bf16", "ptadd_gemm_timeout_selftest", "ptadd_mlp_param_count", "ptadd_mlp_init", "ptadd_mlp_set_params",
            "ptadd_mlp_get_params", "ptadd_mlp_loss_grad", "ptadd_mlp_train", "ptadd_mlp_forward",
            "ptadd_surrogate_fit", "ptadd_surrogate_predict", "ptadd_surrogate_predict_dev",
            "ptadd_closure_sweep", "ptadd_closure_realisation", "ptadd_dissipation_projection",
+           "ptadd_dissipation_projection_dev",
            "ptadd_block_average", "ptadd_block_stress_pair", "ptadd_set_junctions", "ptadd_get_junctions", "ptadd_system_densities",
            "ptadd_surrogate_get_state", "ptadd_surrogate_set_state"]
 NOALLOC_MAX_SEGMENTS = 16384
@@ -148,6 +150,10 @@ def load(build_if_missing=True):
     lib.ptadd_batch_get_info.restype = st
     lib.ptadd_batch_autotune.argtypes = [_VP, ctypes.c_char_p, ctypes.c_int]
     lib.ptadd_batch_autotune.restype = st
+    lib.ptadd_get_polar_velocity.argtypes = [_VP, ctypes.c_double, _D]
+    lib.ptadd_get_polar_velocity.restype = st
+    lib.ptadd_batch_get_polar_velocity.argtypes = [_VP, ctypes.c_double, _D]
+    lib.ptadd_batch_get_polar_velocity.restype = st
     lib.ptadd_batch_configure.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32]
     lib.ptadd_batch_configure.restype = st
     lib.ptadd_batch_get_forces.argtypes = [_VP, _D]
@@ -189,6 +195,8 @@ def load(build_if_missing=True):
     lib.ptadd_closure_realisation.restype = st
     lib.ptadd_dissipation_projection.argtypes = [_D, _D, _D, _D]
     lib.ptadd_dissipation_projection.restype = st
+    lib.ptadd_dissipation_projection_dev.argtypes = [ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP]
+    lib.ptadd_dissipation_projection_dev.restype = st
     _I32 = ctypes.POINTER(ctypes.c_int32)
     lib.ptadd_set_junctions.argtypes = [_VP, ctypes.POINTER(JunctionParams)]
     lib.ptadd_set_junctions.restype = st
@@ -286,6 +294,14 @@ def dissipation_projection(T6, Lp, V=None, alpha=None):
     _check(lib.ptadd_dissipation_projection(_dptr(t), _dptr(a) if a is not None else None, _dptr(L),
                                             _dptr(v) if v is not None else None))
     return L.reshape(3, 3), v
+
+
+def dissipation_projection_dev(n_points, T6_ptr, Lp_ptr, alpha_ptr=None, V_ptr=None, n_bad_ptr=None, stream=None):
+    """ptadd_dissipation_projection_dev on caller-owned device arrays (raw pointers)."""
+    lib = load()
+    _check(lib.ptadd_dissipation_projection_dev(int(n_points), _VP(T6_ptr), _VP(alpha_ptr) if alpha_ptr else None,
+                                                _VP(Lp_ptr), _VP(V_ptr) if V_ptr else None,
+                                                _VP(n_bad_ptr) if n_bad_ptr else None, _VP(stream) if stream else None))
 
 
 def system_densities(net, xyz=None):
@@ -430,6 +446,12 @@ class Context:
         _check(self._lib.ptadd_advance(self._h, int(n_steps), float(dt), _dptr(Lp), ctypes.byref(rho)))
         return Lp.reshape(3, 3), rho.value
 
+    def get_polar_velocity(self, core_area):
+        """R^V (m/s) of the last burst, Eq. 2.11 with one core area for every segment."""
+        V = np.zeros(3)
+        _check(self._lib.ptadd_get_polar_velocity(self._h, float(core_area), _dptr(V)))
+        return V
+
     def get_nodes(self):
         out = np.zeros((self.n_nodes, 3))
         _check(self._lib.ptadd_get_nodes(self._h, _dptr(out)))
@@ -537,6 +559,12 @@ class Context:
         i = BatchInfo()
         _check(self._lib.ptadd_batch_get_info(self._h, ctypes.byref(i)))
         return {k: getattr(i, k) for k, _ in BatchInfo._fields_}
+
+    def batch_get_polar_velocity(self, core_area):
+        """R^V [R, 3] (m/s) of the last batch burst."""
+        V = np.zeros(3 * self.batch_R)
+        _check(self._lib.ptadd_batch_get_polar_velocity(self._h, float(core_area), _dptr(V)))
+        return V.reshape(-1, 3)
 
     def batch_configure(self, tile_targets, chunk_sources):
         _check(self._lib.ptadd_batch_configure(self._h, int(tile_targets), int(chunk_sources)))

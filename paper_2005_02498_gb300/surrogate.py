@@ -62,9 +62,11 @@ def feature_points(rng, n, rho_min=2e12, rho_max=2e13, stress_max=200e6):
     return f
 
 
-def generate(ctx, feats, members, seed, steps, dt, n_loops=128, chunk=512, stratified=True):
+def generate(ctx, feats, members, seed, steps, dt, n_loops=128, chunk=512, stratified=True, singles=None):
     """DD closures at the given feature points: the mean of sym(R^Lp) over
-    `members` realisations drawn for each point (realisation_for_densities)."""
+    `members` realisations drawn for each point (realisation_for_densities).
+    If `singles` is an array [n, members, 6], every realisation's closure is
+    also stored there."""
     rng = np.random.default_rng(seed)
     n = feats.shape[0]
     jobs = [(i, m) for i in range(n) for m in range(members)]
@@ -78,8 +80,10 @@ def generate(ctx, feats, members, seed, steps, dt, n_loops=128, chunk=512, strat
                 for i, _ in part]
         lab = label(ctx, W.batch_from_networks(nets), steps, dt)
         pairs += ctx.batch_info()["pairs_per_step"] * steps
-        for (i, _), y in zip(part, lab):
+        for (i, m), y in zip(part, lab):
             acc[i] += y
+            if singles is not None:
+                singles[i, m] = y
     return acc / members, time.perf_counter() - t0, pairs
 
 
@@ -188,6 +192,41 @@ def relerr(pred, ref):
     return float(np.linalg.norm(pred - ref) / np.linalg.norm(ref))
 
 
+def fit_early_stopping(ctx, Xfit, Yfit, Xval, Yval, augment=True, epochs=60, round_epochs=1, patience=3,
+                       lr_drops=2, batch=512, lr=1e-3, seed=0):
+    """Fit the context's surrogate on (Xfit, Yfit) with early stopping.
+
+    The labels are single noisy realisations, so the network is trained in
+    rounds of `round_epochs` and the round with the lowest relative error on
+    the validation split (also single realisations, never augmented) is
+    kept; on a plateau of `patience` rounds the best state is restored and
+    the learning rate cut by 0.3, up to `lr_drops` times.  With `augment`
+    every fit sample enters in its 48 symmetric forms (cubic_images).
+    Returns (best validation error, [[epoch, lr, loss, val err], ...], fit samples)."""
+    if augment:
+        Xfit, Yfit = cubic_images(Xfit, Yfit)
+        order = np.random.default_rng(seed + 11).permutation(Xfit.shape[0])
+        Xfit, Yfit = Xfit[order], Yfit[order]
+    best, best_err, curve, bad, drops, ep = None, np.inf, [], 0, 0, 0
+    while ep < epochs:
+        losses = ctx.surrogate_fit(Xfit, Yfit, epochs=round_epochs, batch=batch, lr=lr, seed=seed + ep)
+        ep += round_epochs
+        pv, _ = ctx.surrogate_predict(Xval)
+        e = relerr(pv, Yval)
+        curve.append([ep, lr, float(losses[-1]), e])
+        if e < best_err - 1e-4:
+            best, best_err, bad = ctx.surrogate_get_state(), e, 0
+        else:
+            bad += 1
+            if bad >= patience:
+                if drops >= lr_drops:
+                    break
+                ctx.surrogate_set_state(best)
+                lr, drops, bad = lr * 0.3, drops + 1, 0
+    ctx.surrogate_set_state(best)
+    return best_err, curve, int(Xfit.shape[0])
+
+
 def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--samples", type=int, default=20000)
@@ -237,37 +276,14 @@ def main(argv=None):
             out.update({"dd_label_s": t_gen, "dd_closures_per_s": ntr / t_gen, "dd_pair_evals_per_s": pairs / t_gen,
                         "holdout_label_s": t_ho})
             Y1, _, _ = generate(ctx, X[ntr:ntr + nev], 1, a.seed + 3, a.steps, a.dt, a.loops)
-        # early stopping: the labels are single noisy realisations, so the
-        # network is trained in rounds and the round with the lowest error on
-        # a validation split (also single realisations, never augmented) is
-        # kept; on a plateau the best state is restored and the learning rate
-        # cut, up to --lr-drops times
         nval = max(64, int(a.val_frac * ntr))
         nfit = ntr - nval
-        Xf, Yf = X[:nfit], Ytr[:nfit]
-        if a.augment:
-            Xf, Yf = cubic_images(Xf, Yf)
-            order = np.random.default_rng(a.seed + 11).permutation(Xf.shape[0])
-            Xf, Yf = Xf[order], Yf[order]
-        out["fit_samples"] = int(Xf.shape[0])
         t0 = time.perf_counter()
-        best, best_err, curve, bad, lr, drops, ep = None, np.inf, [], 0, a.lr, 0, 0
-        while ep < a.epochs:
-            losses = ctx.surrogate_fit(Xf, Yf, epochs=a.round_epochs, batch=a.batch, lr=lr, seed=a.seed + ep)
-            ep += a.round_epochs
-            pv, _ = ctx.surrogate_predict(X[nfit:ntr])
-            e = relerr(pv, Ytr[nfit:ntr])
-            curve.append([ep, lr, float(losses[-1]), e])
-            if e < best_err - 1e-4:
-                best, best_err, bad = ctx.surrogate_get_state(), e, 0
-            else:
-                bad += 1
-                if bad >= a.patience:
-                    if drops >= a.lr_drops:
-                        break
-                    ctx.surrogate_set_state(best)
-                    lr, drops, bad = lr * 0.3, drops + 1, 0
-        ctx.surrogate_set_state(best)
+        best_err, curve, fit_samples = fit_early_stopping(ctx, X[:nfit], Ytr[:nfit], X[nfit:ntr], Ytr[nfit:ntr],
+                                                          augment=a.augment, epochs=a.epochs,
+                                                          round_epochs=a.round_epochs, patience=a.patience,
+                                                          lr_drops=a.lr_drops, batch=a.batch, lr=a.lr, seed=a.seed)
+        out["fit_samples"] = fit_samples
         out["train_s"] = time.perf_counter() - t0
         out["training_curve_epoch_lr_loss_valerr"] = curve
         out["best_val_rel_err"] = best_err

@@ -475,3 +475,58 @@ def test_c2g_matrices_orthogonal():
     A_ = np.array([[eval(e, {"sqrt": math.sqrt}) for e in r] for r in rows])
     assert np.allclose(A_ @ A_.T, np.eye(3), atol=1e-15)
     assert abs(np.linalg.det(A_) - 1) < 1e-15
+
+
+# ------------------------------------------------------ polar velocity
+def test_polar_velocity_of_a_rigid_translation():
+    """Every node moving with one velocity u: vbar_s = u on every segment, so
+    V = (A / |B|) sum_s l_s u = A rho u (Eq. 2.11)."""
+    net = W.loop_ensemble(15, 4, 0.5e-6, np.zeros(6), nodes_per_loop=19)
+    u = np.array([3.0, -1.0, 2.0])
+    core = 2.0 * BB ** 2
+    V = O.polar_velocity(net, np.tile(u, (net.n_nodes, 1)), core)
+    seg = np.concatenate([np.roll(net.xyz[a:b], -1, axis=0) - net.xyz[a:b]
+                          for a, b in zip(net.loop_off[:-1], net.loop_off[1:])])
+    rho = np.sum(np.linalg.norm(seg, axis=1)) / net.volume
+    assert rel(V, core * rho * u) < 1e-13
+
+
+@pytest.mark.parametrize("sense", [1.0, -1.0])
+def test_polar_velocity_of_a_half_pinned_polygon(sense):
+    """Regular N-gon under uniform resolved shear tau, no self stress, the
+    nodes on one side of a diameter pinned.  A free node moves at
+    tau |b| cos(pi/N) / B along its radial unit vector r_a (outwards when the
+    loop expands), a pinned one not, and every segment has length
+    l = 2 R sin(pi/N), so
+      V = (A / |B|) sum_s l vbar_s = (A l / |B|) sum_free v_a
+        = s (A l / |B|) (tau |b| cos(pi/N) / B) sum_free r_a,
+    with s = +1 when the loop grows: by the swept-area identity pinned above
+    the signed area A_n (orientation from the node order about n) changes at
+    -(|B| / |b|) Lp:(b_hat (x) n), and the loop grows when that rate has the
+    sign of A_n."""
+    N, R = 32, 400 * A
+    tau, Bd = 20e6, 1e-4
+    mat = (MU, NU, BB, A, Bd)
+    bh, nh = W.fcc_slip_systems()
+    m, n = bh[2], nh[2]
+    e2 = np.cross(n, m)
+    centre = np.array([2.0, -1.0, 0.5]) * 1e-7
+    net = _polygon(N, R, centre, m, e2, BB * m, sense)
+    net.sig_app = voigt(_shear_tensor(m, n, tau))
+    rhat = (net.xyz - centre) / R
+    free = rhat @ m > 0.01
+    net.pinned = (~free).astype(np.uint8)
+    F = O.nodal_forces(mat, net, interactions=False)
+    v = O.velocities(mat, net, F)
+    Lp, _ = O.lp_rho(net, v)
+    signed_area = 0.5 * np.sum(np.cross(net.xyz - centre, np.roll(net.xyz, -1, axis=0) - centre) @ n)
+    s = -np.sign(m @ Lp @ n) * np.sign(signed_area)
+    core = BB ** 2
+    V = O.polar_velocity(net, v, core)
+    l = 2 * R * math.sin(math.pi / N)
+    exp = s * core * l / net.volume * tau * BB * math.cos(math.pi / N) / Bd * rhat[free].sum(axis=0)
+    assert rel(V, exp) < 1e-12
+    assert abs(V @ n) <= 1e-12 * np.linalg.norm(V)  # glide: V lies in the slip plane
+    # a 1-step burst averages the step-start state: its R^V is this V
+    one = O.burst(mat, net, 1, 1e-12, interactions=False, core_area=core)
+    assert rel(one["V_avg"], V) < 1e-14
