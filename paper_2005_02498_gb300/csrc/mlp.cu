@@ -48,6 +48,7 @@ struct MlpDev {
     int64_t cap = 0;  // row capacity of the work buffers (multiple of 128)
     float *W[4] = {}, *b[4] = {}, *mW[4] = {}, *vW[4] = {}, *mb[4] = {}, *vb[4] = {}, *gW[4] = {}, *gb[4] = {};
     __nv_bfloat16 *Wb[4] = {}, *Wt[4] = {};
+    __nv_bfloat16* Wc = nullptr;  // W2, W3 pre-tiled for the fused inference kernel (8 x 256 x 64)
     __nv_bfloat16 *X = nullptr, *Xt = nullptr, *Hb[3] = {}, *Ht[3] = {}, *dY = nullptr, *dYt = nullptr;
     __nv_bfloat16 *dZ[3] = {}, *dZt[3] = {};
     float *Z[3] = {}, *Y = nullptr, *T = nullptr, *loss_part = nullptr;
@@ -107,6 +108,7 @@ void free_mlp(MlpDev& m)
     }
     if (m.err) cudaFree(m.err);
     if (m.d_norm) cudaFree(m.d_norm);
+    if (m.Wc) cudaFree(m.Wc);
     m = MlpDev{};
 }
 
@@ -125,6 +127,7 @@ ptadd_status alloc_params(MlpDev& m)
         if (st == PTADD_OK) st = m_alloc(&m.Wt[l], nw);
     }
     if (st == PTADD_OK) st = m_alloc(&m.err, 1);
+    if (st == PTADD_OK) st = m_alloc(&m.Wc, (size_t)8 * 256 * 64);
     if (st == PTADD_OK) st = m_alloc(&m.d_norm, 4 * NIN + 2 * NOUT + NIN * NIN + 1);
     return st;
 }
@@ -733,7 +736,9 @@ static ptadd_status upload_maps(MlpDev& m)
 
 static double host_feature(const double* raw, int c)
 {
-    return c < 6 ? (double)(float)(raw[c] * (1.0 / SIG_SCALE)) : (double)log10f((float)raw[c] + (float)RHO_FLOOR);
+    // the inference kernel's arithmetic: the input rounded to FP32, then FP32 operations
+    return c < 6 ? (double)((float)raw[c] * (float)(1.0 / SIG_SCALE))
+                 : (double)log10f((float)raw[c] + (float)RHO_FLOOR);
 }
 
 ptadd_status ptadd_surrogate_fit(ptadd_ctx* ctx, int64_t n, const double* feat, const double* lp6, int epochs,
@@ -845,8 +850,8 @@ ptadd_status ptadd_surrogate_predict_dev(ptadd_ctx* ctx, int64_t n, const double
     // one fused persistent kernel: input map, trust region, the four layers, output map
     const __nv_bfloat16* W[4] = {m.Wb[0], m.Wb[1], m.Wb[2], m.Wb[3]};
     const float* b[4] = {m.b[0], m.b[1], m.b[2], m.b[3]};
-    PTADD_CUDA(launch_mlp_infer(feat_dev, n, m.d_norm, W, b, lp6_dev, in_region_dev, m.err, ctx->stream));
-    ctx->kernel_launches += 1;
+    PTADD_CUDA(launch_mlp_infer(feat_dev, n, m.d_norm, W, b, m.Wc, lp6_dev, in_region_dev, m.err, ctx->stream));
+    ctx->kernel_launches += 2;
     return PTADD_OK;
 }
 

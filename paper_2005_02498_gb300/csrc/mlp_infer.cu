@@ -1,34 +1,65 @@
 // mlp_infer.cu -- fused surrogate inference: raw closure inputs -> sym(Lp),
 // the whole 30 -> 256 -> 256 -> 256 -> 6 network in one persistent kernel.
 //
-// One CTA of 512 threads per SM walks 128-row tiles of the input.  Per tile:
-//   1. the tile's raw features arrive in a transposed shared-memory staging
-//      buffer (cp.async, issued while the previous tile was in its layers);
-//      four threads per row each map and standardise 8 of its features
-//      (sigma / 200 MPa, log10(rho + 1e10)), write them as one 8-column slice
-//      of the BF16 row of the layer-1 operand and share them through shared
-//      memory; the trust region (box, and the Mahalanobis distance |L^-1 z|^2
-//      split over the four threads) follows;
-//   2. four tcgen05 MMA chains (BF16 x BF16 -> FP32 in one 256-column TMEM
-//      accumulator) with the hidden activations kept in shared memory: in
-//      every epilogue warp w reads TMEM lanes 32 (w mod 4) .. + 31 (its rows),
-//      columns 64 (w / 4) .. + 63, adds the bias, applies GELU and writes BF16
-//      in the canonical operand layout of the next layer;
-//   3. the last epilogue de-standardises the 6 outputs and writes them in FP64.
-// W1 (256 x 32) and W4 (16 x 256) stay resident in shared memory; W2 and W3
-// (256 x 256 each) stream from L2 in K-chunks of 64 through two buffers
-// filled with cp.async two chunks ahead of the MMAs that read them.  Layouts
-// are the no-swizzle K-major canonical layout of the tensor core (8-row x
-// 16-byte core matrices, K-adjacent core matrices 128 B apart, 8-row groups
-// SBO bytes apart).  Every mbarrier wait has an iteration limit; a wait that
-// gives up sets the error flag and the CTA leaves after a last bounded wait.
+// One CTA per SM walks 128-row tiles of the input with 18 warps in three roles:
+//   * warps 0-15 ("epilogue warps"): per tile they map and standardise the
+//     raw features (sigma / 200 MPa, log10(rho + 1e10)) into the FP16
+//     layer-1 operand (and its rounding residual, for the trust region), test
+//     the box of the trust region, prefetch the features of the tile after
+//     next with cp.async, and run the epilogues: accumulator + bias -> GELU
+//     -> FP16 activations in shared memory, 64 columns at a time (warp w:
+//     TMEM lanes 32 (w mod 4) .. +31, i.e. its rows, and 16 columns), the
+//     Mahalanobis test, and the de-standardised FP64 outputs.  The map of
+//     tile t + 1 runs right after the layer-3 epilogue of tile t, so the
+//     tensor core starts layer 1 of the next tile while the epilogue warps
+//     wait for layer 4 of this one;
+//   * warp 16, lane 0 ("MMA issuer"): issues every tcgen05 MMA, each
+//     weight K-slice as soon as its activation chunk and its weights are in
+//     shared memory, and never waits for an MMA to finish;
+//   * warp 17, lane 0 ("weight producer"): streams W2 and W3 through NST
+//     shared-memory stages in bulk copies (cp.async.bulk, completion counted
+//     on an mbarrier) from a copy of the weights pre-tiled into the canonical
+//     operand layout, refilling a stage once the MMAs that read it are done
+//     (tcgen05.commit on the stage's "empty" barrier).
+// Trust region: the distance d2 = |L^-1 z|^2 is a 128 x 32 x 32 product,
+// W = Z L^-T, that the tensor core computes next to layer 1 (into 32 spare
+// columns of the second accumulator) in split FP16: z = z_hi + z_lo with
+// z_hi the layer-1 operand itself, s L^-1 = L_hi + L_lo with s a power of
+// two that brings max |L^-1| to [2^13, 2^14), and W = z_hi L_hi + z_hi L_lo +
+// z_lo L_hi (the dropped z_lo L_lo term is ~2^-22 relative).  The epilogue
+// warps of the first column slice read their row of W once layer 1 is done
+// and sum w_i^2 / s^2 in FP32.
+// Two TMEM accumulators of 256 columns alternate between the layers (1 -> A,
+// 2 -> B, 3 -> A, 4 -> B), and the activations of a layer are handed over in
+// 64-column chunks, each with its own mbarrier: while the epilogue warps turn
+// chunk c + 1 of layer l's accumulator into activations, the tensor core
+// already runs layer l + 1 on chunk c (its K-slice 64 c .. 64 c + 63).  So
+// the GELU work of a layer runs beside the next layer's MMAs instead of
+// between them.  Per tile: xbar (layer-1 operand ready, 512 arrivals),
+// hbar[4] (activation chunk ready, 512 arrivals each; a chunk's barrier
+// cannot run two phases ahead of the MMA issuer, because its next phase needs
+// the next layer's accumulator, which needs this phase), accbar[4] (layer l's
+// MMAs complete, tcgen05.commit; one barrier per layer, because layer 1 of the
+// next tile may complete before the epilogue has waited for layer 4 of this
+// one), full[NST] / empty[NST] (the weight stages).  Every wait has an
+// iteration limit; a wait that gives up raises a CTA-wide abort flag, every
+// role leaves its loop, the MMA issuer waits (bounded) for its last MMAs and
+// the producer for its last bulk copies, and the kernel frees its tensor
+// memory and sets the error flag.
 //
-// GELU here is 0.5 z (1 + erf(z / sqrt 2)) with erf(x) ~ tanh(x (A + B x^2)),
-// A = 1.12967582605, B = 0.0997927024 (a minimax fit of erf on [0, 6] made
-// for this kernel; |error| <= 2.8e-4), the tanh by the hardware f16x2
-// approximation (one special-function instruction per two values).  The
-// activations are rounded to BF16 (relative step 2^-8 = 3.9e-3) right after,
-// so the approximation stays below the rounding of the value it produces.
+// Operands are FP16 (the trained weights are BF16, which FP16 holds exactly
+// in its normal range; activations and inputs are rounded to FP16, relative
+// step 2^-11), accumulators FP32.  GELU here is 0.5 z (1 + erf(z / sqrt 2))
+// with erf(x) ~ tanh(x (A + B x^2)), A = 1.12967582605, B = 0.0997927024 (a
+// minimax fit of erf on [0, 6] made for this kernel; |error| <= 2.8e-4), the
+// tanh by the hardware f16x2 approximation, and the whole activation in f16x2
+// arithmetic: the kernel stores a' = z (1 + tanh(u)) = 2 GELU(z) and takes
+// the factor 1/2 into the next layer's weights (W2, W3, W4 are scaled by 1/2
+// when they are staged, exactly), so an activation pair costs one FP32 bias
+// add, one conversion, four f16x2 FMA-pipe operations and one special-function
+// operation.  Layer 1's bias rides in the two padding columns of its K = 32
+// operand: the inputs there are 1 and W1's columns hold the bias split into
+// two FP16 parts (b_hi = fp16(b), b_lo = fp16(b - b_hi)).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -40,353 +71,568 @@ namespace ptadd {
 
 namespace {
 
-constexpr int IT = 512;  // threads per CTA (rows per tile: 128)
+constexpr int EW = 16;             // epilogue warps
+constexpr int IT = 32 * EW;        // epilogue threads (rows per tile: 128)
+constexpr int IT_ALL = IT + 64;    // + the MMA warp and the weight-producer warp
 constexpr int NF = 30, NO = 6;
-constexpr int X_BYTES = 128 * 32 * 2;   // layer-1 A operand, SBO 512
+constexpr int X_BYTES = 128 * 32 * 2;   // layer-1 A operand (FP16), SBO 512
 constexpr int W1_BYTES = 256 * 32 * 2;  // SBO 512
 constexpr int W4_BYTES = 16 * 256 * 2;  // SBO 4096
 constexpr int H_BYTES = 128 * 256 * 2;  // hidden activations, SBO 4096
-constexpr int WC_BYTES = 256 * 64 * 2;  // one K-chunk of W2 or W3, SBO 1024
+constexpr int KCH = 64;                 // K per streamed weight chunk
+constexpr int NST = 2;                  // weight stages in shared memory
+constexpr int CPL = 256 / KCH;          // chunks per layer (W2, W3)
+constexpr int WC_BYTES = 256 * KCH * 2; // one K-chunk of W2 or W3, 8-row groups 16 KCH bytes apart
 constexpr int NV_FLOATS = 4 * NF + 2 * NO + NF * NF + 1;
+constexpr int LI_BYTES = 32 * 32 * 2;   // L_hi or L_lo: 32 rows (i) x 32 K (j), SBO 512
+constexpr int MAHA_COL = 288;           // TMEM columns of W (second accumulator, clear of layer 4's 16)
 constexpr int OFF_X = 0;
-constexpr int OFF_W1 = OFF_X + X_BYTES;
-constexpr int OFF_W4 = OFF_W1 + W1_BYTES;
+constexpr int OFF_XLO = OFF_X + X_BYTES;  // z_lo, the same layout
+constexpr int OFF_W1 = OFF_XLO + X_BYTES;
+constexpr int OFF_LH = OFF_W1 + W1_BYTES;
+constexpr int OFF_LL = OFF_LH + LI_BYTES;
+constexpr int OFF_W4 = OFF_LL + LI_BYTES;
 constexpr int OFF_H = OFF_W4 + W4_BYTES;
 constexpr int OFF_WC = OFF_H + H_BYTES;
-constexpr int OFF_NV = OFF_WC + 2 * WC_BYTES;
-constexpr int OFF_D2 = OFF_NV + ((NV_FLOATS * 4 + 15) / 16) * 16;  // [4][128] partial Mahalanobis sums
-constexpr int OFF_B = OFF_D2 + 4 * 128 * 4;                        // biases: 3 x 256 + 16
-constexpr int F_LD = 129;                                          // staging row pitch (doubles)
-constexpr int OFF_F = OFF_B + (3 * 256 + 16) * 4;                  // raw features [30][F_LD], transposed
-constexpr int OFF_Z = OFF_F + NF * F_LD * 8;                       // standardised features [30][128]
-constexpr int INFER_SMEM = OFF_Z + NF * 128 * 4;
+constexpr int OFF_NV = OFF_WC + NST * WC_BYTES;
+constexpr int OFF_B = OFF_NV + ((NV_FLOATS * 4 + 15) / 16) * 16;   // biases: 3 x 256 + 16
+constexpr int OFF_F = OFF_B + (3 * 256 + 16) * 4;                  // raw features of a tile [128][30]
+constexpr int OFF_BOX = OFF_F + 128 * NF * 8;                      // box test per quarter row [4][128]
+static_assert(OFF_F % 16 == 0, "bulk copies into the staging buffer need 16-byte alignment");
+constexpr int INFER_SMEM = OFF_BOX + 4 * 128;
 
 __device__ __forceinline__ uint32_t canon(int r, int k, int sbo)
 {
     return (uint32_t)((r >> 3) * sbo + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(__cvta_generic_to_global(src))
-                 : "memory");
-}
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src)
 {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(__cvta_generic_to_global(src))
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// Row-major BF16 [rows x K] (global) -> canonical layout with 8-row groups sbo apart.
-__device__ __forceinline__ void copy_canon(uint8_t* dst, const __nv_bfloat16* src, int rows, int K, int sbo)
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar)
 {
-    const int per_row = K / 8;
-    for (int v = threadIdx.x; v < rows * per_row; v += IT) {
-        const int r = v / per_row, kc = v % per_row;
-        *reinterpret_cast<uint4*>(dst + (r >> 3) * sbo + kc * 128 + (r & 7) * 16) =
-            *reinterpret_cast<const uint4*>(src + (int64_t)r * K + kc * 8);
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+// bytes (a multiple of 16, both addresses 16-byte aligned) from global to shared, completion on mbar
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+// Raw features of one tile (rows r0 .. r0 + valid - 1, 240 valid bytes a row,
+// contiguous) into the staging buffer, the same layout: one bulk copy with its
+// completion on mbar when the input is 16-byte aligned (issued by one thread),
+// else 8-byte asynchronous copies by every epilogue thread.
+__device__ __forceinline__ void issue_features(bool bulk, uint32_t dst, const double* feat, int64_t r0, int valid,
+                                               uint32_t mbar)
+{
+    if (bulk) {
+        if (threadIdx.x == 0) {
+            fence_async_smem();  // the buffer's last reads were generic
+            mbar_expect_tx(mbar, (uint32_t)valid * 240u);
+            bulk_g2s(dst, feat + r0 * 30, (uint32_t)valid * 240u, mbar);
+        }
+    } else {
+        for (int e = threadIdx.x; e < valid * 30; e += IT) cp_async8(dst + (uint32_t)e * 8, feat + r0 * 30 + e);
+        cp_async_commit();
     }
 }
 
-// Chunk q of the W2/W3 stream (8 per tile: W2 K-chunks 0..3, W3 K-chunks 0..3).
-__device__ __forceinline__ void issue_chunk(uint32_t dst, const __nv_bfloat16* W2, const __nv_bfloat16* W3,
-                                            int64_t q)
+// 2 GELU(z) of two values in f16x2 (see the header for the approximation)
+__device__ __forceinline__ uint32_t gelu2x2_f16(float2 z)
 {
-    const int j = (int)(q & 7);
-    const __nv_bfloat16* W = j < 4 ? W2 : W3;
-    const int k0 = 64 * (j & 3);
-    // a warp covers 8 rows x 4 core-matrix columns: 64 contiguous bytes per row
-    // in global memory, 128 contiguous bytes per 8 threads in shared memory
-    for (int v = threadIdx.x; v < 256 * 8; v += IT) {
-        const int r = (v >> 6) * 8 + (v & 7), kk = (v >> 3) & 7;
-        cp_async16(dst + (r >> 3) * 1024 + kk * 128 + (r & 7) * 16, W + r * 256 + k0 + kk * 8);
-    }
+    const __half2 h = __floats2half2_rn(z.x, z.y);
+    const __half2 z2 = __hmul2(h, h);
+    const __half2 u = __hmul2(h, __hfma2(z2, __float2half2_rn(0.03528185f), __float2half2_rn(0.79880562f)));
+    uint32_t t;  // K3 = B / (2 sqrt 2), K1 = A / sqrt 2
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(*reinterpret_cast<const uint32_t*>(&u)));
+    const __half2 g = __hfma2(h, *reinterpret_cast<const __half2*>(&t), h);
+    return *reinterpret_cast<const uint32_t*>(&g);
 }
 
-// Raw features of one tile (rows r0 .. r0 + valid - 1) into the transposed staging buffer.
-__device__ __forceinline__ void issue_features(uint32_t dst, const double* feat, int64_t r0, int valid)
+// 16 consecutive FP32 columns of this thread's TMEM lane, without waiting:
+// the registers hold the values only after the next tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t r[16])
 {
-    for (int e = threadIdx.x; e < valid * 30; e += IT) {
-        const int row = e / 30, c = e - 30 * row;
-        cp_async8(dst + (uint32_t)(c * F_LD + row) * 8, feat + r0 * 30 + e);
-    }
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// GELU of two values (see the header for the erf approximation).
-__device__ __forceinline__ uint32_t gelu2_bf16(float2 z)
+// Accumulator values (16 columns from c0) [+ bias] -> 2 GELU -> FP16 into H (this thread's row).
+template <bool BIAS>
+__device__ __forceinline__ void epilogue16(const uint32_t r[16], int row, int c0, const float* __restrict__ bias,
+                                           uint8_t* sH)
 {
-    constexpr float K1 = 0.79880562f;  // A / sqrt 2
-    constexpr float K3 = 0.03528185f;  // B / (2 sqrt 2)
-    const float2 z2 = __fmul2_rn(z, z);
-    const float2 u = __fmul2_rn(z, __ffma2_rn(z2, make_float2(K3, K3), make_float2(K1, K1)));
-    const __half2 hu = __floats2half2_rn(u.x, u.y);
-    uint32_t t;
-    asm("tanh.approx.f16x2 %0, %1;" : "=r"(t) : "r"(*reinterpret_cast<const uint32_t*>(&hu)));
-    const float2 th = __half22float2(*reinterpret_cast<const __half2*>(&t));
-    const float2 hz = __fmul2_rn(z, make_float2(0.5f, 0.5f));
-    const float2 g = __ffma2_rn(hz, th, hz);
-    const __nv_bfloat162 h = __floats2bfloat162_rn(g.x, g.y);
-    return *reinterpret_cast<const uint32_t*>(&h);
-}
-
-// Accumulator + bias -> GELU -> BF16 into H: this warp's 32 rows, 64 columns.
-__device__ __forceinline__ void epilogue_hidden(uint32_t tmem_row, int row, int col0, const float* __restrict__ bias,
-                                                uint8_t* sH)
-{
+    uint32_t w[8];
 #pragma unroll
-    for (int c0 = col0; c0 < col0 + 64; c0 += 16) {
-        float v[16];
-        tmem_ld16(tmem_row + (uint32_t)c0, v);
-        uint32_t w[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-            w[i] = gelu2_bf16(__fadd2_rn(make_float2(v[2 * i], v[2 * i + 1]),
-                                         *reinterpret_cast<const float2*>(bias + c0 + 2 * i)));
-        *reinterpret_cast<uint4*>(sH + canon(row, c0, 4096)) = make_uint4(w[0], w[1], w[2], w[3]);
-        *reinterpret_cast<uint4*>(sH + canon(row, c0 + 8, 4096)) = make_uint4(w[4], w[5], w[6], w[7]);
+    for (int i = 0; i < 8; ++i) {
+        float2 z = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+        if (BIAS) z = __fadd2_rn(z, *reinterpret_cast<const float2*>(bias + c0 + 2 * i));
+        w[i] = gelu2x2_f16(z);
     }
+    *reinterpret_cast<uint4*>(sH + canon(row, c0, 4096)) = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(sH + canon(row, c0 + 8, 4096)) = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
-__device__ __forceinline__ float raw_feature(double v, int c)
+// 8 BF16 values -> 8 FP16 values times a power of two (exact in FP16's normal range)
+__device__ __forceinline__ uint4 bf16x8_to_f16x8(uint4 v, float scale)
 {
-    return c < 6 ? (float)(v * (1.0 / 200e6)) : log10f((float)v + 1e10f);
+    uint32_t in[4] = {v.x, v.y, v.z, v.w}, out[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&in[i]));
+        const __half2 h = __floats2half2_rn(f.x * scale, f.y * scale);
+        out[i] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    return make_uint4(out[0], out[1], out[2], out[3]);
+}
+
+// IEEE-754 round-to-nearest-even FP64 -> FP32 and exact FP32 -> FP64 on the
+// integer pipe, for values in the normal FP32 range (others take the
+// hardware conversion, which on this GPU runs on the 1/64-rate FP64 pipe).
+__device__ __forceinline__ float d2f_rn(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned e = (unsigned)(b >> 52) & 0x7FFu;
+    if (e < 1023u - 126u || e > 1023u + 127u) return (float)x;  // zero, FP32-subnormal range, overflow, inf, nan
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    unsigned f = ((unsigned)(b >> 32) & 0x80000000u) | ((e - 896u) << 23) | (unsigned)(m >> 29);
+    const unsigned rest = (unsigned)m & 0x1FFFFFFFu;  // the 29 dropped bits
+    f += (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u))) ? 1u : 0u;  // carries into the exponent
+    return __uint_as_float(f);
+}
+__device__ __forceinline__ double f2d(float x)
+{
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xFFu;
+    if (e == 0u || e == 0xFFu) return (double)x;  // zero, subnormal, inf, nan
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+// Bounded wait on an mbarrier phase that also gives up when another role has
+// raised the CTA's abort flag: false if the phase did not complete.
+__device__ __forceinline__ bool wait_or_abort(uint32_t mbar, uint32_t parity, volatile int* abort_flag)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(mbar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > MBAR_WAIT_LIMIT) return false;
+    }
+    return true;
+}
+
+// epilogue-warp barrier (named barrier 1; the MMA and producer warps do not take part)
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(IT) : "memory"); }
+
+// sigma / 200 MPa, or log10(rho + 1e10), from the FP64 input rounded to FP32
+// (all FP32 arithmetic: the FP64 pipe is slow on this part)
+__device__ __forceinline__ float raw_feature(double v, bool stress)
+{
+    const float x = d2f_rn(v);
+    return stress ? x * (float)(1.0 / 200e6) : __log10f(x + 1e10f);
 }
 
 struct InferArgs {
     const double* feat;  // [n x 30]
     int64_t n;
+    int feat_bulk;       // feat is 16-byte aligned: one bulk copy per tile
     const float* nv;     // xm, xs, ym, ys, box lo, box hi, inverse Cholesky factor, d2 threshold
     const __nv_bfloat16* W[4];
+    const __half* Wc;    // W2 / 2, W3 / 2 (FP16) in 2 CPL pre-tiled K-chunks of 256 x KCH (canonical layout)
     const float* b[4];
     double* lp6;         // [n x 6]
     uint8_t* in_region;  // [n] or null
     int* err;
 };
 
-__global__ void __launch_bounds__(IT, 1) mlp_infer_kernel(InferArgs g)
+__global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
 {
     // every region below starts at a multiple of 16 bytes, all the no-swizzle
     // operand layouts need; pointers derived from the array itself keep the
     // compiler's shared-memory address space (plain shared loads and stores)
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t xbar, hbar[4], accbar[4], full[NST], empty[NST], drainbar, fbar;
     __shared__ uint32_t tmem_base;
+    __shared__ unsigned li_max;  // bits of max |L^-1| (non-negative floats order as integers)
+    __shared__ volatile int abort_flag;
     uint8_t* base = smem_raw;
     uint8_t* sX = base + OFF_X;
     uint8_t* sW1 = base + OFF_W1;
     uint8_t* sW4 = base + OFF_W4;
     uint8_t* sH = base + OFF_H;
+    uint8_t* sXlo = base + OFF_XLO;
     float* snv = reinterpret_cast<float*>(base + OFF_NV);
+    uint8_t* sBox = base + OFF_BOX;
     const uint32_t uX = smem_u32(sX), uW1 = smem_u32(sW1), uW4 = smem_u32(sW4), uH = smem_u32(sH);
+    const uint32_t uXlo = smem_u32(sXlo), uLH = smem_u32(base + OFF_LH), uLL = smem_u32(base + OFF_LL);
     const uint32_t uWC = smem_u32(base + OFF_WC);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int64_t n_tiles = (g.n + 127) / 128;
     if ((int64_t)blockIdx.x >= n_tiles) return;  // whole CTA, before any allocation
     const int64_t my_tiles = (n_tiles - 1 - blockIdx.x) / gridDim.x + 1;
-    const int64_t Q = 8 * my_tiles;  // chunks of the W2/W3 stream
-    const uint32_t mb = smem_u32(&mbar);
+    const int64_t Q = 2 * CPL * my_tiles;  // chunks of the W2/W3 stream
+    const uint32_t ux = smem_u32(&xbar), uacc0 = smem_u32(&accbar[0]);
+    const uint32_t uh0 = smem_u32(&hbar[0]), ufull0 = smem_u32(&full[0]), uempty0 = smem_u32(&empty[0]);
+    // each mbarrier is 8 bytes: barrier k of an array at u0 + 8 k
 
     if (warp == 0) {
-        tmem_alloc(smem_u32(&tmem_base), 256);
+        tmem_alloc(smem_u32(&tmem_base), 512);
         tmem_relinquish();
     }
-    if (tid == 0) mbar_init(mb, 1);
+    if (tid == 0) {
+        abort_flag = 0;
+        mbar_init(ux, IT);
+        for (int c = 0; c < 4; ++c) mbar_init(uh0 + 8 * c, IT);
+        for (int l = 0; l < 4; ++l) mbar_init(uacc0 + 8 * l, 1);
+        li_max = 0u;
+        mbar_init(smem_u32(&drainbar), 1);
+        mbar_init(smem_u32(&fbar), 1);
+        for (int k = 0; k < NST; ++k) {
+            mbar_init(ufull0 + 8 * k, 1);
+            mbar_init(uempty0 + 8 * k, 1);
+        }
+    }
     // resident operands and maps
-    copy_canon(sW1, g.W[0], 256, 32, 512);
-    copy_canon(sW4, g.W[3], 16, 256, 4096);
-    for (int e = tid; e < NV_FLOATS; e += IT) snv[e] = g.nv[e];
-    float* sB = reinterpret_cast<float*>(base + OFF_B);
-    for (int e = tid; e < 3 * 256 + 16; e += IT) sB[e] = e < 768 ? g.b[e >> 8][e & 255] : g.b[3][e - 768];
-    const uint32_t uF = smem_u32(base + OFF_F);
-    const double* sF = reinterpret_cast<const double*>(base + OFF_F);
-    // group 0: the first tile's features and W2 chunk 0; group 1: W2 chunk 1
-    issue_features(uF, g.feat, (int64_t)blockIdx.x * 128, (int)min((int64_t)128, g.n - (int64_t)blockIdx.x * 128));
-    issue_chunk(uWC, g.W[1], g.W[2], 0);
-    cp_async_commit();
-    if (Q > 1) issue_chunk(uWC + WC_BYTES, g.W[1], g.W[2], 1);
-    cp_async_commit();
-    tc_fence_before();
+    for (int e = tid; e < 256 * 4; e += IT_ALL) {  // W1: 256 rows x 32 K (4 x 8-element groups)
+        const int r = e >> 2, kc = e & 3;
+        uint4 v = bf16x8_to_f16x8(*reinterpret_cast<const uint4*>(g.W[0] + (int64_t)r * 32 + kc * 8), 1.0f);
+        if (kc == 3) {  // K columns 30, 31: the bias in two FP16 parts
+            const float bb = g.b[0][r];
+            const __half hi = __float2half_rn(bb), lo = __float2half_rn(bb - __half2float(hi));
+            const __half2 h2 = __halves2half2(hi, lo);
+            v.w = *reinterpret_cast<const uint32_t*>(&h2);
+        }
+        *reinterpret_cast<uint4*>(sW1 + (r >> 3) * 512 + kc * 128 + (r & 7) * 16) = v;
+    }
+    for (int e = tid; e < 16 * 32; e += IT_ALL) {  // W4 / 2: 16 rows x 256 K
+        const int r = e >> 5, kc = e & 31;
+        *reinterpret_cast<uint4*>(sW4 + (r >> 3) * 4096 + kc * 128 + (r & 7) * 16) =
+            bf16x8_to_f16x8(*reinterpret_cast<const uint4*>(g.W[3] + (int64_t)r * 256 + kc * 8), 0.5f);
+    }
+    for (int e = tid; e < NV_FLOATS; e += IT_ALL) snv[e] = g.nv[e];
+    const float* gLi = g.nv + 4 * NF + 2 * NO;  // L^-1, NF x NF row-major, lower triangle
+    __syncthreads();  // li_max is cleared
+    for (int e = tid; e < NF * NF; e += IT_ALL) atomicMax(&li_max, __float_as_uint(fabsf(gLi[e])));
     __syncthreads();
+    int li_exp = 0;
+    frexpf(__uint_as_float(li_max), &li_exp);
+    const int li_k = li_max ? max(-60, min(60, 14 - li_exp)) : 0;  // s = 2^li_k
+    const float li_s = ldexpf(1.0f, li_k), inv_s2 = ldexpf(1.0f, -2 * li_k);
+    for (int e = tid; e < 32 * 32; e += IT_ALL) {  // s L^-1 = L_hi + L_lo, rows i and K columns j, zero-padded
+        const int i = e >> 5, j = e & 31;
+        const float v = (i < NF && j <= i) ? gLi[i * NF + j] * li_s : 0.0f;
+        const __half hi = __float2half_rn(v);
+        *reinterpret_cast<__half*>(base + OFF_LH + canon(i, j, 512)) = hi;
+        *reinterpret_cast<__half*>(base + OFF_LL + canon(i, j, 512)) = __float2half_rn(v - __half2float(hi));
+    }
+    float* sB = reinterpret_cast<float*>(base + OFF_B);
+    // (the layer index is a constant in each loop: indexing the parameter's
+    // pointer array with a variable would copy the parameters to local memory)
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+        for (int e = tid; e < 256; e += IT_ALL) sB[256 * l + e] = g.b[l][e];
+    for (int e = tid; e < 16; e += IT_ALL) sB[768 + e] = g.b[3][e];
+    const uint32_t uF = smem_u32(base + OFF_F), ufbar = smem_u32(&fbar);
+    const double* sF = reinterpret_cast<const double*>(base + OFF_F);
+    const bool fbulk = g.feat_bulk != 0;
+    fence_async_smem();  // the resident operands were written by the generic proxy
+    tc_fence_before();
+    __syncthreads();  // (the barrier inits are visible)
+    if (tid < IT)
+        issue_features(fbulk, uF, g.feat, (int64_t)blockIdx.x * 128,
+                       (int)min((int64_t)128, g.n - (int64_t)blockIdx.x * 128), ufbar);
     tc_fence_after();
     const uint32_t tmem = tmem_base;
-    // epilogue roles: TMEM lane group (rows) and column quarter of this warp
-    const int lg = warp & 3, cq = warp >> 2;
-    const int erow = 32 * lg + (tid & 31);
-    const uint32_t tmem_row = tmem + ((uint32_t)(32 * lg) << 16);
-    // input-map roles: row and quarter (8 of the 32 operand columns, a share of the Mahalanobis sum)
-    const int mrow = tid & 127, part = tid >> 7;
-    const float* xm = snv;
-    const float* xs = snv + NF;
-    const float* ym = snv + 2 * NF;
-    const float* ys = ym + NO;
-    const float* lo = snv + 2 * NF + 2 * NO;
-    const float* hi = lo + NF;
-    const float* Li = hi + NF;  // inverse of the Cholesky factor, lower triangle
-    const float d2_thr = Li[NF * NF];
-    float* sd2 = reinterpret_cast<float*>(base + OFF_D2);
-    float* sZ = reinterpret_cast<float*>(base + OFF_Z);
-    const uint32_t id_h = idesc_bf16_f32(128, 256), id_o = idesc_bf16_f32(128, 16);
-    uint32_t phase = 0;
     bool ok = true;
-    int64_t q = 0;
 
-    for (int64_t it = 0; it < my_tiles; ++it) {
-        const int64_t r0 = ((int64_t)blockIdx.x + it * gridDim.x) * 128;
-        const int valid = (int)min((int64_t)128, g.n - r0);
-        // 1. raw features, prefetched into the staging buffer (with the first W2
-        //    chunk for the first tile, with W2 chunk 2 of the previous tile after that)
-        cp_async_wait1();
-        __syncthreads();
-        // features 8 part .. 8 part + 7 of this row: standardised once, kept
-        // for the other three threads of the row, and written as the BF16
-        // slice of the layer-1 operand
-        {
-            float zc[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int k = 8 * part + i;
-                zc[i] = (k < NF && mrow < valid) ? (raw_feature(sF[k * F_LD + mrow], k) - xm[k]) / xs[k] : 0.0f;
-                if (k < NF) sZ[k * 128 + mrow] = zc[i];
-            }
-            uint32_t w4[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const __nv_bfloat162 h = __floats2bfloat162_rn(zc[2 * i], zc[2 * i + 1]);
-                w4[i] = *reinterpret_cast<const uint32_t*>(&h);
-            }
-            *reinterpret_cast<uint4*>(sX + canon(mrow, 8 * part, 512)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-        }
-        __syncthreads();
-        // this thread's share of |L^-1 z|^2 (rows i = part, part + 4, ...);
-        // the box test once per row
-        bool inbox = true;
-        {
-            float z[NF];
-#pragma unroll
-            for (int c = 0; c < NF; ++c) z[c] = sZ[c * 128 + mrow];
-            if (part == 0) {
-#pragma unroll
-                for (int c = 0; c < NF; ++c) inbox = inbox && z[c] >= lo[c] && z[c] <= hi[c];
-            }
-            float d2 = 0.0f;
-#pragma unroll
-            for (int i = 0; i < NF; ++i) {
-                if ((i & 3) != part) continue;
-                float w = 0.0f;
-#pragma unroll
-                for (int j = 0; j <= i; ++j) w = fmaf(Li[i * NF + j], z[j], w);
-                d2 = fmaf(w, w, d2);
-            }
-            sd2[part * 128 + mrow] = d2;
-        }
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (part == 0 && mrow < valid && g.in_region) {
-            const float d2 = (sd2[mrow] + sd2[128 + mrow]) + (sd2[256 + mrow] + sd2[384 + mrow]);
-            g.in_region[r0 + mrow] = (inbox && d2 <= d2_thr) ? 1 : 0;
-        }
-        // 2. layer 1: X [128 x 32] W1^T
-        if (tid == 0) {
-            tc_fence_after();
-            for (int s = 0; s < 2; ++s)
-                tc_mma_bf16(tmem, smem_desc(uX + s * 256, 128, 512), smem_desc(uW1 + s * 256, 128, 512), id_h,
-                            s ? 1u : 0u);
-            tc_commit(mb);
-        }
-        ok = mbar_wait_bounded(mb, phase, MBAR_WAIT_LIMIT);
-        phase ^= 1u;
-        if (!__syncthreads_and(ok)) {
-            ok = false;
-            break;
-        }
-        tc_fence_after();
-        epilogue_hidden(tmem_row, erow, 64 * cq, sB, sH);
-        // layers 2 and 3: H [128 x 256] W^T, W streamed in K-chunks of 64
-        for (int l = 1; l <= 2 && ok; ++l) {
-            for (int kc = 0; kc < 4; ++kc, ++q) {
-                cp_async_wait1();  // chunk q has landed (the newest group is chunk q + 1)
-                fence_async_smem();
-                tc_fence_before();
-                __syncthreads();
-                if (tid == 0) {
-                    tc_fence_after();
-                    const uint32_t ub = uWC + (uint32_t)(q & 1) * WC_BYTES;
-                    for (int s = 0; s < 4; ++s)
-                        tc_mma_bf16(tmem, smem_desc(uH + (kc * 4 + s) * 256, 128, 4096), smem_desc(ub + s * 256, 128, 1024),
-                                    id_h, (kc | s) ? 1u : 0u);
-                    tc_commit(mb);
-                }
-                ok = mbar_wait_bounded(mb, phase, MBAR_WAIT_LIMIT);
-                phase ^= 1u;
-                if (!__syncthreads_and(ok)) {
-                    ok = false;
+    if (warp == EW + 1) {
+        // ------------------------------------------------ weight producer
+        if ((tid & 31) == 0) {
+            int64_t issued = 0;
+            for (; issued < Q; ++issued) {
+                const uint32_t st = (uint32_t)(issued % NST);
+                if (issued >= NST &&  // the stage's previous chunk must have been read by its MMAs
+                    !wait_or_abort(uempty0 + 8 * st, (uint32_t)(((issued - NST) / NST) & 1), &abort_flag)) {
+                    abort_flag = 1;
                     break;
                 }
-                // the buffer of chunk q is free again: fetch chunk q + 2 (and, with
-                // chunk 2 of this tile, the next tile's features: the staging
-                // buffer was read before the first barrier of this layer)
-                if (q + 2 < Q) issue_chunk(uWC + (uint32_t)(q & 1) * WC_BYTES, g.W[1], g.W[2], q + 2);
-                if (l == 1 && kc == 0 && it + 1 < my_tiles) {
-                    const int64_t rn = ((int64_t)blockIdx.x + (it + 1) * gridDim.x) * 128;
-                    issue_features(uF, g.feat, rn, (int)min((int64_t)128, g.n - rn));
+                mbar_expect_tx(ufull0 + 8 * st, WC_BYTES);
+                bulk_g2s(uWC + st * WC_BYTES, g.Wc + (size_t)(issued % (2 * CPL)) * (WC_BYTES / 2), WC_BYTES,
+                         ufull0 + 8 * st);
+            }
+            // no copy may still be landing when the CTA leaves: wait (bounded)
+            // for the last copy into each stage
+            for (int64_t j = issued > NST ? issued - NST : 0; j < issued; ++j)
+                mbar_wait_bounded(ufull0 + 8 * (uint32_t)(j % NST), (uint32_t)((j / NST) & 1), MBAR_WAIT_LIMIT);
+            if (abort_flag) atomicExch(g.err, 1);
+        }
+    } else if (warp == EW) {
+        // ------------------------------------------------ MMA issuer
+        if ((tid & 31) == 0) {
+            const uint32_t id_h = idesc_f16_f32(128, 256), id_o = idesc_f16_f32(128, 16);
+            const uint32_t id_m = idesc_f16_f32(128, 32);
+            const uint32_t accA = tmem, accB = tmem + 256;
+            int64_t q = 0;              // weight chunks consumed
+            uint32_t xph = 0, hph = 0;  // hph bit kc: parity of hbar[kc]
+            bool mma_out = false;       // MMAs issued (for the abort path)
+            for (int64_t it = 0; it < my_tiles && ok; ++it) {
+                // layer 1: X [128 x 32] W1^T -> A
+                ok = wait_or_abort(ux, xph, &abort_flag);
+                xph ^= 1u;
+                if (!ok) break;
+                tc_fence_after();
+                for (int s = 0; s < 2; ++s)
+                    tc_mma_bf16(accA, smem_desc(uX + s * 256, 128, 512), smem_desc(uW1 + s * 256, 128, 512), id_h,
+                                s ? 1u : 0u);
+                // trust region: W = z_hi L_hi + z_hi L_lo + z_lo L_hi (kind::f16 with FP16 operands)
+                for (int s = 0; s < 2; ++s) {
+                    const uint64_t zh = smem_desc(uX + s * 256, 128, 512), zl = smem_desc(uXlo + s * 256, 128, 512);
+                    const uint64_t lh = smem_desc(uLH + s * 256, 128, 512), ll = smem_desc(uLL + s * 256, 128, 512);
+                    tc_mma_bf16(tmem + MAHA_COL, zh, lh, id_m, s ? 1u : 0u);
+                    tc_mma_bf16(tmem + MAHA_COL, zh, ll, id_m, 1u);
+                    tc_mma_bf16(tmem + MAHA_COL, zl, lh, id_m, 1u);
                 }
-                cp_async_commit();
+                tc_commit(uacc0);
+                mma_out = true;
+                // layers 2, 3: H [128 x 256] W^T, K-slice by K-slice as soon as the
+                // epilogue has written its activation chunk and the weights have landed
+                for (int l = 1; l <= 2 && ok; ++l) {
+                    const uint32_t acc = (l == 1) ? accB : accA;
+                    for (int jj = 0; jj < CPL; ++jj, ++q) {
+                        const int kc = jj * KCH / 64;  // the activation chunk this K-slice lies in
+                        if ((jj * KCH) % 64 == 0) {
+                            ok = wait_or_abort(uh0 + 8 * kc, (hph >> kc) & 1u, &abort_flag);
+                            hph ^= 1u << kc;
+                            if (!ok) break;
+                        }
+                        const uint32_t st = (uint32_t)(q % NST);
+                        ok = wait_or_abort(ufull0 + 8 * st, (uint32_t)((q / NST) & 1), &abort_flag);
+                        if (!ok) break;
+                        tc_fence_after();
+                        const uint32_t ub = uWC + st * WC_BYTES;
+                        for (int s = 0; s < KCH / 16; ++s)
+                            tc_mma_bf16(acc, smem_desc(uH + (jj * (KCH / 16) + s) * 256, 128, 4096),
+                                        smem_desc(ub + s * 256, 128, 16 * KCH), id_h, (jj | s) ? 1u : 0u);
+                        tc_commit(uempty0 + 8 * st);  // the stage is free once these MMAs are done
+                    }
+                    if (!ok) break;
+                    tc_commit(uacc0 + 8 * l);
+                }
+                if (!ok) break;
+                // layer 4: H [128 x 256] W4^T -> B (16 columns, 6 used)
+                for (int kc = 0; kc < 4 && ok; ++kc) {
+                    ok = wait_or_abort(uh0 + 8 * kc, (hph >> kc) & 1u, &abort_flag);
+                    hph ^= 1u << kc;
+                    if (!ok) break;
+                    tc_fence_after();
+                    for (int s = 4 * kc; s < 4 * kc + 4; ++s)
+                        tc_mma_bf16(accB, smem_desc(uH + s * 256, 128, 4096), smem_desc(uW4 + s * 256, 128, 4096),
+                                    id_o, s ? 1u : 0u);
+                }
+                if (!ok) break;
+                tc_commit(uacc0 + 24);
+            }
+            if (!ok) {
+                abort_flag = 1;
+                // the tensor core may still be busy: wait (bounded) for a commit
+                // of everything issued before the tensor memory is freed
+                if (mma_out) {
+                    tc_commit(smem_u32(&drainbar));
+                    mbar_wait_bounded(smem_u32(&drainbar), 0u, MBAR_WAIT_LIMIT);
+                }
+                atomicExch(g.err, 1);
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue warps
+        const int lg = warp & 3, cs = warp >> 2;  // TMEM lane group (rows) and 16-column slice of a chunk
+        const int erow = 32 * lg + (tid & 31);
+        const uint32_t tmem_row = tmem + ((uint32_t)(32 * lg) << 16);
+        // input-map roles: row and quarter (8 of the 32 operand columns)
+        const int mrow = tid & 127, part = tid >> 7;
+        const float* xm = snv;
+        const float* xs = snv + NF;
+        const float* ym = snv + 2 * NF;
+        const float* ys = ym + NO;
+        const float* lo = snv + 2 * NF + 2 * NO;
+        const float* hi = lo + NF;
+        const float d2_thr = snv[4 * NF + 2 * NO + NF * NF];
+        // this thread's 8 features: mean and reciprocal deviation, once
+        float fxm[8], fxr[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = 8 * part + i;
+            fxm[i] = k < NF ? xm[k] : 0.0f;
+            fxr[i] = k < NF ? 1.0f / xs[k] : 0.0f;
+        }
+        uint32_t accph = 0;  // bit l: parity of accbar[l]
+        auto wait_acc = [&](int l) {
+            const bool w = wait_or_abort(uacc0 + 8 * l, (accph >> l) & 1u, &abort_flag);
+            accph ^= 1u << l;
+            if (!w) abort_flag = 1;
+            tc_fence_after();
+            return w;
+        };
+        // hand a finished operand chunk to the MMA issuer
+        auto publish = [&](uint32_t mbar) {
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(mbar);
+        };
+        // the input map of tile it: raw features (prefetched into the staging
+        // buffer) -> the FP16 layer-1 operand z_hi, its residual z_lo and this
+        // quarter row's box test; then the prefetch of tile it + 1
+        int fpend = 0;  // tile whose feature copy is in flight, or -1
+        auto map_tile = [&](int64_t it) {
+            const int64_t r0 = ((int64_t)blockIdx.x + it * gridDim.x) * 128;
+            const int valid = (int)min((int64_t)128, g.n - r0);
+            if (fbulk) {
+                if (!wait_or_abort(ufbar, (uint32_t)(it & 1), &abort_flag)) abort_flag = 1;
+                fpend = -1;
+                // (on abort the values read below are stale but in bounds; the tile loop ends)
+            } else {
+                cp_async_wait0();
+                epi_sync();
+            }
+            float zc[8];
+            bool box = true;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int k = 8 * part + i;  // warp-uniform: part is
+                zc[i] = k >= NF ? 1.0f       // the bias columns
+                                : mrow < valid ? (raw_feature(sF[mrow * NF + k], k < 6) - fxm[i]) * fxr[i] : 0.0f;
+                if (k < NF) box = box && zc[i] >= lo[k] && zc[i] <= hi[k];
+            }
+            uint32_t w4[4], l4[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const __half2 h = __floats2half2_rn(zc[2 * i], zc[2 * i + 1]);
+                const float2 hf = __half22float2(h);
+                const __half2 r = __floats2half2_rn(zc[2 * i] - hf.x, zc[2 * i + 1] - hf.y);  // 0 for the bias columns
+                w4[i] = *reinterpret_cast<const uint32_t*>(&h);
+                l4[i] = *reinterpret_cast<const uint32_t*>(&r);
+            }
+            *reinterpret_cast<uint4*>(sX + canon(mrow, 8 * part, 512)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+            *reinterpret_cast<uint4*>(sXlo + canon(mrow, 8 * part, 512)) = make_uint4(l4[0], l4[1], l4[2], l4[3]);
+            sBox[part * 128 + mrow] = box ? 1 : 0;
+            publish(ux);
+            epi_sync();  // the staging buffer has been read; the box tests are visible
+            if (it + 1 < my_tiles) {
+                const int64_t rn = ((int64_t)blockIdx.x + (it + 1) * gridDim.x) * 128;
+                issue_features(fbulk, uF, g.feat, rn, (int)min((int64_t)128, g.n - rn), ufbar);
+                fpend = (int)(it + 1);
+            }
+        };
+        map_tile(0);
+        for (int64_t it = 0; it < my_tiles && ok; ++it) {
+            if (abort_flag) {
+                ok = false;
+                break;
+            }
+            const int64_t r0 = ((int64_t)blockIdx.x + it * gridDim.x) * 128;
+            const int valid = (int)min((int64_t)128, g.n - r0);
+            // 1. hidden layers: activations chunk by chunk, each handed over at once
+            for (int l = 0; l < 3 && ok; ++l) {
+                ok = wait_acc(l);
+                if (!ok) break;
+                if (l == 0 && cs == 0) {
+                    // trust region of this row: its row of W lies in columns the
+                    // layer-2 MMAs overwrite, so it is read before the first hand-over
+                    float wv[32];
+                    tmem_ld16(tmem_row + (uint32_t)MAHA_COL, wv);
+                    tmem_ld16(tmem_row + (uint32_t)MAHA_COL + 16u, wv + 16);
+                    float d2 = 0.0f;
+#pragma unroll
+                    for (int i = 0; i < NF; ++i) d2 = fmaf(wv[i], wv[i], d2);
+                    const bool box = sBox[erow] & sBox[128 + erow] & sBox[256 + erow] & sBox[384 + erow];
+                    if (erow < valid && g.in_region) g.in_region[r0 + erow] = (box && d2 * inv_s2 <= d2_thr) ? 1 : 0;
+                }
+                const uint32_t acc_col = (l == 1) ? 256u : 0u;
+                // the load of chunk kc + 1 runs while chunk kc is turned into activations
+                uint32_t ra[16], rb[16];
+                tmem_ld16_async(tmem_row + acc_col + (uint32_t)(16 * cs), ra);
+#pragma unroll
+                for (int kc = 0; kc < 4; ++kc) {
+                    const int c0 = 64 * kc + 16 * cs;
+                    tmem_wait_ld();
+                    uint32_t* cur = (kc & 1) ? rb : ra;
+                    uint32_t* nxt = (kc & 1) ? ra : rb;
+                    if (kc < 3) tmem_ld16_async(tmem_row + acc_col + (uint32_t)(c0 + 64), nxt);
+                    if (l == 0)
+                        epilogue16<false>(cur, erow, c0, nullptr, sH);
+                    else
+                        epilogue16<true>(cur, erow, c0, sB + 256 * l, sH);
+                    publish(uh0 + 8 * kc);
+                }
             }
             if (!ok) break;
-            tc_fence_after();
-            epilogue_hidden(tmem_row, erow, 64 * cq, sB + 256 * l, sH);
-        }
-        if (!ok) break;
-        // layer 4: H [128 x 256] W4^T, N = 16 (6 used)
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            for (int s = 0; s < 16; ++s)
-                tc_mma_bf16(tmem, smem_desc(uH + s * 256, 128, 4096), smem_desc(uW4 + s * 256, 128, 4096), id_o,
-                            s ? 1u : 0u);
-            tc_commit(mb);
-        }
-        ok = mbar_wait_bounded(mb, phase, MBAR_WAIT_LIMIT);
-        phase ^= 1u;
-        if (!__syncthreads_and(ok)) {
-            ok = false;
-            break;
-        }
-        tc_fence_after();
-        if (cq == 0) {  // warps 0-3: one row each per thread
-            float v[16];
-            tmem_ld16(tmem_row, v);
-            if (erow < valid) {
+            // 2. the next tile's input map (accumulator A is free again: its
+            // layer-3 values have all been read)
+            if (it + 1 < my_tiles) map_tile(it + 1);
+            // 3. layer 4 -> FP64 outputs (warps of the first column slice: one row each)
+            if (!(ok = wait_acc(3))) break;
+            if (cs == 0) {
+                float v[16];
+                tmem_ld16(tmem_row + 256u, v);
+                if (erow < valid) {
 #pragma unroll
-                for (int c = 0; c < NO; ++c)
-                    g.lp6[(r0 + erow) * NO + c] = (double)((v[c] + sB[768 + c]) * ys[c] + ym[c]);
+                    for (int c = 0; c < NO; ++c)
+                        g.lp6[(r0 + erow) * NO + c] = f2d((v[c] + sB[768 + c]) * ys[c] + ym[c]);
+                }
             }
+            tc_fence_before();
         }
-        tc_fence_before();
-        __syncthreads();  // accumulator read and hidden buffer free before the next tile
-    }
-    cp_async_wait0();
-    if (!ok && tid == 0) {
-        atomicExch(g.err, 1);
-        // give the tensor core a last bounded chance to finish the phase that was
-        // given up on (phase was already toggled) before TMEM is freed
-        mbar_wait_bounded(mb, phase ^ 1u, MBAR_WAIT_LIMIT);
+        cp_async_wait0();
+        // a feature copy still landing (the loop ended early): wait (bounded) for it
+        if (fbulk && tid == 0 && fpend >= 0) mbar_wait_bounded(ufbar, (uint32_t)(fpend & 1), MBAR_WAIT_LIMIT);
+        if (!ok && (tid & 31) == 0) atomicExch(g.err, 1);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 256);
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// W2 / 2 and W3 / 2 (row-major 256 x 256 BF16 in, FP16 out) -> 2 CPL K-chunks
+// of 256 rows x KCH in the canonical no-swizzle K-major layout (8-row x
+// 16-byte core matrices, K-adjacent ones 128 B apart, 8-row groups 16 KCH
+// bytes apart), WC_BYTES each, so a chunk is one contiguous bulk copy into
+// shared memory.
+__global__ void tile_weights_kernel(const __nv_bfloat16* __restrict__ W2, const __nv_bfloat16* __restrict__ W3,
+                                    __half* __restrict__ Wc)
+{
+    constexpr int G = KCH / 8;  // 16-byte groups per row of a chunk
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;  // one 16-byte group: chunk j, row r, group kk
+    if (v >= 2 * CPL * 256 * G) return;
+    const int j = v / (256 * G), r = (v / G) % 256, kk = v % G;
+    const __nv_bfloat16* W = j < CPL ? W2 : W3;
+    const int k0 = KCH * (j % CPL) + 8 * kk;
+    uint8_t* dst = reinterpret_cast<uint8_t*>(Wc) + (size_t)j * WC_BYTES + (r >> 3) * (16 * KCH) + kk * 128 + (r & 7) * 16;
+    *reinterpret_cast<uint4*>(dst) = bf16x8_to_f16x8(*reinterpret_cast<const uint4*>(W + r * 256 + k0), 0.5f);
 }
 
 }  // namespace
 
 cudaError_t launch_mlp_infer(const double* feat, int64_t n, const float* nv, const __nv_bfloat16* const W[4],
-                             const float* const b[4], double* lp6, uint8_t* in_region, int* err, cudaStream_t s)
+                             const float* const b[4], __nv_bfloat16* wc, double* lp6, uint8_t* in_region, int* err,
+                             cudaStream_t s)
 {
     static bool attr_set[64] = {};  // the attribute is per function and device
     int dev = 0;
@@ -398,21 +644,28 @@ cudaError_t launch_mlp_infer(const double* feat, int64_t n, const float* nv, con
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     if (n <= 0) return cudaSuccess;
+    // the staged FP16 weights live in the 2-byte-per-element scratch wc
+    __half* wh = reinterpret_cast<__half*>(wc);
+    tile_weights_kernel<<<(2 * 256 * 256 / 8 + 255) / 256, 256, 0, s>>>(W[1], W[2], wh);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     int sms = 152;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t tiles = (n + 127) / 128;
     InferArgs g{};
     g.feat = feat;
     g.n = n;
+    g.feat_bulk = ((uintptr_t)feat & 15u) == 0;
     g.nv = nv;
     for (int l = 0; l < 4; ++l) {
         g.W[l] = W[l];
         g.b[l] = b[l];
     }
+    g.Wc = wh;
     g.lp6 = lp6;
     g.in_region = in_region;
     g.err = err;
-    mlp_infer_kernel<<<(unsigned)(tiles < sms ? tiles : sms), IT, INFER_SMEM, s>>>(g);
+    mlp_infer_kernel<<<(unsigned)(tiles < sms ? tiles : sms), IT_ALL, INFER_SMEM, s>>>(g);
     return cudaGetLastError();
 }
 

@@ -111,6 +111,11 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
 {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// the same with both operands FP16 (A and B type fields 0)
+__host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
 // ---------------------------------------------------------------- GEMM
 enum GemmEpi : int {
@@ -187,8 +192,11 @@ cudaError_t launch_tc_gemm(const GemmArgs& g, cudaStream_t s);
 
 // Fused surrogate inference (mlp_infer.cu): raw features [n x 30] -> sym(Lp)
 // [n x 6] in FP64 and the trust-region flags; nv = the FP32 maps (xm, xs, ym,
-// ys, box, Cholesky factor, threshold), W/b the BF16 weights and FP32 biases.
+// ys, box, Cholesky factor, threshold), W/b the BF16 weights and FP32 biases,
+// wc a device buffer of 8 x 256 x 64 BF16 for the pre-tiled W2/W3 chunks
+// (rewritten by every launch).  Two launches: the tiling, the fused kernel.
 cudaError_t launch_mlp_infer(const double* feat, int64_t n, const float* nv, const __nv_bfloat16* const W[4],
-                             const float* const b[4], double* lp6, uint8_t* in_region, int* err, cudaStream_t s);
+                             const float* const b[4], __nv_bfloat16* wc, double* lp6, uint8_t* in_region, int* err,
+                             cudaStream_t s);
 
 }  // namespace ptadd

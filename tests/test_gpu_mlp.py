@@ -150,8 +150,8 @@ def _parse_state(blob):
 
 def test_fused_inference_matches_oracle():
     """The fused inference kernel (input map, trust region, four layers, output
-    map in one launch) against the FP64 oracle on the BF16-rounded weights and
-    standardised inputs.  50 001 points = 391 tiles of 128 (the last one
+    map in one launch) against the FP64 oracle on the BF16 weights and the
+    standardised inputs rounded to FP16 (the kernel's layer-1 operand type).  50 001 points = 391 tiles of 128 (the last one
     ragged), so every persistent CTA walks several tiles and the W2/W3 chunk
     stream crosses tile boundaries."""
     rng = np.random.default_rng(21)
@@ -173,11 +173,11 @@ def test_fused_inference_matches_oracle():
         params, m = _parse_state(c.surrogate_get_state())
     f32 = np.float32
     f = np.empty((n, 30), f32)
-    f[:, :6] = (test[:, :6] * (1.0 / 200e6)).astype(f32)
+    f[:, :6] = test[:, :6].astype(f32) * f32(1.0 / 200e6)
     f[:, 6:] = np.log10(test[:, 6:].astype(f32) + f32(1e10))
     z = (f - m["xm"].astype(f32)) / m["xs"].astype(f32)
     sel = np.concatenate([rng.choice(n - 128, size=2000, replace=False), np.arange(n - 97, n)])
-    yo = O.mlp_forward(DIMS, weights_bf16(params), bf16(z[sel]))
+    yo = O.mlp_forward(DIMS, weights_bf16(params), z[sel].astype(np.float16).astype(np.float64))
     ref = yo * m["ys"] + m["ym"]
     err = relfro(pred[sel], ref)
     print("fused inference vs oracle: %.3e" % err)
@@ -193,3 +193,38 @@ def test_fused_inference_matches_oracle():
     assert clear.mean() > 0.9
     assert np.array_equal(inr[clear], host[clear])
     assert 0.2 < host.mean() < 0.8  # both outcomes occur
+
+
+def test_fused_inference_unaligned_input_takes_the_copy_path_and_agrees():
+    """Features at an address that is 8 but not 16 bytes aligned cannot be
+    staged with one bulk copy per tile: the kernel then stages them with 8-byte
+    asynchronous copies.  Both paths feed the same arithmetic, so the outputs
+    and trust-region flags agree bit for bit (2 000 rows: 16 tiles, the last
+    ragged)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(31)
+    n_fit, n = 2048, 2000
+    feat_fit = np.hstack([rng.uniform(-200e6, 200e6, size=(n_fit, 6)), 10 ** rng.uniform(11, 13, size=(n_fit, 24))])
+    lp = np.tanh(feat_fit[:, :6] / 1e8) * 20.0
+    test = np.hstack([rng.uniform(-220e6, 220e6, size=(n, 6)), 10 ** rng.uniform(10.8, 13.2, size=(n, 24))])
+    dev = torch.device("cuda", 0)
+    buf = torch.zeros(n * 30 + 2, dtype=torch.float64, device=dev)  # storage is 256-byte aligned
+    aligned = buf[:n * 30]
+    shifted = buf[1:1 + n * 30]
+    assert aligned.data_ptr() % 16 == 0 and shifted.data_ptr() % 16 == 8
+    outs = []
+    with ptadd.Context(MAT, ptadd.PTADD_FP64, 0) as c:
+        c.surrogate_fit(feat_fit, lp, epochs=4, batch=256, lr=2e-3, seed=5)
+        for view in (aligned, shifted):
+            view.copy_(torch.from_numpy(test.reshape(-1)))
+            lp6 = torch.empty(n * 6, dtype=torch.float64, device=dev)
+            reg = torch.empty(n, dtype=torch.uint8, device=dev)
+            torch.cuda.synchronize()
+            c.surrogate_predict_dev(n, view.data_ptr(), lp6.data_ptr(), reg.data_ptr())
+            torch.cuda.synchronize()
+            outs.append((lp6.cpu().numpy().copy(), reg.cpu().numpy().copy()))
+        ref, ref_in = c.surrogate_predict(test)
+    assert np.all(np.isfinite(outs[0][0]))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][0].reshape(n, 6), ref) and np.array_equal(outs[0][1].astype(bool), ref_in)
+    assert 0 < outs[0][1].sum() < n
