@@ -97,9 +97,9 @@ constexpr int OFF_WC = OFF_H + H_BYTES;
 constexpr int OFF_NV = OFF_WC + NST * WC_BYTES;
 constexpr int OFF_B = OFF_NV + ((NV_FLOATS * 4 + 15) / 16) * 16;   // biases: 3 x 256 + 16
 constexpr int OFF_F = OFF_B + (3 * 256 + 16) * 4;                  // raw features of a tile [128][30]
-constexpr int OFF_BOX = OFF_F + 128 * NF * 8;                      // box test per quarter row [4][128]
+constexpr int OFF_BOX = OFF_F + 128 * NF * 8;                      // box test per quarter row [2][4][128]
 static_assert(OFF_F % 16 == 0, "bulk copies into the staging buffer need 16-byte alignment");
-constexpr int INFER_SMEM = OFF_BOX + 4 * 128;
+constexpr int INFER_SMEM = OFF_BOX + 2 * 4 * 128;
 
 __device__ __forceinline__ uint32_t canon(int r, int k, int sbo)
 {
@@ -174,20 +174,31 @@ __device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t r[16])
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Accumulator values (16 columns from c0) [+ bias] -> 2 GELU -> FP16 into H (this thread's row).
+// Accumulator values (16 columns from c0) [+ bias] -> 2 GELU as 8 f16x2 words.
 template <bool BIAS>
-__device__ __forceinline__ void epilogue16(const uint32_t r[16], int row, int c0, const float* __restrict__ bias,
-                                           uint8_t* sH)
+__device__ __forceinline__ void gelu16(const uint32_t r[16], int c0, const float* __restrict__ bias, uint32_t w[8])
 {
-    uint32_t w[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         float2 z = make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
         if (BIAS) z = __fadd2_rn(z, *reinterpret_cast<const float2*>(bias + c0 + 2 * i));
         w[i] = gelu2x2_f16(z);
     }
+}
+// ... into H (row, columns c0 .. c0 + 15)
+__device__ __forceinline__ void store16(const uint32_t w[8], int row, int c0, uint8_t* sH)
+{
     *reinterpret_cast<uint4*>(sH + canon(row, c0, 4096)) = make_uint4(w[0], w[1], w[2], w[3]);
     *reinterpret_cast<uint4*>(sH + canon(row, c0 + 8, 4096)) = make_uint4(w[4], w[5], w[6], w[7]);
+}
+// Two consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float v[2])
+{
+    uint32_t r0, r1;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(taddr) : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    v[0] = __uint_as_float(r0);
+    v[1] = __uint_as_float(r1);
 }
 
 // 8 BF16 values -> 8 FP16 values times a power of two (exact in FP16's normal range)
@@ -327,7 +338,8 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
         *reinterpret_cast<uint4*>(sW4 + (r >> 3) * 4096 + kc * 128 + (r & 7) * 16) =
             bf16x8_to_f16x8(*reinterpret_cast<const uint4*>(g.W[3] + (int64_t)r * 256 + kc * 8), 0.5f);
     }
-    for (int e = tid; e < NV_FLOATS; e += IT_ALL) snv[e] = g.nv[e];
+    for (int e = tid; e < NV_FLOATS; e += IT_ALL)  // (the deviations xs are kept as reciprocals)
+        snv[e] = (e >= NF && e < 2 * NF) ? 1.0f / g.nv[e] : g.nv[e];
     const float* gLi = g.nv + 4 * NF + 2 * NO;  // L^-1, NF x NF row-major, lower triangle
     __syncthreads();  // li_max is cleared
     for (int e = tid; e < NF * NF; e += IT_ALL) atomicMax(&li_max, __float_as_uint(fabsf(gLi[e])));
@@ -469,20 +481,12 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
         // input-map roles: row and quarter (8 of the 32 operand columns)
         const int mrow = tid & 127, part = tid >> 7;
         const float* xm = snv;
-        const float* xs = snv + NF;
+        const float* xr = snv + NF;  // 1 / xs
         const float* ym = snv + 2 * NF;
         const float* ys = ym + NO;
         const float* lo = snv + 2 * NF + 2 * NO;
         const float* hi = lo + NF;
         const float d2_thr = snv[4 * NF + 2 * NO + NF * NF];
-        // this thread's 8 features: mean and reciprocal deviation, once
-        float fxm[8], fxr[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int k = 8 * part + i;
-            fxm[i] = k < NF ? xm[k] : 0.0f;
-            fxr[i] = k < NF ? 1.0f / xs[k] : 0.0f;
-        }
         uint32_t accph = 0;  // bit l: parity of accbar[l]
         auto wait_acc = [&](int l) {
             const bool w = wait_or_abort(uacc0 + 8 * l, (accph >> l) & 1u, &abort_flag);
@@ -518,7 +522,7 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
             for (int i = 0; i < 8; ++i) {
                 const int k = 8 * part + i;  // warp-uniform: part is
                 zc[i] = k >= NF ? 1.0f       // the bias columns
-                                : mrow < valid ? (raw_feature(sF[mrow * NF + k], k < 6) - fxm[i]) * fxr[i] : 0.0f;
+                                : mrow < valid ? (raw_feature(sF[mrow * NF + k], k < 6) - xm[k]) * xr[k] : 0.0f;
                 if (k < NF) box = box && zc[i] >= lo[k] && zc[i] <= hi[k];
             }
             uint32_t w4[4], l4[4];
@@ -532,7 +536,7 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
             }
             *reinterpret_cast<uint4*>(sX + canon(mrow, 8 * part, 512)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
             *reinterpret_cast<uint4*>(sXlo + canon(mrow, 8 * part, 512)) = make_uint4(l4[0], l4[1], l4[2], l4[3]);
-            sBox[part * 128 + mrow] = box ? 1 : 0;
+            sBox[(it & 1) * 512 + part * 128 + mrow] = box ? 1 : 0;
             publish(ux);
             epi_sync();  // the staging buffer has been read; the box tests are visible
             if (it + 1 < my_tiles) {
@@ -562,13 +566,16 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
                     float d2 = 0.0f;
 #pragma unroll
                     for (int i = 0; i < NF; ++i) d2 = fmaf(wv[i], wv[i], d2);
-                    const bool box = sBox[erow] & sBox[128 + erow] & sBox[256 + erow] & sBox[384 + erow];
+                    const uint8_t* bx = sBox + (it & 1) * 512 + erow;  // this tile's half: the next tile's map
+                    const bool box = bx[0] & bx[128] & bx[256] & bx[384];  // may already be writing the other
                     if (erow < valid && g.in_region) g.in_region[r0 + erow] = (box && d2 * inv_s2 <= d2_thr) ? 1 : 0;
                 }
                 const uint32_t acc_col = (l == 1) ? 256u : 0u;
                 // the load of chunk kc + 1 runs while chunk kc is turned into activations
                 uint32_t ra[16], rb[16];
                 tmem_ld16_async(tmem_row + acc_col + (uint32_t)(16 * cs), ra);
+                // chunk kc is handed over one step late, after chunk kc + 1's
+                // arithmetic, so that its proxy fence finds the stores done
 #pragma unroll
                 for (int kc = 0; kc < 4; ++kc) {
                     const int c0 = 64 * kc + 16 * cs;
@@ -576,26 +583,33 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
                     uint32_t* cur = (kc & 1) ? rb : ra;
                     uint32_t* nxt = (kc & 1) ? ra : rb;
                     if (kc < 3) tmem_ld16_async(tmem_row + acc_col + (uint32_t)(c0 + 64), nxt);
+                    uint32_t w[8];
                     if (l == 0)
-                        epilogue16<false>(cur, erow, c0, nullptr, sH);
+                        gelu16<false>(cur, c0, nullptr, w);
                     else
-                        epilogue16<true>(cur, erow, c0, sB + 256 * l, sH);
-                    publish(uh0 + 8 * kc);
+                        gelu16<true>(cur, c0, sB + 256 * l, w);
+                    if (kc > 0) publish(uh0 + 8 * (kc - 1));
+                    store16(w, erow, c0, sH);
                 }
+                publish(uh0 + 24);
+                // the next tile's input map, while layer 2 finishes: its operand
+                // may be published now, because the MMA issuer starts the next
+                // tile's layer 1 only after this tile's layer 4, i.e. after
+                // every layer-3 chunk (accumulator A) has been read
+                if (l == 0 && it + 1 < my_tiles) map_tile(it + 1);
             }
             if (!ok) break;
-            // 2. the next tile's input map (accumulator A is free again: its
-            // layer-3 values have all been read)
-            if (it + 1 < my_tiles) map_tile(it + 1);
-            // 3. layer 4 -> FP64 outputs (warps of the first column slice: one row each)
+            // 2. layer 4 -> FP64 outputs (two columns per thread of the first three column slices)
             if (!(ok = wait_acc(3))) break;
-            if (cs == 0) {
-                float v[16];
-                tmem_ld16(tmem_row + 256u, v);
+            if (cs < 3) {
+                float v[2];
+                tmem_ld2(tmem_row + 256u + (uint32_t)(2 * cs), v);
                 if (erow < valid) {
 #pragma unroll
-                    for (int c = 0; c < NO; ++c)
-                        g.lp6[(r0 + erow) * NO + c] = f2d((v[c] + sB[768 + c]) * ys[c] + ym[c]);
+                    for (int c = 0; c < 2; ++c) {
+                        const int o = 2 * cs + c;
+                        g.lp6[(r0 + erow) * NO + o] = f2d((v[c] + sB[768 + o]) * ys[o] + ym[o]);
+                    }
                 }
             }
             tc_fence_before();
