@@ -405,8 +405,9 @@ ptadd_status ptadd_dissipation_projection_dev(int64_t n_points, const double* T6
  * ptadd_set_nodes moves nodes and leaves the junctions as they are (a held
  * node stays held where it was put).
  * The state blob of ptadd_get_state carries the junction state while they
- * are on.  Single-realisation API only (not the batch).  PTADD_ERR_ARG on
- * negative or non-finite parameters; PTADD_ERR_STATE without a network. */
+ * are on.  Single-realisation API (ptadd_batch_set_junctions below is the
+ * batch's).  PTADD_ERR_ARG on negative or non-finite parameters;
+ * PTADD_ERR_STATE without a network. */
 typedef struct {
     double capture_radius;  /* m */
     double max_break_time;  /* a, s */
@@ -429,6 +430,30 @@ typedef struct {
  * PTADD_ERR_STATE when junctions are off. */
 ptadd_status ptadd_get_junctions(ptadd_ctx* ctx, ptadd_junction_info* info, int32_t* seg, int32_t* last,
                                  int32_t* count, double* break_time);
+
+/* Junctions in a batched ensemble (Sec. 2.2, in each of the independent
+ * bursts of Sec. 4.1): the rules of ptadd_set_junctions in every realisation
+ * r, each with its own DD clock, stuck test and jumps; the break fractions of
+ * realisation r come from the stream of seed ^ (r * 0x9E3779B97F4A7C15)
+ * (unsigned 64-bit product) with the realisation-local node number, so that
+ * realisation r behaves as it would alone under ptadd_set_junctions with
+ * that seed (the capture search reaches the same segment: the lowest
+ * position among the realisation's sessile segments, in node order).
+ * ptadd_batch_advance's averages of realisation r divide by the steps' time
+ * plus that realisation's jumps.  p = NULL switches them off; setting them
+ * again clears every junction and every clock.  ptadd_batch_set switches
+ * them off; ptadd_batch_set_nodes and ptadd_batch_set_stress leave them.
+ * PTADD_ERR_STATE without a batch; PTADD_ERR_ARG on negative or non-finite
+ * parameters. */
+ptadd_status ptadd_batch_set_junctions(ptadd_ctx* ctx, const ptadd_junction_params* p);
+/* info[R] (one per realisation, caller-owned); the per-node arrays (n nodes
+ * of the batch each, any may be NULL) in realisation-local numbers: seg =
+ * start node of the held sessile segment within its realisation or -1, last
+ * = loop (numbered from 0 within the realisation) last broken from or -1,
+ * count = junctions formed, break_time (s, on the realisation's clock).
+ * PTADD_ERR_STATE when the batch's junctions are off. */
+ptadd_status ptadd_batch_get_junctions(ptadd_ctx* ctx, ptadd_junction_info* info, int32_t* seg, int32_t* last,
+                                       int32_t* count, double* break_time);
 
 /* Block stress average of the coupling (Sec. 4.2, the stress-averaging
  * block; host only, no GPU): <T>_r = sum_{g in r} w_g T_g / sum_{g in r} w_g

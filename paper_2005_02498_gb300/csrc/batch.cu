@@ -4,7 +4,8 @@
 //
 // Layout: the realisations' nodes are concatenated (realisation r owns nodes
 // [node_off[r], node_off[r+1])); every per-node table is indexed globally.
-// One DD step is five phases, each one launch:
+// One DD step is five phases, each one launch (nine with junctions: release,
+// capture search and hold after the node phase, the clock event at the end):
 //   prep     : source records (FP64 + FP32 hi/lo about the realisation's origin)
 //   pair     : PERSISTENT kernel (one block per SM slot) that pulls work tiles
 //              (realisation, <= TPB targets, source chunk) from a list sorted
@@ -93,6 +94,10 @@ struct DevBatch {
     double graph_dt = 0.0;
     int graph_prec = -1;
     int graph_cur = -1;
+    bool graph_junc = false;
+    DevBatchJunctions* junc = nullptr;  // junctions (ptadd_batch_set_junctions), NULL: off
+    double dt_s = 0.0;                  // the step of the current burst, s (the junction clock)
+    double time_scale = 0.0;            // mu / B: internal time -> s
 };
 
 namespace {
@@ -302,7 +307,8 @@ __global__ void __launch_bounds__(BRED) batch_lp_euler_kernel(
 }
 
 // One block per realisation: its partials in order, weighted by dt, into
-// acc[16 r + 0..9] (Lp, rho) and acc[16 r + 13..15] (polar velocity).
+// acc[16 r + 0..9] (Lp, rho) and acc[16 r + 13..15] (polar velocity); the
+// unweighted line length into acc[16 r + 11].
 __global__ void batch_finish_kernel(const int32_t* __restrict__ real_blk, const double* __restrict__ partial,
                                     double dt, double* __restrict__ acc)
 {
@@ -328,6 +334,7 @@ __global__ void batch_finish_kernel(const int32_t* __restrict__ real_blk, const 
         const int slot = threadIdx.x < 10 ? threadIdx.x : threadIdx.x + 3;
         acc[16 * r + slot] = fma(red[0][threadIdx.x], dt, acc[16 * r + slot]);
     }
+    if (threadIdx.x == 9) acc[16 * r + 11] = red[0][9];  // the step's line length (junction jumps weight it)
 }
 
 __global__ void batch_soa_to_aos(int64_t n, const double* __restrict__ soa, double scale, double* __restrict__ aos)
@@ -495,19 +502,31 @@ cudaError_t batch_step(DevBatch& B, int prec, const Consts& c, double dt_hat, cu
                                          B.d_node_off, B.d_fp_base, B.d_chunks, B.fpart, B.force, B.vel);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (B.junc) {
+        e = launch_batch_junction_update(B.junc, B.pos[B.cur], B.src32, B.nxt, B.loop_of, B.real_of, B.d_node_off,
+                                         B.pinned, B.vel, s);
+        if (e != cudaSuccess) return e;
+    }
     batch_lp_euler_kernel<<<B.nblk, BRED, 0, s>>>(B.n, B.pos[B.cur], B.pos[1 - B.cur], B.nxt, B.loop_of, B.loop_b,
                                                   B.vel, B.d_blk_real, B.d_blk_start, B.d_node_off, dt_hat, B.partial,
                                                   B.flag);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     batch_finish_kernel<<<B.R, 128, 0, s>>>(B.d_real_blk, B.partial, dt_hat, B.acc);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (B.junc) {
+        e = launch_batch_junction_event(B.junc, B.acc, B.dt_s, dt_hat, B.time_scale, s);
+        if (e != cudaSuccess) return e;
+    }
     B.cur = 1 - B.cur;
-    return cudaGetLastError();
+    return cudaSuccess;
 }
 
 void free_batch(DevBatch& B)
 {
     if (B.graph) cudaGraphExecDestroy(B.graph);
+    batch_junctions_free(B.junc);
     void* ptrs[] = {B.pos[0],   B.pos[1],    B.nxt,       B.prv,        B.loop_of,  B.real_of, B.tgt,
                     B.loop_b,   B.loop_n,    B.pinned,    B.src,        B.src32,    B.fpart,   B.vel,
                     B.force,    B.partial,   B.acc,       B.d_node_off, B.d_fp_base, B.d_chunks, B.d_origin,
@@ -844,9 +863,13 @@ ptadd_status ptadd_batch_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, dou
     const int prec = (int)ctx->prec;
     PTADD_CUDA(cudaMemsetAsync(B.acc, 0, 16 * (size_t)B.R * sizeof(double), s));
     PTADD_CUDA(cudaMemsetAsync(B.flag, 0, sizeof(int), s));
+    B.dt_s = dt;
+    B.time_scale = ctx->mat.mu / ctx->mat.B;
+    const bool junc = B.junc != nullptr;
+    const int per_step = junc ? 9 : 5;
     int64_t left = n_steps;
     if (left >= 2) {
-        if (!B.graph || B.graph_dt != dt_hat || B.graph_prec != prec || B.graph_cur != B.cur) {
+        if (!B.graph || B.graph_dt != dt_hat || B.graph_prec != prec || B.graph_cur != B.cur || B.graph_junc != junc) {
             if (B.graph) cudaGraphExecDestroy(B.graph);
             B.graph = nullptr;
             const int cur0 = B.cur;
@@ -872,16 +895,17 @@ ptadd_status ptadd_batch_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, dou
             B.graph_dt = dt_hat;
             B.graph_prec = prec;
             B.graph_cur = B.cur;
+            B.graph_junc = junc;
         }
         while (left >= 2) {
             PTADD_CUDA(cudaGraphLaunch(B.graph, s));
             left -= 2;
-            ctx->kernel_launches += 2 * 5;
+            ctx->kernel_launches += 2 * per_step;
         }
     }
     if (left == 1) {
         PTADD_CUDA(batch_step(B, prec, c, dt_hat, s));
-        ctx->kernel_launches += 5;
+        ctx->kernel_launches += per_step;
     }
     std::vector<double> acc(16 * (size_t)B.R);
     int flag = 0;
@@ -889,10 +913,11 @@ ptadd_status ptadd_batch_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, dou
     PTADD_CUDA(cudaMemcpyAsync(&flag, B.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     PTADD_CUDA(cudaStreamSynchronize(s));
     const double l = ctx->len_unit;
-    const double St = dt_hat * (double)n_steps;
     bool finite = flag == 0;
     B.last_LV.assign(3 * (size_t)B.R, 0.0);
     for (int r = 0; r < B.R; ++r) {
+        // Eq. 2.5; the time a realisation jumped over while stuck counts with Lp = 0 and the step's rho
+        const double St = dt_hat * (double)n_steps + (junc ? acc[16 * r + 12] : 0.0);
         const double lp_scale = l * l * l * ctx->mat.mu / (ctx->mat.B * B.volume[r]);
         const double rho_scale = l / B.volume[r];
         const double v_scale = l * l * ctx->mat.mu / (ctx->mat.B * B.volume[r]);
@@ -910,6 +935,45 @@ ptadd_status ptadd_batch_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, dou
         return PTADD_ERR_NONFINITE;
     }
     return PTADD_OK;
+}
+
+ptadd_status ptadd_batch_set_junctions(ptadd_ctx* ctx, const ptadd_junction_params* p)
+{
+    if (!ctx || !ctx->batch) {
+        set_error("ptadd_batch_set_junctions: no batch loaded");
+        return PTADD_ERR_STATE;
+    }
+    if (p && !(p->capture_radius >= 0.0 && isfinite(p->capture_radius) && p->max_break_time >= 0.0 &&
+               isfinite(p->max_break_time) && p->stuck_disp >= 0.0 && isfinite(p->stuck_disp)))
+        return barg("ptadd_batch_set_junctions: parameters must be non-negative and finite");
+    PTADD_CUDA(cudaSetDevice(ctx->device));
+    DevBatch& B = *ctx->batch;
+    PTADD_CUDA(cudaStreamSynchronize(ctx->own_stream));
+    batch_junctions_free(B.junc);
+    if (B.graph) {  // it holds the old junction state's pointers
+        cudaGraphExecDestroy(B.graph);
+        B.graph = nullptr;
+    }
+    if (!p) return PTADD_OK;
+    const int64_t n = B.n;
+    std::vector<uint8_t> pin(n);
+    std::vector<int32_t> nxt(n), lof(n);
+    PTADD_CUDA(cudaMemcpy(pin.data(), B.pinned, n, cudaMemcpyDeviceToHost));
+    PTADD_CUDA(cudaMemcpy(nxt.data(), B.nxt, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    PTADD_CUDA(cudaMemcpy(lof.data(), B.loop_of, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return batch_junctions_create(&B.junc, p, ctx->len_unit, B.R, B.node_off, pin, nxt, lof);
+}
+
+ptadd_status ptadd_batch_get_junctions(ptadd_ctx* ctx, ptadd_junction_info* info, int32_t* seg, int32_t* last,
+                                       int32_t* count, double* break_time)
+{
+    if (!ctx || !ctx->batch || !ctx->batch->junc) {
+        set_error("ptadd_batch_get_junctions: junctions of the batch are off");
+        return PTADD_ERR_STATE;
+    }
+    PTADD_CUDA(cudaSetDevice(ctx->device));
+    DevBatch& B = *ctx->batch;
+    return batch_junctions_get(B.junc, B.node_off, ctx->own_stream, info, seg, last, count, break_time);
 }
 
 ptadd_status ptadd_batch_get_polar_velocity(ptadd_ctx* ctx, double core_area, double* V_avg)

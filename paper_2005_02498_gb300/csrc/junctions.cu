@@ -28,11 +28,25 @@
 //     interval to the time sum.
 // Distances and times are formed with explicit round-to-nearest operations,
 // no contraction, so a decision depends only on the positions and the clock.
+//
+// Batched ensembles (ptadd_batch_set_junctions): the same rules per
+// realisation, each with its own clock, stuck test and jumps, and break
+// fractions drawn from the stream of seed ^ (r * 0x9E3779B97F4A7C15) with the
+// realisation-local node number, so realisation r behaves as it would alone
+// under ptadd_set_junctions with that seed.  The capture search is one thread
+// per free node over its realisation's sessile list, staged through shared
+// memory in ascending order: an FP32 distance (positions split into an exact
+// integer part and a remainder about the realisation's origin, as in the pair
+// kernel's records) rejects the segments that are clearly out of reach, with
+// a margin of 4e-6 (|w|_1 + L) that covers its rounding, and the first
+// segment that passes the FP64 test of the single-network search is the
+// node's junction: the lowest position, as there.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "ptadd_internal.cuh"
@@ -199,6 +213,161 @@ __global__ void junction_event_kernel(double* __restrict__ clock, unsigned long 
     red[2] = 0;
 }
 
+// ------------------------------------------------------ batched ensembles
+__global__ void __launch_bounds__(JT) bj_release_kernel(int64_t n, const int32_t* __restrict__ real_of,
+                                                        const int32_t* __restrict__ loop_of,
+                                                        const uint8_t* __restrict__ pinned, int32_t* __restrict__ jseg,
+                                                        int32_t* __restrict__ jlast, const double* __restrict__ jbrk,
+                                                        const double* __restrict__ clock,
+                                                        unsigned long long* __restrict__ red)
+{
+    const int64_t p = blockIdx.x * (int64_t)JT + threadIdx.x;
+    if (p >= n || pinned[p]) return;
+    const int r = real_of[p];
+    const int32_t js = jseg[p];
+    if (js >= 0 && jbrk[p] <= clock[2 * r]) {
+        jlast[p] = loop_of[js];
+        jseg[p] = -1;
+        atomicAdd(&red[6 * r + 4], 1ull);
+    }
+}
+
+constexpr int JB = 128;  // free nodes per search block = sessile segments per staged tile
+constexpr int JREC = 11; // staged record: x1 integer part (3), remainder (3), L, unit tangent (3), loop
+
+// Block: one item (realisation r, up to JB consecutive entries of its free-node
+// list); thread t looks for node free_nodes[f0 + t] if it holds nothing.
+__global__ void __launch_bounds__(JB) bj_search_kernel(
+    const double* __restrict__ pos, int64_t n, const int32_t* __restrict__ nxt, const int32_t* __restrict__ loop_of,
+    const float* __restrict__ src32, const int32_t* __restrict__ sess, const int32_t* __restrict__ sess_off,
+    const int32_t* __restrict__ free_nodes, const int32_t* __restrict__ items, const int32_t* __restrict__ jseg,
+    const int32_t* __restrict__ jlast, int32_t* __restrict__ found, double rc2, float rc_f)
+{
+    __shared__ float rec[JB][JREC];
+    const int r = items[3 * blockIdx.x], f0 = items[3 * blockIdx.x + 1], fc = items[3 * blockIdx.x + 2];
+    const int t = threadIdx.x;
+    int32_t p = -1;
+    bool look = false;
+    if (t < fc) {
+        p = free_nodes[f0 + t];
+        look = jseg[p] < 0;
+    }
+    float ph[3] = {0.f, 0.f, 0.f}, pl[3] = {0.f, 0.f, 0.f};
+    double px = 0.0, py = 0.0, pz = 0.0;
+    int32_t own = -1, left = -1;
+    if (look) {
+        const float* f = src32 + (int64_t)SRC32_STRIDE * p;  // the record of segment p starts at node p
+        for (int c = 0; c < 3; ++c) {
+            ph[c] = f[c];
+            pl[c] = f[3 + c];
+        }
+        px = pos[p];
+        py = pos[n + p];
+        pz = pos[2 * n + p];
+        own = loop_of[p];
+        left = jlast[p];
+    }
+    int32_t best = INT32_MAX;
+    const int k0 = sess_off[r], k1 = sess_off[r + 1];
+    for (int kb = k0; kb < k1; kb += JB) {
+        // (also the barrier between the last tile's reads and this tile's writes)
+        if (!__syncthreads_or(look && best == INT32_MAX)) break;
+        if (kb + t < k1) {
+            const int32_t sg = sess[kb + t];
+            const float* f = src32 + (int64_t)SRC32_STRIDE * sg;
+#pragma unroll
+            for (int c = 0; c < 10; ++c) rec[t][c] = f[c];
+            rec[t][10] = __int_as_float(loop_of[sg]);
+        }
+        __syncthreads();
+        if (look && best == INT32_MAX) {
+            const int m = min(JB, k1 - kb);
+            for (int q = 0; q < m; ++q) {
+                const int32_t sl = __float_as_int(rec[q][10]);
+                if (sl == own || sl == left) continue;
+                // w = x_p - x_1: integer parts exactly, then the remainders
+                const float wx = (ph[0] - rec[q][0]) + (pl[0] - rec[q][3]);
+                const float wy = (ph[1] - rec[q][1]) + (pl[1] - rec[q][4]);
+                const float wz = (ph[2] - rec[q][2]) + (pl[2] - rec[q][5]);
+                const float L = rec[q][6], tx = rec[q][7], ty = rec[q][8], tz = rec[q][9];
+                const float u = fminf(fmaxf(wx * tx + wy * ty + wz * tz, 0.0f), L);
+                const float rx = wx - u * tx, ry = wy - u * ty, rz = wz - u * tz;
+                const float dl = 4e-6f * (fabsf(wx) + fabsf(wy) + fabsf(wz) + L);
+                if (rx * rx + ry * ry + rz * rz >= (rc_f + dl) * (rc_f + dl)) continue;
+                const int32_t sg = sess[kb + q], e = nxt[sg];
+                const double sp[6] = {pos[sg], pos[n + sg], pos[2 * n + sg], pos[e], pos[n + e], pos[2 * n + e]};
+                if (seg_dist2(px, py, pz, sp) < rc2) {
+                    best = kb + q;
+                    break;
+                }
+            }
+        }
+    }
+    if (look) found[p] = best;
+}
+
+__global__ void __launch_bounds__(JT) bj_hold_kernel(
+    int64_t n, const int32_t* __restrict__ real_of, const int64_t* __restrict__ node_off,
+    const uint8_t* __restrict__ pinned, double* __restrict__ vel, const int32_t* __restrict__ sess,
+    int32_t* __restrict__ jseg, int32_t* __restrict__ jcount, double* __restrict__ jbrk,
+    const int32_t* __restrict__ found, const double* __restrict__ clock, double a, uint64_t seed,
+    unsigned long long* __restrict__ red)
+{
+    const int64_t p = blockIdx.x * (int64_t)JT + threadIdx.x;
+    if (p >= n || pinned[p]) return;
+    const int r = real_of[p];
+    unsigned long long* rd = red + 6 * r;
+    int32_t js = jseg[p];
+    if (js < 0 && found[p] != INT32_MAX) {  // (found is written for every node that looked this step)
+        js = sess[found[p]];
+        const int32_t k = jcount[p];
+        const uint64_t sr = seed ^ ((uint64_t)r * 0x9E3779B97F4A7C15ull);
+        jbrk[p] = __dadd_rn(clock[2 * r], __dmul_rn(a, break_fraction(sr, p - node_off[r], k)));
+        jcount[p] = k + 1;
+        jseg[p] = js;
+        atomicAdd(&rd[3], 1ull);
+    }
+    if (js >= 0) {
+        vel[p] = 0.0;
+        vel[n + p] = 0.0;
+        vel[2 * n + p] = 0.0;
+        atomicAdd(&rd[2], 1ull);
+        atomicMin(&rd[1], (unsigned long long)__double_as_longlong(jbrk[p]));
+    } else {
+        const double v2 = vel[p] * vel[p] + vel[n + p] * vel[n + p] + vel[2 * n + p] * vel[2 * n + p];
+        atomicMax(&rd[0], (unsigned long long)__double_as_longlong(v2));
+    }
+}
+
+// one thread per realisation: the clock step or the jump (as junction_event_kernel)
+__global__ void bj_event_kernel(int R, double* __restrict__ clock, unsigned long long* __restrict__ red,
+                                double* __restrict__ acc, double dt_s, double dt_hat, double stuck_hat,
+                                double time_scale)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    double* ck = clock + 2 * r;
+    unsigned long long* rd = red + 6 * r;
+    double* ac = acc + 16 * r;
+    const double t1 = __dadd_rn(ck[0], dt_s);
+    const double vmax = sqrt(__longlong_as_double((long long)rd[0]));
+    const double tmin = __longlong_as_double((long long)rd[1]);
+    double tn = t1;
+    if (rd[2] > 0 && vmax * dt_hat < stuck_hat && tmin > t1) {
+        const double jump = __dsub_rn(tmin, t1);
+        ck[1] = __dadd_rn(ck[1], jump);
+        const double jh = jump * time_scale;
+        ac[9] = fma(ac[11], jh, ac[9]);
+        ac[12] += jh;
+        rd[5] += 1;
+        tn = tmin;
+    }
+    ck[0] = tn;
+    rd[0] = 0;
+    rd[1] = INF_BITS;
+    rd[2] = 0;
+}
+
 }  // namespace
 
 void junctions_free(ptadd_ctx* ctx)
@@ -276,6 +445,186 @@ ptadd_status junction_state_set(ptadd_ctx* ctx, const char* src)
     PTADD_CUDA(cudaMemcpyAsync(j->clock, src + n * 20, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
     PTADD_CUDA(cudaMemcpyAsync(j->red + 3, src + n * 20 + 16, 3 * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
     PTADD_CUDA(cudaStreamSynchronize(s));
+    return PTADD_OK;
+}
+
+struct DevBatchJunctions {
+    double rc2 = 0, a = 0, stuck_hat = 0;
+    float rc_f = 0;
+    uint64_t seed = 0;
+    int32_t R = 0;
+    int64_t n = 0;
+    int32_t* sess = nullptr;        // sessile segments, by realisation, ascending
+    int32_t* sess_off = nullptr;    // [R + 1]
+    int32_t* free_nodes = nullptr;  // unpinned nodes, by realisation, ascending
+    int32_t* items = nullptr;       // [3 n_items]: realisation, first free-list entry, count (<= JB)
+    int n_items = 0;
+    int32_t* seg = nullptr;    // per node: held sessile segment (global node number) or -1
+    int32_t* last = nullptr;   // per node: sessile loop last broken from (global loop number) or -1
+    int32_t* count = nullptr;  // per node: junctions formed
+    int32_t* found = nullptr;  // per node: this step's capture (sessile list position) or INT32_MAX
+    double* brk = nullptr;     // per node: break time on its realisation's clock, s
+    double* clock = nullptr;   // [2R]: DD time, time jumped (s)
+    unsigned long long* red = nullptr;  // [6R]: as DevJunctions::red, per realisation
+    std::vector<int64_t> loop_base;     // first loop of each realisation (host)
+};
+
+void batch_junctions_free(DevBatchJunctions*& j)
+{
+    if (!j) return;
+    void* ptrs[] = {j->sess, j->sess_off, j->free_nodes, j->items, j->seg, j->last,
+                    j->count, j->found, j->brk, j->clock, j->red};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    delete j;
+    j = nullptr;
+}
+
+ptadd_status batch_junctions_create(DevBatchJunctions** out, const ptadd_junction_params* p, double len_unit,
+                                    int32_t R, const std::vector<int64_t>& node_off, const std::vector<uint8_t>& pin,
+                                    const std::vector<int32_t>& nxt, const std::vector<int32_t>& loop_of)
+{
+    *out = nullptr;
+    const int64_t n = node_off[R];
+    std::vector<int32_t> sess, sess_off(R + 1, 0), freel, items;
+    DevBatchJunctions* j = new DevBatchJunctions;
+    j->loop_base.assign(R, 0);
+    for (int r = 0; r < R; ++r) {
+        sess_off[r] = (int32_t)sess.size();
+        const size_t f0 = freel.size();
+        j->loop_base[r] = loop_of[node_off[r]];
+        for (int64_t i = node_off[r]; i < node_off[r + 1]; ++i) {
+            if (pin[i] && pin[nxt[i]]) sess.push_back((int32_t)i);
+            if (!pin[i]) freel.push_back((int32_t)i);
+        }
+        for (size_t f = f0; f < freel.size(); f += JB) {
+            items.push_back(r);
+            items.push_back((int32_t)f);
+            items.push_back((int32_t)std::min<size_t>(JB, freel.size() - f));
+        }
+    }
+    sess_off[R] = (int32_t)sess.size();
+    j->rc2 = (p->capture_radius / len_unit) * (p->capture_radius / len_unit);
+    j->rc_f = (float)(p->capture_radius / len_unit);
+    j->a = p->max_break_time;
+    j->stuck_hat = p->stuck_disp / len_unit;
+    j->seed = p->seed;
+    j->R = R;
+    j->n = n;
+    j->n_items = (int)(items.size() / 3);
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void** q, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(q, bytes > 0 ? bytes : 1);
+    };
+    al((void**)&j->sess, sess.size() * sizeof(int32_t));
+    al((void**)&j->sess_off, sess_off.size() * sizeof(int32_t));
+    al((void**)&j->free_nodes, freel.size() * sizeof(int32_t));
+    al((void**)&j->items, items.size() * sizeof(int32_t));
+    al((void**)&j->seg, n * sizeof(int32_t));
+    al((void**)&j->last, n * sizeof(int32_t));
+    al((void**)&j->count, n * sizeof(int32_t));
+    al((void**)&j->found, n * sizeof(int32_t));
+    al((void**)&j->brk, n * sizeof(double));
+    al((void**)&j->clock, 2 * (size_t)R * sizeof(double));
+    al((void**)&j->red, 6 * (size_t)R * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        set_error("ptadd_batch_set_junctions: cudaMalloc failed: %s", cudaGetErrorString(e));
+        batch_junctions_free(j);
+        return PTADD_ERR_NOMEM;
+    }
+    std::vector<unsigned long long> red0(6 * (size_t)R, 0ull);
+    for (int r = 0; r < R; ++r) red0[6 * r + 1] = INF_BITS;
+    auto chk = [&](cudaError_t c) {
+        if (e == cudaSuccess) e = c;
+    };
+    auto up = [&](void* d, const void* h, size_t bytes) {
+        if (bytes) chk(cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice));
+    };
+    up(j->sess, sess.data(), sess.size() * sizeof(int32_t));
+    up(j->sess_off, sess_off.data(), sess_off.size() * sizeof(int32_t));
+    up(j->free_nodes, freel.data(), freel.size() * sizeof(int32_t));
+    up(j->items, items.data(), items.size() * sizeof(int32_t));
+    up(j->red, red0.data(), red0.size() * sizeof(unsigned long long));
+    chk(cudaMemset(j->seg, 0xFF, n * sizeof(int32_t)));  // -1
+    chk(cudaMemset(j->last, 0xFF, n * sizeof(int32_t)));
+    chk(cudaMemset(j->count, 0, n * sizeof(int32_t)));
+    {
+        const std::vector<int32_t> none(n, INT32_MAX);  // no capture
+        up(j->found, none.data(), n * sizeof(int32_t));
+    }
+    chk(cudaMemset(j->brk, 0, n * sizeof(double)));
+    chk(cudaMemset(j->clock, 0, 2 * (size_t)R * sizeof(double)));
+    if (e != cudaSuccess) {
+        set_error("ptadd_batch_set_junctions: initialising the junction state failed: %s", cudaGetErrorString(e));
+        batch_junctions_free(j);
+        return PTADD_ERR_CUDA;
+    }
+    *out = j;
+    return PTADD_OK;
+}
+
+cudaError_t launch_batch_junction_update(DevBatchJunctions* j, const double* pos, const float* src32,
+                                         const int32_t* nxt, const int32_t* loop_of, const int32_t* real_of,
+                                         const int64_t* node_off_dev, const uint8_t* pinned, double* vel,
+                                         cudaStream_t st)
+{
+    const int64_t n = j->n;
+    const unsigned nb = (unsigned)((n + JT - 1) / JT);
+    bj_release_kernel<<<nb, JT, 0, st>>>(n, real_of, loop_of, pinned, j->seg, j->last, j->brk, j->clock, j->red);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (j->n_items > 0) {
+        bj_search_kernel<<<(unsigned)j->n_items, JB, 0, st>>>(pos, n, nxt, loop_of, src32, j->sess, j->sess_off,
+                                                            j->free_nodes, j->items, j->seg, j->last, j->found,
+                                                            j->rc2, j->rc_f);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    bj_hold_kernel<<<nb, JT, 0, st>>>(n, real_of, node_off_dev, pinned, vel, j->sess, j->seg, j->count, j->brk,
+                                      j->found, j->clock, j->a, j->seed, j->red);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_junction_event(DevBatchJunctions* j, double* acc, double dt_s, double dt_hat,
+                                        double time_scale, cudaStream_t st)
+{
+    bj_event_kernel<<<(unsigned)((j->R + 127) / 128), 128, 0, st>>>(j->R, j->clock, j->red, acc, dt_s, dt_hat,
+                                                                    j->stuck_hat, time_scale);
+    return cudaGetLastError();
+}
+
+ptadd_status batch_junctions_get(DevBatchJunctions* j, const std::vector<int64_t>& node_off, cudaStream_t s,
+                                 ptadd_junction_info* info, int32_t* seg, int32_t* last, int32_t* count,
+                                 double* break_time)
+{
+    const int64_t n = j->n;
+    const int R = j->R;
+    std::vector<int32_t> sg(n), ls(n);
+    std::vector<double> clock(2 * (size_t)R);
+    std::vector<unsigned long long> red(6 * (size_t)R);
+    PTADD_CUDA(cudaMemcpyAsync(sg.data(), j->seg, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PTADD_CUDA(cudaMemcpyAsync(ls.data(), j->last, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PTADD_CUDA(cudaMemcpyAsync(clock.data(), j->clock, clock.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PTADD_CUDA(cudaMemcpyAsync(red.data(), j->red, red.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    if (count) PTADD_CUDA(cudaMemcpyAsync(count, j->count, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    if (break_time) PTADD_CUDA(cudaMemcpyAsync(break_time, j->brk, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    PTADD_CUDA(cudaStreamSynchronize(s));
+    for (int r = 0; r < R; ++r) {
+        int64_t held = 0;
+        for (int64_t i = node_off[r]; i < node_off[r + 1]; ++i) {
+            held += sg[i] >= 0;
+            if (seg) seg[i] = sg[i] >= 0 ? (int32_t)(sg[i] - node_off[r]) : -1;
+            if (last) last[i] = ls[i] >= 0 ? (int32_t)(ls[i] - j->loop_base[r]) : -1;
+        }
+        if (info) {
+            info[r].clock = clock[2 * r];
+            info[r].jumped = clock[2 * r + 1];
+            info[r].held = held;
+            info[r].formed = (int64_t)red[6 * r + 3];
+            info[r].broken = (int64_t)red[6 * r + 4];
+            info[r].jumps = (int64_t)red[6 * r + 5];
+        }
+    }
     return PTADD_OK;
 }
 

@@ -123,6 +123,24 @@ ptadd_status junction_state_set(ptadd_ctx* ctx, const char* src);
 
 struct DevBatch;
 void batch_free(ptadd_ctx* ctx);
+// junctions of a batched ensemble (junctions.cu)
+struct DevBatchJunctions;
+void batch_junctions_free(DevBatchJunctions*& j);
+ptadd_status batch_junctions_create(DevBatchJunctions** out, const ptadd_junction_params* p, double len_unit,
+                                    int32_t R, const std::vector<int64_t>& node_off, const std::vector<uint8_t>& pin,
+                                    const std::vector<int32_t>& nxt, const std::vector<int32_t>& loop_of);
+// release, capture search and hold of one step (after the velocity stage)
+cudaError_t launch_batch_junction_update(DevBatchJunctions* j, const double* pos, const float* src32,
+                                         const int32_t* nxt, const int32_t* loop_of, const int32_t* real_of,
+                                         const int64_t* node_off_dev, const uint8_t* pinned, double* vel,
+                                         cudaStream_t st);
+// the per-realisation clock step or jump (after the reduction of the step into acc[16 r ..])
+cudaError_t launch_batch_junction_event(DevBatchJunctions* j, double* acc, double dt_s, double dt_hat,
+                                        double time_scale, cudaStream_t st);
+// junction state with realisation-local node and loop numbers; info[R]
+ptadd_status batch_junctions_get(DevBatchJunctions* j, const std::vector<int64_t>& node_off, cudaStream_t s,
+                                 ptadd_junction_info* info, int32_t* seg, int32_t* last, int32_t* count,
+                                 double* break_time);
 struct MlpDev;
 void mlp_free(ptadd_ctx* ctx);
 

@@ -35,7 +35,8 @@ EXPORTS = ["ptadd_version", "ptadd_create", "ptadd_destroy", "ptadd_last_error",
            "ptadd_surrogate_fit", "ptadd_surrogate_predict", "ptadd_surrogate_predict_dev",
            "ptadd_closure_sweep", "ptadd_closure_realisation", "ptadd_dissipation_projection",
            "ptadd_dissipation_projection_dev",
-           "ptadd_block_average", "ptadd_block_stress_pair", "ptadd_set_junctions", "ptadd_get_junctions", "ptadd_system_densities",
+           "ptadd_block_average", "ptadd_block_stress_pair", "ptadd_set_junctions", "ptadd_get_junctions",
+           "ptadd_batch_set_junctions", "ptadd_batch_get_junctions", "ptadd_system_densities",
            "ptadd_surrogate_get_state", "ptadd_surrogate_set_state"]
 NOALLOC_MAX_SEGMENTS = 16384
 
@@ -202,6 +203,10 @@ def load(build_if_missing=True):
     lib.ptadd_set_junctions.restype = st
     lib.ptadd_get_junctions.argtypes = [_VP, ctypes.POINTER(JunctionInfo), _I32, _I32, _I32, _D]
     lib.ptadd_get_junctions.restype = st
+    lib.ptadd_batch_set_junctions.argtypes = [_VP, ctypes.POINTER(JunctionParams)]
+    lib.ptadd_batch_set_junctions.restype = st
+    lib.ptadd_batch_get_junctions.argtypes = [_VP, ctypes.POINTER(JunctionInfo), _I32, _I32, _I32, _D]
+    lib.ptadd_batch_get_junctions.restype = st
     lib.ptadd_system_densities.argtypes = [ctypes.c_int64, _D, ctypes.c_int64, _I64, _D, _D, _U8, ctypes.c_double, _D]
     lib.ptadd_system_densities.restype = st
     lib.ptadd_block_average.argtypes = [ctypes.c_int64, _D, _D, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, _D]
@@ -574,6 +579,28 @@ class Context:
         out = np.zeros((self.batch_n, 3))
         _check(self._lib.ptadd_batch_get_forces(self._h, _dptr(out)))
         return out
+
+    def batch_set_junctions(self, capture_radius=None, max_break_time=1e-3, stuck_disp=0.0, seed=0):
+        """ptadd_batch_set_junctions; capture_radius None switches them off."""
+        if capture_radius is None:
+            _check(self._lib.ptadd_batch_set_junctions(self._h, None))
+            return
+        p = JunctionParams(float(capture_radius), float(max_break_time), float(stuck_disp), int(seed))
+        _check(self._lib.ptadd_batch_set_junctions(self._h, ctypes.byref(p)))
+
+    def batch_junctions(self):
+        """ptadd_batch_get_junctions: list of R dicts (clock, jumped, held,
+        formed, broken, jumps) and the per-node arrays seg, last, count,
+        break_time [n_nodes] in realisation-local numbers."""
+        R, n = self.batch_R, self.batch_n
+        info = (JunctionInfo * R)()
+        seg, last, cnt = (np.zeros(n, np.int32) for _ in range(3))
+        brk = np.zeros(n)
+        i32 = ctypes.POINTER(ctypes.c_int32)
+        _check(self._lib.ptadd_batch_get_junctions(self._h, info, seg.ctypes.data_as(i32), last.ctypes.data_as(i32),
+                                                   cnt.ctypes.data_as(i32), _dptr(brk)))
+        per = [{k: getattr(info[r], k) for k, _ in JunctionInfo._fields_} for r in range(R)]
+        return per, dict(seg=seg, last=last, count=cnt, break_time=brk)
 
     def batch_autotune(self, cache_path=None, force=False):
         _check(self._lib.ptadd_batch_autotune(self._h, cache_path.encode() if cache_path else None,
