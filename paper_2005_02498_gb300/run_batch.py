@@ -8,7 +8,10 @@ fraction ~ U(0.1, 0.9), loop density 16 per um^3, dt = 1e-11 s.  One PTA
 closure is one realisation's burst of --burst-steps (2000) steps; the
 closures/s figure extrapolates the measured time per step to that burst.
 Optionally times plain FP64 on the first --fp64-R realisations and reports
-its closures/s extrapolated per segment pair to the whole batch.
+its closures/s extrapolated per segment pair to the whole batch.  With
+--junction-radius the burst runs with junctions (ptadd_batch_set_junctions:
+maximum break time --junction-a, stuck displacement --junction-stuck, every
+realisation on its own clock) and reports their counts and the clocks.
 Prints one JSON line.
 """
 
@@ -38,6 +41,9 @@ def main(argv=None):
     p.add_argument("--fp64-R", type=int, default=0)
     p.add_argument("--fp64-steps", type=int, default=2)
     p.add_argument("--device", type=int, default=0)
+    p.add_argument("--junction-radius", type=float, default=0.0, help="m; 0: junctions off")
+    p.add_argument("--junction-a", type=float, default=1e-3)
+    p.add_argument("--junction-stuck", type=float, default=2.556e-12)
     a = p.parse_args(argv)
 
     t0 = time.perf_counter()
@@ -56,12 +62,28 @@ def main(argv=None):
             out["autotune_s"] = time.perf_counter() - t0
         info = ctx.batch_info()
         out.update({k: info[k] for k in ("pairs_per_step", "work_items", "tile_targets", "chunk_sources", "tuned")})
+        if a.junction_radius > 0:
+            ctx.batch_set_junctions(a.junction_radius, a.junction_a, a.junction_stuck, a.seed)
         ctx.batch_advance(2, a.dt)  # warm-up (captures the step graph)
         ctx.batch_set_nodes(batch.xyz)
+        if a.junction_radius > 0:  # clear the warm-up's junctions and clocks
+            ctx.batch_set_junctions(a.junction_radius, a.junction_a, a.junction_stuck, a.seed)
+            ctx.batch_advance(2, a.dt)  # (the graph is captured again)
+            ctx.batch_set_nodes(batch.xyz)
+            ctx.batch_set_junctions(a.junction_radius, a.junction_a, a.junction_stuck, a.seed)
         t0 = time.perf_counter()
         Lp, rho = ctx.batch_advance(a.steps, a.dt)
         el = time.perf_counter() - t0
         ms_step = 1e3 * el / a.steps
+        if a.junction_radius > 0:
+            per, _ = ctx.batch_junctions()
+            out["junctions"] = {"radius_m": a.junction_radius, "a_s": a.junction_a, "stuck_m": a.junction_stuck,
+                                "formed": int(sum(q["formed"] for q in per)),
+                                "held": int(sum(q["held"] for q in per)),
+                                "broken": int(sum(q["broken"] for q in per)),
+                                "jumps": int(sum(q["jumps"] for q in per)),
+                                "realisations_with_junctions": int(sum(q["formed"] > 0 for q in per)),
+                                "clock_median_s": float(np.median([q["clock"] for q in per]))}
         out.update({"steps": a.steps, "ms_per_step": ms_step,
                     "pair_evals_per_s": info["pairs_per_step"] * a.steps / el,
                     "closures_per_s": a.R / (ms_step * 1e-3 * a.burst_steps),
