@@ -458,14 +458,17 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
             d[11] = make_float4(v[6] * v[6], v[6] * v[6], v[6] + v[6], v[6] + v[6]);
         }
         __syncthreads();
-        // plain sums of the current group of SUM_GROUP sources (/ c2)
-        float2 SG[2][3];
+        // plain sums of the current group of SUM_GROUP sources (/ c2); the
+        // b' term's coefficient is summed on its own (b' is the target's)
+        float2 SG[2][3], SB[2];
         for (int g0 = 0; g0 < cnt; g0 += SUM_GROUP) {
             const int g1 = min(cnt, g0 + SUM_GROUP);
 #pragma unroll
-            for (int p = 0; p < 2; ++p)
+            for (int p = 0; p < 2; ++p) {
+                SB[p] = f2(0.0f);
 #pragma unroll
                 for (int e = 0; e < 3; ++e) SG[p][e] = f2(0.0f);
+            }
 #pragma unroll MIX_UNROLL
             for (int jj = g0; jj < g1; ++jj) {
                 const float2* r = sm.tile + jj * MIX_REC;
@@ -511,17 +514,23 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
                     same_all = same_all && (ny.x >= 0.0f || u2.x <= 0.0f) && (ny.y >= 0.0f || u2.y <= 0.0f);
                 }
                 const bool uni = __all_sync(0xffffffffu, same_all);
+                // both Gauss-point pairs in one straight block per branch, so
+                // that their two chains interleave
+                Coef2 C[2];
+                if (uni) {
+                    seg_coef2<1>(G[0], S, bt2, P, a2, nr, nrq[0][0], nrq[0][1], C[0]);
+                    seg_coef2<1>(G[1], S, bt2, P, a2, nr, nrq[1][0], nrq[1][1], C[1]);
+                } else {
+                    seg_coef2<0>(G[0], S, bt2, P, a2, nr, nrq[0][0], nrq[0][1], C[0]);
+                    seg_coef2<0>(G[1], S, bt2, P, a2, nr, nrq[1][0], nrq[1][1], C[1]);
+                }
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {
-                    Coef2 C;
-                    if (uni)
-                        seg_coef2<1>(G[p], S, bt2, P, a2, nr, nrq[p][0], nrq[p][1], C);
-                    else
-                        seg_coef2<0>(G[p], S, bt2, P, a2, nr, nrq[p][0], nrq[p][1], C);
+                    SB[p] = add2(SB[p], C[p].cb);  // (times b' when the group closes)
 #pragma unroll
                     for (int e = 0; e < 3; ++e)
-                        SG[p][e] = fma2(C.cRxb, C.X[e], fma2(C.cq, S.q[e], fma2(C.cRp, G[p].Rp[e],
-                                        fma2(C.ct, S.t[e], fma2(C.cb, bt2[e], SG[p][e])))));
+                        SG[p][e] = fma2(C[p].cRxb, C[p].X[e], fma2(C[p].cq, S.q[e], fma2(C[p].cRp, G[p].Rp[e],
+                                        fma2(C[p].ct, S.t[e], SG[p][e]))));
                 }
                 if (__any_sync(0xffffffffu, nrq[0][0] || nrq[0][1] || nrq[1][0] || nrq[1][1])) {
                     const unsigned js = (unsigned)(j0 + jj);
@@ -542,6 +551,10 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
                 }
             }
             // close the group
+#pragma unroll
+            for (int p = 0; p < 2; ++p)
+#pragma unroll
+                for (int e = 0; e < 3; ++e) SG[p][e] = fma2(SB[p], bt2[e], SG[p][e]);
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
                 float2 sk = sm.ksum[k * TPB + threadIdx.x], ck = sm.ksum[(6 + k) * TPB + threadIdx.x];
