@@ -11,6 +11,9 @@
 //                   partial sums; lp_finish sums them in a fixed order into
 //                   the running averages of Eq. 2.5.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
 #include <math.h>
 
 #include "pair_tile.cuh"
@@ -113,16 +116,32 @@ int choose_chunks(int64_t n_tgt, int64_t n_src, int max_chunks, int precision)
     // About 16 waves of resident blocks, so that the blocks still running
     // when the others have finished (the tail) cost a few per cent; chunks of
     // at least two source tiles, so the per-block set-up and the nodal
-    // output stay small next to the pair work.
+    // output stay small next to the pair work, unless that leaves less than
+    // one wave (a small network): then chunks down to 32 sources, so that the
+    // few targets' work (and their FP64 near pairs) spreads over more SMs.
+    // The device queries are made once per device and precision.
+    static std::atomic<int> cached[64][2][2];  // [device][mixed] -> {sms, blocks per SM}; 0: not yet
     int dev = 0, sms = 152, per_sm = 2;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (precision == (int)PTADD_MIXED)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_mixed_kernel, MIX_TPB, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_fp64_kernel, PAIR_TPB, 0);
-    if (per_sm < 1) per_sm = 1;
+    const int mixed = precision == (int)PTADD_MIXED ? 1 : 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 &&
+        cached[dev][mixed][0].load(std::memory_order_acquire) > 0) {
+        sms = cached[dev][mixed][0].load(std::memory_order_relaxed);
+        per_sm = cached[dev][mixed][1].load(std::memory_order_relaxed);
+    } else {
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (mixed)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_mixed_kernel, MIX_TPB, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pair_fp64_kernel, PAIR_TPB, 0);
+        if (per_sm < 1) per_sm = 1;
+        if (dev >= 0 && dev < 64) {
+            cached[dev][mixed][1].store(per_sm, std::memory_order_relaxed);
+            cached[dev][mixed][0].store(sms, std::memory_order_release);
+        }
+    }
     const int64_t tiles_t = (n_tgt + PAIR_TPB - 1) / PAIR_TPB;
     int64_t cap = n_src / (2 * PAIR_TILE);
+    if (tiles_t * cap < (int64_t)sms * per_sm) cap = std::max<int64_t>(cap, n_src / 32);
     if (cap > max_chunks) cap = max_chunks;
     if (cap < 1) cap = 1;
     const int64_t want_blocks = (int64_t)sms * per_sm * 16;
