@@ -48,7 +48,7 @@ struct MlpDev {
     int64_t cap = 0;  // row capacity of the work buffers (multiple of 128)
     float *W[4] = {}, *b[4] = {}, *mW[4] = {}, *vW[4] = {}, *mb[4] = {}, *vb[4] = {}, *gW[4] = {}, *gb[4] = {};
     __nv_bfloat16 *Wb[4] = {}, *Wt[4] = {};
-    __nv_bfloat16* Wc = nullptr;  // W2, W3 pre-tiled for the fused inference kernel (8 x 256 x 64)
+    __nv_bfloat16* Wc = nullptr;  // layers 2, 3 staged for the fused inference kernel (bias block + 4 x 256 x 64 each)
     __nv_bfloat16 *X = nullptr, *Xt = nullptr, *Hb[3] = {}, *Ht[3] = {}, *dY = nullptr, *dYt = nullptr;
     __nv_bfloat16 *dZ[3] = {}, *dZt[3] = {};
     float *Z[3] = {}, *Y = nullptr, *T = nullptr, *loss_part = nullptr;
@@ -127,7 +127,7 @@ ptadd_status alloc_params(MlpDev& m)
         if (st == PTADD_OK) st = m_alloc(&m.Wt[l], nw);
     }
     if (st == PTADD_OK) st = m_alloc(&m.err, 1);
-    if (st == PTADD_OK) st = m_alloc(&m.Wc, (size_t)8 * 256 * 64);
+    if (st == PTADD_OK) st = m_alloc(&m.Wc, (size_t)2 * (256 * 16 + 4 * 256 * 64));
     if (st == PTADD_OK) st = m_alloc(&m.d_norm, 4 * NIN + 2 * NOUT + NIN * NIN + 1);
     return st;
 }

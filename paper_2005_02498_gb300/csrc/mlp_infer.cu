@@ -16,11 +16,12 @@
 //   * warp 16, lane 0 ("MMA issuer"): issues every tcgen05 MMA, each
 //     weight K-slice as soon as its activation chunk and its weights are in
 //     shared memory, and never waits for an MMA to finish;
-//   * warp 17, lane 0 ("weight producer"): streams W2 and W3 through NST
-//     shared-memory stages in bulk copies (cp.async.bulk, completion counted
-//     on an mbarrier) from a copy of the weights pre-tiled into the canonical
-//     operand layout, refilling a stage once the MMAs that read it are done
-//     (tcgen05.commit on the stage's "empty" barrier).
+//   * warp 17, lane 0 ("weight producer"): streams layers 2 and 3 (a bias
+//     block, then the weights in K-chunks) through NST shared-memory stages
+//     in bulk copies (cp.async.bulk, completion counted on an mbarrier) from
+//     a copy pre-tiled into the canonical operand layout, refilling a stage
+//     once the MMAs that read it are done (tcgen05.commit on the stage's
+//     "empty" barrier).
 // Trust region: the distance d2 = |L^-1 z|^2 is a 128 x 32 x 32 product,
 // W = Z L^-T, that the tensor core computes next to layer 1 (into 32 spare
 // columns of the second accumulator) in split FP16: z = z_hi + z_lo with
@@ -55,11 +56,14 @@
 // tanh by the hardware f16x2 approximation, and the whole activation in f16x2
 // arithmetic: the kernel stores a' = z (1 + tanh(u)) = 2 GELU(z) and takes
 // the factor 1/2 into the next layer's weights (W2, W3, W4 are scaled by 1/2
-// when they are staged, exactly), so an activation pair costs one FP32 bias
-// add, one conversion, four f16x2 FMA-pipe operations and one special-function
-// operation.  Layer 1's bias rides in the two padding columns of its K = 32
-// operand: the inputs there are 1 and W1's columns hold the bias split into
-// two FP16 parts (b_hi = fp16(b), b_lo = fp16(b - b_hi)).
+// when they are staged, exactly).  Every hidden layer's bias is already in
+// its accumulator, split into two FP16 parts (b_hi = fp16(b), b_lo = fp16(b -
+// b_hi)): layer 1's rides in the two padding columns of its K = 32 operand
+// (inputs 1 there, W1's columns the bias), layers 2 and 3 start with one
+// K = 16 MMA of a constant operand (1 in K columns 0 and 1) against a bias
+// block streamed ahead of the layer's weights.  So an activation pair costs
+// one conversion, four f16x2 FMA-pipe operations and one special-function
+// operation.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -83,6 +87,10 @@ constexpr int KCH = 64;                 // K per streamed weight chunk
 constexpr int NST = 2;                  // weight stages in shared memory
 constexpr int CPL = 256 / KCH;          // chunks per layer (W2, W3)
 constexpr int WC_BYTES = 256 * KCH * 2; // one K-chunk of W2 or W3, 8-row groups 16 KCH bytes apart
+constexpr int BB_BYTES = 256 * 16 * 2;  // a layer's bias block: 256 rows x K 16 (b_hi, b_lo, 0...), SBO 256
+constexpr int IPL = CPL + 1;            // stream items per layer: the bias block, then the K-chunks
+constexpr int LAYER_BYTES = BB_BYTES + CPL * WC_BYTES;
+constexpr int ONES_BYTES = 128 * 16 * 2;  // A operand of the bias MMA: K columns 0, 1 = 1, the rest 0
 constexpr int NV_FLOATS = 4 * NF + 2 * NO + NF * NF + 1;
 constexpr int LI_BYTES = 32 * 32 * 2;   // L_hi or L_lo: 32 rows (i) x 32 K (j), SBO 512
 constexpr int MAHA_COL = 288;           // TMEM columns of W (second accumulator, clear of layer 4's 16)
@@ -94,9 +102,10 @@ constexpr int OFF_LL = OFF_LH + LI_BYTES;
 constexpr int OFF_W4 = OFF_LL + LI_BYTES;
 constexpr int OFF_H = OFF_W4 + W4_BYTES;
 constexpr int OFF_WC = OFF_H + H_BYTES;
-constexpr int OFF_NV = OFF_WC + NST * WC_BYTES;
-constexpr int OFF_B = OFF_NV + ((NV_FLOATS * 4 + 15) / 16) * 16;   // biases: 3 x 256 + 16
-constexpr int OFF_F = OFF_B + (3 * 256 + 16) * 4;                  // raw features of a tile [128][30]
+constexpr int OFF_ONES = OFF_WC + NST * WC_BYTES;
+constexpr int OFF_NV = OFF_ONES + ONES_BYTES;
+constexpr int OFF_B = OFF_NV + ((NV_FLOATS * 4 + 15) / 16) * 16;   // layer 4's bias (16)
+constexpr int OFF_F = OFF_B + 16 * 4;                              // raw features of a tile [128][30]
 constexpr int OFF_BOX = OFF_F + 128 * NF * 8;                      // box test per quarter row [2][4][128]
 static_assert(OFF_F % 16 == 0, "bulk copies into the staging buffer need 16-byte alignment");
 constexpr int INFER_SMEM = OFF_BOX + 2 * 4 * 128;
@@ -105,6 +114,16 @@ __device__ __forceinline__ uint32_t canon(int r, int k, int sbo)
 {
     return (uint32_t)((r >> 3) * sbo + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
 }
+
+// Item k (0 <= k < 2 IPL) of the per-tile weight stream: the bias block of
+// layer 2, W2's K-chunks, then the same for layer 3; its offset in the staged
+// copy and its size.
+__device__ __forceinline__ uint32_t item_offset(int k)
+{
+    const int l = k / IPL, i = k % IPL;
+    return (uint32_t)(l * LAYER_BYTES + (i ? BB_BYTES + (i - 1) * WC_BYTES : 0));
+}
+__device__ __forceinline__ uint32_t item_bytes(int k) { return (k % IPL) ? (uint32_t)WC_BYTES : (uint32_t)BB_BYTES; }
 
 __device__ __forceinline__ void cp_async8(uint32_t dst, const void* src)
 {
@@ -267,7 +286,7 @@ struct InferArgs {
     int feat_bulk;       // feat is 16-byte aligned: one bulk copy per tile
     const float* nv;     // xm, xs, ym, ys, box lo, box hi, inverse Cholesky factor, d2 threshold
     const __nv_bfloat16* W[4];
-    const __half* Wc;    // W2 / 2, W3 / 2 (FP16) in 2 CPL pre-tiled K-chunks of 256 x KCH (canonical layout)
+    const __half* Wc;    // per layer 2, 3: bias block, then W / 2 (FP16) in CPL pre-tiled K-chunks of 256 x KCH
     const float* b[4];
     double* lp6;         // [n x 6]
     uint8_t* in_region;  // [n] or null
@@ -294,12 +313,12 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
     uint8_t* sBox = base + OFF_BOX;
     const uint32_t uX = smem_u32(sX), uW1 = smem_u32(sW1), uW4 = smem_u32(sW4), uH = smem_u32(sH);
     const uint32_t uXlo = smem_u32(sXlo), uLH = smem_u32(base + OFF_LH), uLL = smem_u32(base + OFF_LL);
-    const uint32_t uWC = smem_u32(base + OFF_WC);
+    const uint32_t uWC = smem_u32(base + OFF_WC), uOnes = smem_u32(base + OFF_ONES);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int64_t n_tiles = (g.n + 127) / 128;
     if ((int64_t)blockIdx.x >= n_tiles) return;  // whole CTA, before any allocation
     const int64_t my_tiles = (n_tiles - 1 - blockIdx.x) / gridDim.x + 1;
-    const int64_t Q = 2 * CPL * my_tiles;  // chunks of the W2/W3 stream
+    const int64_t Q = 2 * IPL * my_tiles;  // items of the W2/W3 stream
     const uint32_t ux = smem_u32(&xbar), uacc0 = smem_u32(&accbar[0]);
     const uint32_t uh0 = smem_u32(&hbar[0]), ufull0 = smem_u32(&full[0]), uempty0 = smem_u32(&empty[0]);
     // each mbarrier is 8 bytes: barrier k of an array at u0 + 8 k
@@ -356,12 +375,11 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
         *reinterpret_cast<__half*>(base + OFF_LL + canon(i, j, 512)) = __float2half_rn(v - __half2float(hi));
     }
     float* sB = reinterpret_cast<float*>(base + OFF_B);
-    // (the layer index is a constant in each loop: indexing the parameter's
-    // pointer array with a variable would copy the parameters to local memory)
-#pragma unroll
-    for (int l = 0; l < 3; ++l)
-        for (int e = tid; e < 256; e += IT_ALL) sB[256 * l + e] = g.b[l][e];
-    for (int e = tid; e < 16; e += IT_ALL) sB[768 + e] = g.b[3][e];
+    for (int e = tid; e < 16; e += IT_ALL) sB[e] = g.b[3][e];
+    for (int e = tid; e < 128 * 16; e += IT_ALL) {  // the ones operand of the bias MMAs
+        const int r = e >> 4, k = e & 15;
+        *reinterpret_cast<__half*>(base + OFF_ONES + canon(r, k, 256)) = __float2half_rn(k < 2 ? 1.0f : 0.0f);
+    }
     const uint32_t uF = smem_u32(base + OFF_F), ufbar = smem_u32(&fbar);
     const double* sF = reinterpret_cast<const double*>(base + OFF_F);
     const bool fbulk = g.feat_bulk != 0;
@@ -386,8 +404,9 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
                     abort_flag = 1;
                     break;
                 }
-                mbar_expect_tx(ufull0 + 8 * st, WC_BYTES);
-                bulk_g2s(uWC + st * WC_BYTES, g.Wc + (size_t)(issued % (2 * CPL)) * (WC_BYTES / 2), WC_BYTES,
+                const int k = (int)(issued % (2 * IPL));
+                mbar_expect_tx(ufull0 + 8 * st, item_bytes(k));
+                bulk_g2s(uWC + st * WC_BYTES, reinterpret_cast<const uint8_t*>(g.Wc) + item_offset(k), item_bytes(k),
                          ufull0 + 8 * st);
             }
             // no copy may still be landing when the CTA leaves: wait (bounded)
@@ -435,6 +454,18 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
                             hph ^= 1u << kc;
                             if (!ok) break;
                         }
+                        if (jj == 0) {
+                            // the bias first: ones [128 x 16] (b_hi, b_lo, 0..)^T sets the
+                            // accumulator (only now: the previous layer's epilogue has read it)
+                            const uint32_t st = (uint32_t)(q % NST);
+                            ok = wait_or_abort(ufull0 + 8 * st, (uint32_t)((q / NST) & 1), &abort_flag);
+                            if (!ok) break;
+                            tc_fence_after();
+                            tc_mma_bf16(acc, smem_desc(uOnes, 128, 256), smem_desc(uWC + st * WC_BYTES, 128, 256), id_h,
+                                        0u);
+                            tc_commit(uempty0 + 8 * st);
+                            ++q;
+                        }
                         const uint32_t st = (uint32_t)(q % NST);
                         ok = wait_or_abort(ufull0 + 8 * st, (uint32_t)((q / NST) & 1), &abort_flag);
                         if (!ok) break;
@@ -442,7 +473,7 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
                         const uint32_t ub = uWC + st * WC_BYTES;
                         for (int s = 0; s < KCH / 16; ++s)
                             tc_mma_bf16(acc, smem_desc(uH + (jj * (KCH / 16) + s) * 256, 128, 4096),
-                                        smem_desc(ub + s * 256, 128, 16 * KCH), id_h, (jj | s) ? 1u : 0u);
+                                        smem_desc(ub + s * 256, 128, 16 * KCH), id_h, 1u);
                         tc_commit(uempty0 + 8 * st);  // the stage is free once these MMAs are done
                     }
                     if (!ok) break;
@@ -584,10 +615,7 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
                     uint32_t* nxt = (kc & 1) ? ra : rb;
                     if (kc < 3) tmem_ld16_async(tmem_row + acc_col + (uint32_t)(c0 + 64), nxt);
                     uint32_t w[8];
-                    if (l == 0)
-                        gelu16<false>(cur, c0, nullptr, w);
-                    else
-                        gelu16<true>(cur, c0, sB + 256 * l, w);
+                    gelu16<false>(cur, c0, nullptr, w);  // (every layer's bias is in its accumulator)
                     if (kc > 0) publish(uh0 + 8 * (kc - 1));
                     store16(w, erow, c0, sH);
                 }
@@ -608,7 +636,7 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
                         const int o = 2 * cs + c;
-                        g.lp6[(r0 + erow) * NO + o] = f2d((v[c] + sB[768 + o]) * ys[o] + ym[o]);
+                        g.lp6[(r0 + erow) * NO + o] = f2d((v[c] + sB[o]) * ys[o] + ym[o]);
                     }
                 }
             }
@@ -624,22 +652,37 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
-// W2 / 2 and W3 / 2 (row-major 256 x 256 BF16 in, FP16 out) -> 2 CPL K-chunks
-// of 256 rows x KCH in the canonical no-swizzle K-major layout (8-row x
-// 16-byte core matrices, K-adjacent ones 128 B apart, 8-row groups 16 KCH
-// bytes apart), WC_BYTES each, so a chunk is one contiguous bulk copy into
-// shared memory.
+// The staged copy of layers 2 and 3, LAYER_BYTES each: the bias block
+// (256 rows x K 16 in the canonical no-swizzle K-major layout, 8-row groups
+// 256 B apart: row r holds b_hi = fp16(b_r), b_lo = fp16(b_r - b_hi), then
+// zeros), then W / 2 (row-major 256 x 256 BF16 in, FP16 out) in CPL K-chunks
+// of 256 rows x KCH in the same layout (K-adjacent core matrices 128 B apart,
+// 8-row groups 16 KCH bytes apart), WC_BYTES each; every item is one
+// contiguous bulk copy into shared memory.
 __global__ void tile_weights_kernel(const __nv_bfloat16* __restrict__ W2, const __nv_bfloat16* __restrict__ W3,
+                                    const float* __restrict__ b2, const float* __restrict__ b3,
                                     __half* __restrict__ Wc)
 {
     constexpr int G = KCH / 8;  // 16-byte groups per row of a chunk
-    const int v = blockIdx.x * blockDim.x + threadIdx.x;  // one 16-byte group: chunk j, row r, group kk
-    if (v >= 2 * CPL * 256 * G) return;
-    const int j = v / (256 * G), r = (v / G) % 256, kk = v % G;
-    const __nv_bfloat16* W = j < CPL ? W2 : W3;
-    const int k0 = KCH * (j % CPL) + 8 * kk;
-    uint8_t* dst = reinterpret_cast<uint8_t*>(Wc) + (size_t)j * WC_BYTES + (r >> 3) * (16 * KCH) + kk * 128 + (r & 7) * 16;
-    *reinterpret_cast<uint4*>(dst) = bf16x8_to_f16x8(*reinterpret_cast<const uint4*>(W + r * 256 + k0), 0.5f);
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    uint8_t* base = reinterpret_cast<uint8_t*>(Wc);
+    if (v < 2 * CPL * 256 * G) {  // one 16-byte group of W: chunk j, row r, group kk
+        const int j = v / (256 * G), r = (v / G) % 256, kk = v % G;
+        const int l = j / CPL;
+        const __nv_bfloat16* W = l == 0 ? W2 : W3;
+        const int k0 = KCH * (j % CPL) + 8 * kk;
+        uint8_t* dst = base + (size_t)l * LAYER_BYTES + BB_BYTES + (size_t)(j % CPL) * WC_BYTES + (r >> 3) * (16 * KCH) +
+                       kk * 128 + (r & 7) * 16;
+        *reinterpret_cast<uint4*>(dst) = bf16x8_to_f16x8(*reinterpret_cast<const uint4*>(W + r * 256 + k0), 0.5f);
+    } else if (v < 2 * CPL * 256 * G + 2 * 256) {  // one row of a bias block
+        const int u = v - 2 * CPL * 256 * G, l = u / 256, r = u % 256;
+        const float bb = (l == 0 ? b2 : b3)[r];
+        const __half hi = __float2half_rn(bb), lo = __float2half_rn(bb - __half2float(hi));
+        const __half2 h2 = __halves2half2(hi, lo);
+        uint8_t* dst = base + (size_t)l * LAYER_BYTES + (r >> 3) * 256 + (r & 7) * 16;
+        *reinterpret_cast<uint4*>(dst) = make_uint4(*reinterpret_cast<const uint32_t*>(&h2), 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(dst + 128) = make_uint4(0u, 0u, 0u, 0u);
+    }
 }
 
 }  // namespace
@@ -660,7 +703,7 @@ cudaError_t launch_mlp_infer(const double* feat, int64_t n, const float* nv, con
     if (n <= 0) return cudaSuccess;
     // the staged FP16 weights live in the 2-byte-per-element scratch wc
     __half* wh = reinterpret_cast<__half*>(wc);
-    tile_weights_kernel<<<(2 * 256 * 256 / 8 + 255) / 256, 256, 0, s>>>(W[1], W[2], wh);
+    tile_weights_kernel<<<(2 * CPL * 256 * (KCH / 8) + 2 * 256 + 255) / 256, 256, 0, s>>>(W[1], W[2], b[1], b[2], wh);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int sms = 152;
