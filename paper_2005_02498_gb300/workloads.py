@@ -436,17 +436,46 @@ def schmid_factors(sig6):
 
 
 def junction_microstructure(seed, sig6, rho_m, rho_s, n_loops=64, nodes_per_loop=32,
-                            r_min=0.05 * MICRON, r_max=0.2 * MICRON):
+                            r_min=0.05 * MICRON, r_max=0.2 * MICRON, sessile_case=2):
     """One realisation of the paper's recipe with n_loops glide loops:
     mobile density rho_m (1/m^2) per system in proportion to |f_i|, sessile
     density rho_s evenly over the systems; class counts, radii and senses
-    stratified as in realisation_for_densities."""
+    stratified as in realisation_for_densities.
+
+    sessile_case (the two cases of Sec. 3.2): 2, the sessile loops' Burgers
+    vectors lie in their planes (b . n = 0); 1, Lomer-Cottrell-type locks,
+    whose Burgers vectors lie out of their planes (lomer_cottrell_sessiles).
+    Both cases share the geometry of a seed."""
     f = np.abs(schmid_factors(sig6))
     rho_mi = rho_m * f / f.sum()
     rho_si = np.full(12, rho_s / 12.0)
     rng = np.random.default_rng(seed)
-    return realisation_for_densities(rng, sig6, rho_mi, rho_si, n_loops, nodes_per_loop, r_min, r_max,
-                                     stratified=True)
+    net = realisation_for_densities(rng, sig6, rho_mi, rho_si, n_loops, nodes_per_loop, r_min, r_max,
+                                    stratified=True)
+    if sessile_case == 1:
+        return lomer_cottrell_sessiles(net, np.random.default_rng([seed, 1]))
+    if sessile_case != 2:
+        raise ValueError("sessile_case must be 1 or 2")
+    return net
+
+
+def lomer_cottrell_sessiles(net, rng):
+    """Case 1 of Sec. 3.2: every sessile loop (all its nodes pinned) keeps
+    its plane, line and |b| and takes a Burgers vector along one of the three
+    <110> directions that do not lie in its plane (b . n = +-(2/sqrt 6)|b|),
+    drawn uniformly, with a random sign; mobile loops are unchanged."""
+    cands = np.array([[0, 1, -1], [1, 0, -1], [1, -1, 0], [0, 1, 1], [1, 0, 1], [1, 1, 0]], float) / math.sqrt(2.0)
+    out = net.copy()
+    bv = out.burgers.copy()
+    for k in range(out.n_loops):
+        a, b = out.loop_off[k], out.loop_off[k + 1]
+        if not np.all(out.pinned[a:b]):
+            continue
+        off_plane = cands[np.abs(cands @ out.normal[k]) > 0.5]
+        d = off_plane[rng.integers(off_plane.shape[0])] * rng.choice(np.array([-1.0, 1.0]))
+        bv[k] = np.linalg.norm(bv[k]) * d
+    out.burgers = bv
+    return out
 
 
 # --------------------------------------------------------------------------

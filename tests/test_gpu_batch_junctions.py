@@ -4,9 +4,10 @@ junction burst run on every realisation alone.
 
 Three realisations of the paper's microstructure recipe (Sec. 3.2.1) of
 different sizes and applied stresses (16, 20 and 24 loops of 32 nodes, each
-with mobile and sessile loops), capture radius 20 nm, maximum break time 50
-DD steps, FP64 pair kernel, 100 steps (the batch runs them as 50 replays of
-its two-step graph).  Realisation r draws its break fractions from the
+with mobile and sessile loops; the 16-loop one with Lomer-Cottrell-type
+sessiles, Case 1 of Sec. 3.2, the others with Case 2), capture radius 20 nm,
+maximum break time 50 DD steps, FP64 pair kernel, 100 steps (the batch runs
+them as 50 replays of its two-step graph).  Realisation r draws its break fractions from the
 stream of seed ^ (r * 0x9E3779B97F4A7C15), so the oracle runs it with that
 seed.  Two stuck rules: never, and always while a junction is held (every
 realisation then jumps its own clock to each of its breaks).  Each case is
@@ -24,7 +25,7 @@ from paper_2005_02498_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 MAT = W.Material().as_tuple()
 STEPS, DT, RC, AMAX, SEED = 100, 5e-13, 2e-8, 2.5e-11, 5
-CASES = [(12, 20, 200e6), (13, 16, 180e6), (14, 24, 220e6)]  # (seed, loops, uniaxial stress)
+CASES = [(12, 20, 200e6, 2), (13, 16, 180e6, 1), (14, 24, 220e6, 2)]  # (seed, loops, uniaxial stress, sessile case)
 MASK = (1 << 64) - 1
 
 
@@ -33,7 +34,8 @@ def _seed(r):
 
 
 def _nets():
-    return [W.junction_microstructure(s, W.uniaxial_stress(sg), 1e13, 3e13, n_loops=nl) for s, nl, sg in CASES]
+    return [W.junction_microstructure(s, W.uniaxial_stress(sg), 1e13, 3e13, n_loops=nl, sessile_case=c)
+            for s, nl, sg, c in CASES]
 
 
 def _relmax(a, b):

@@ -2,9 +2,10 @@
 (ptadd_set_junctions, Sec. 2.2) with the oracle's junction burst, on the
 paper's microstructure recipe (Sec. 3.2.1): 20 loops of 32 nodes (4 mobile,
 16 sessile), 200 MPa [001], capture radius 20 nm, maximum break time 50 DD
-steps, FP64 pair kernel.  Two stuck rules: never (junctions form and break
-on the clock) and always while a junction is held (the clock jumps to every
-break).  The case is checked to be well conditioned first: the oracle's
+steps, FP64 pair kernel, with the sessile loops of both of the paper's cases
+(their Burgers vectors in their planes, or out of them as in Lomer-Cottrell
+locks).  Two stuck rules: never (junctions form and break on the clock) and
+always while a junction is held (the clock jumps to every break).  The case is checked to be well conditioned first: the oracle's
 junction decisions do not change when the start positions move by 1e-10
 relative, far more than the GPU and the oracle differ by."""
 
@@ -20,17 +21,18 @@ MAT = W.Material().as_tuple()
 STEPS, DT, RC, AMAX, SEED = 100, 5e-13, 2e-8, 2.5e-11, 5
 
 
-def _net():
-    return W.junction_microstructure(12, W.uniaxial_stress(200e6), 1e13, 3e13, n_loops=20)
+def _net(case=2):
+    return W.junction_microstructure(12, W.uniaxial_stress(200e6), 1e13, 3e13, n_loops=20, sessile_case=case)
 
 
 def _relmax(a, b):
     return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / np.max(np.abs(b)))
 
 
+@pytest.mark.parametrize("case", [2, 1])
 @pytest.mark.parametrize("stuck", [0.0, 1.0])
-def test_junction_burst_matches_oracle(stuck):
-    net = _net()
+def test_junction_burst_matches_oracle(stuck, case):
+    net = _net(case)
     ref = O.burst_junctions(MAT, net, STEPS, DT, RC, AMAX, stuck, SEED)
     pert = net.copy()
     pert.xyz = net.xyz * (1 + 1e-10 * np.random.default_rng(0).uniform(-1, 1, net.xyz.shape))

@@ -3,6 +3,7 @@
 import math
 
 import numpy as np
+import pytest
 
 from paper_2005_02498_gb300 import workloads as W
 
@@ -273,3 +274,29 @@ def test_native_system_densities_closed_form_and_features():
         raise AssertionError("a loop off the FCC systems must be rejected")
     except ptadd.PtaddError:
         pass
+
+
+def test_junction_microstructure_sessile_cases():
+    """Sec. 3.2's two cases share the geometry of a seed: Case 2 sessile
+    loops have b in their planes, Case 1 (Lomer-Cottrell-type locks) along a
+    <110> direction out of it, b . n = +-(2/sqrt 6)|b|, with |b| and the
+    mobile loops unchanged."""
+    sig = W.uniaxial_stress(100e6)
+    c2 = W.junction_microstructure(5, sig, 1e13, 2e14, n_loops=40, sessile_case=2)
+    c1 = W.junction_microstructure(5, sig, 1e13, 2e14, n_loops=40, sessile_case=1)
+    for k in ("xyz", "loop_off", "normal", "pinned"):
+        assert np.array_equal(getattr(c1, k), getattr(c2, k))
+    assert c1.volume == c2.volume
+    ses = np.array([bool(np.all(c2.pinned[a:b])) for a, b in zip(c2.loop_off[:-1], c2.loop_off[1:])])
+    assert 0 < ses.sum() < ses.size
+    mag2 = np.linalg.norm(c2.burgers, axis=1)
+    bh2 = c2.burgers / mag2[:, None]
+    assert np.all(np.abs(np.sum(bh2 * c2.normal, axis=1)) < 1e-12)  # every loop: b in its plane
+    assert np.array_equal(c1.burgers[~ses], c2.burgers[~ses])
+    assert np.allclose(np.linalg.norm(c1.burgers, axis=1), mag2, rtol=1e-14)
+    bh1 = c1.burgers[ses] / mag2[ses, None]
+    assert np.allclose(np.abs(np.sum(bh1 * c1.normal[ses], axis=1)), 2.0 / np.sqrt(6.0), rtol=1e-12)
+    # along a <110> direction: two components +-1/sqrt 2, one zero
+    assert np.allclose(np.sort(np.abs(bh1), axis=1), [0.0, 1 / np.sqrt(2.0), 1 / np.sqrt(2.0)], atol=1e-12)
+    with pytest.raises(ValueError):
+        W.junction_microstructure(5, sig, 1e13, 2e14, n_loops=40, sessile_case=3)
