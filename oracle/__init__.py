@@ -63,9 +63,10 @@ def _load():
         lib.orc_velocities.argtypes = [_D, ctypes.c_int64, _D, ctypes.c_int64, _I64, _D, _U8, _D, _D]
         lib.orc_lp_rho.argtypes = [ctypes.c_int64, _D, ctypes.c_int64, _I64, _D, _D,
                                    ctypes.c_double, _D, _D]
+        lib.orc_velocities_consistent.argtypes = [_D, ctypes.c_int64, _D, ctypes.c_int64, _I64, _D, _U8, _D, _D]
         lib.orc_burst.argtypes = [_D, ctypes.c_int64, _D, ctypes.c_int64, _I64, _D, _D, _U8,
                                   ctypes.c_double, _D, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
-                                  _D, _D, _D, _D, _D, ctypes.c_double, _D]
+                                  _D, _D, _D, _D, _D, ctypes.c_double, _D, ctypes.c_int]
         lib.orc_polar_velocity.argtypes = [ctypes.c_int64, _D, ctypes.c_int64, _I64, _D, ctypes.c_double,
                                            ctypes.c_double, _D]
         lib.orc_burst.restype = ctypes.c_int
@@ -207,7 +208,8 @@ def nodal_forces_subset(mat, net, sel, interactions=True, xyz=None):
     return F
 
 
-def velocities(mat, net, F, xyz=None):
+def velocities(mat, net, F, xyz=None, consistent=False):
+    """Glide mobility of Eq. 2.1: lumped (default) or with the consistent mass matrix."""
     lib = _load()
     m, mp = _mat(mat)
     x, px = _d(net.xyz if xyz is None else xyz)
@@ -216,7 +218,8 @@ def velocities(mat, net, F, xyz=None):
     pin, ppin = _u8(net.pinned)
     f, pf = _d(F)
     v = np.zeros((net.n_nodes, 3))
-    lib.orc_velocities(mp, net.n_nodes, px, net.n_loops, poff, pn, ppin, pf, v.ctypes.data_as(_D))
+    fn = lib.orc_velocities_consistent if consistent else lib.orc_velocities
+    fn(mp, net.n_nodes, px, net.n_loops, poff, pn, ppin, pf, v.ctypes.data_as(_D))
     return v
 
 
@@ -245,8 +248,9 @@ def polar_velocity(net, v, core_area, xyz=None):
     return V
 
 
-def burst(mat, net, n_steps, dt, interactions=True, trace=False, core_area=None):
-    """Run n_steps Euler steps; returns dict(xyz, Lp_avg (3x3), rho_avg[, Lp_trace, rho_trace][, V_avg])."""
+def burst(mat, net, n_steps, dt, interactions=True, trace=False, core_area=None, consistent_mass=False):
+    """Run n_steps Euler steps; returns dict(xyz, Lp_avg (3x3), rho_avg[, Lp_trace, rho_trace][, V_avg]).
+    consistent_mass: the consistent mobility of Eq. 2.1 instead of the lumped one."""
     lib = _load()
     m, mp = _mat(mat)
     x, px = _d(net.xyz)
@@ -266,7 +270,8 @@ def burst(mat, net, n_steps, dt, interactions=True, trace=False, core_area=None)
                        Lp.ctypes.data_as(_D), ctypes.byref(rho),
                        tL.ctypes.data_as(_D) if trace else None,
                        tr.ctypes.data_as(_D) if trace else None,
-                       float(core_area or 0.0), V.ctypes.data_as(_D) if core_area is not None else None)
+                       float(core_area or 0.0), V.ctypes.data_as(_D) if core_area is not None else None,
+                       int(bool(consistent_mass)))
     out = dict(xyz=xo, Lp_avg=Lp.reshape(3, 3), rho_avg=rho.value, status=rc)
     if core_area is not None:
         out["V_avg"] = V

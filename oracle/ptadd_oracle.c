@@ -17,8 +17,9 @@
  *      nonsingular form replaces |R| by R_a = sqrt(R.R + a^2) (core width a).
  *   2. Peach-Koehler force per length f = (sigma b) x t (Sec. 2.1).
  *   3. Nodal forces with linear shape functions, 4-point Gauss-Legendre.
- *   4. Glide mobility, lumped form of the Galerkin problem Eq. 2.1, the
- *      no-climb multiplier read as projection onto the loop's glide plane.
+ *   4. Glide mobility: the Galerkin problem Eq. 2.1 in its lumped form (the
+ *      default) or with its consistent mass matrix, the no-climb multiplier
+ *      read as projection onto the loop's glide plane.
  *   5. Explicit Euler x_p(t + dt) = x_p(t) + w_p dt (Sec. 2.1).
  *   6. The running time average R^Lambda of Eq. 2.5 for Lambda = Lp (the
  *      volume-averaged segment plastic distortion rate of Sec. 2.2) and
@@ -430,6 +431,82 @@ void orc_velocities(const double mat[5], int64_t n_nodes, const double* xyz,
     }
 }
 
+/* Solve A x = rhs (m x m, row-major, 3 right-hand sides as rows of rhs[m][3])
+ * by Gaussian elimination with partial pivoting; A and rhs are overwritten. */
+static void solve_dense3(int64_t m, double* A, double* rhs)
+{
+    for (int64_t c = 0; c < m; ++c) {
+        int64_t piv = c;
+        for (int64_t r = c + 1; r < m; ++r)
+            if (fabs(A[r * m + c]) > fabs(A[piv * m + c])) piv = r;
+        if (piv != c) {
+            for (int64_t k = 0; k < m; ++k) {
+                const double t = A[c * m + k];
+                A[c * m + k] = A[piv * m + k];
+                A[piv * m + k] = t;
+            }
+            for (int e = 0; e < 3; ++e) {
+                const double t = rhs[3 * c + e];
+                rhs[3 * c + e] = rhs[3 * piv + e];
+                rhs[3 * piv + e] = t;
+            }
+        }
+        for (int64_t r = c + 1; r < m; ++r) {
+            const double f = A[r * m + c] / A[c * m + c];
+            if (f == 0.0) continue;
+            for (int64_t k = c; k < m; ++k) A[r * m + k] -= f * A[c * m + k];
+            for (int e = 0; e < 3; ++e) rhs[3 * r + e] -= f * rhs[3 * c + e];
+        }
+    }
+    for (int64_t r = m - 1; r >= 0; --r) {
+        for (int e = 0; e < 3; ++e) {
+            double s = rhs[3 * r + e];
+            for (int64_t k = r + 1; k < m; ++k) s -= A[r * m + k] * rhs[3 * k + e];
+            rhs[3 * r + e] = s / A[r * m + r];
+        }
+    }
+}
+
+void orc_velocities_consistent(const double mat[5], int64_t n_nodes, const double* xyz,
+                               int64_t n_loops, const int64_t* loop_off, const double* normal,
+                               const uint8_t* pinned, const double* F, double* v_out)
+{
+    const double B = mat[4];
+    for (int64_t k = 0; k < n_loops; ++k) {
+        const int64_t b = loop_off[k], e = loop_off[k + 1], m = e - b;
+        const double* n = normal + 3 * k;
+        double* A = (double*)calloc((size_t)(m * m), sizeof(double));
+        double* r = (double*)malloc(sizeof(double) * (size_t)(3 * m));
+        /* assembly: int N_a N_b over segment a -> a+1 of length L gives L/3 on
+         * its two diagonal entries and L/6 between them */
+        for (int64_t i = 0; i < m; ++i) {
+            const int64_t j = (i + 1 < m) ? i + 1 : 0;
+            double d[3];
+            for (int c = 0; c < 3; ++c) d[c] = xyz[3 * (b + j) + c] - xyz[3 * (b + i) + c];
+            const double L = sqrt(dot3(d, d));
+            A[i * m + i] += B * L / 3.0;
+            A[j * m + j] += B * L / 3.0;
+            A[i * m + j] += B * L / 6.0;
+            A[j * m + i] += B * L / 6.0;
+        }
+        for (int64_t i = 0; i < m; ++i) {
+            const double* Fa = F + 3 * (b + i);
+            const double nF = dot3(n, Fa);
+            const int held = (pinned && pinned[b + i]) || !(A[i * m + i] > 0.0);
+            for (int c = 0; c < 3; ++c) r[3 * i + c] = held ? 0.0 : Fa[c] - n[c] * nF;
+            if (held) { /* Dirichlet row: w_i = 0 */
+                for (int64_t q = 0; q < m; ++q) A[i * m + q] = 0.0;
+                A[i * m + i] = 1.0;
+            }
+        }
+        solve_dense3(m, A, r);
+        memcpy(v_out + 3 * b, r, sizeof(double) * (size_t)(3 * m));
+        free(A);
+        free(r);
+    }
+    (void)n_nodes;
+}
+
 void orc_lp_rho(int64_t n_nodes, const double* xyz, int64_t n_loops,
                 const int64_t* loop_off, const double* burgers, const double* v,
                 double volume, double Lp[9], double* rho)
@@ -480,7 +557,8 @@ int orc_burst(const double mat[5], int64_t n_nodes, const double* xyz,
               const double* normal, const uint8_t* pinned, double volume,
               const double sig_app[6], int interactions, int64_t n_steps, double dt,
               double* xyz_out, double Lp_avg[9], double* rho_avg,
-              double* Lp_trace, double* rho_trace, double core_area, double* V_avg)
+              double* Lp_trace, double* rho_trace, double core_area, double* V_avg,
+              int consistent_mass)
 {
     const size_t n3 = (size_t)(3 * (n_nodes > 0 ? n_nodes : 1));
     double* x = (double*)malloc(sizeof(double) * n3);
@@ -492,7 +570,10 @@ int orc_burst(const double mat[5], int64_t n_nodes, const double* xyz,
     for (int64_t s = 0; s < n_steps; ++s) {
         orc_nodal_forces(mat, n_nodes, x, n_loops, loop_off, burgers, pinned, sig_app,
                          interactions, 1, F);
-        orc_velocities(mat, n_nodes, x, n_loops, loop_off, normal, pinned, F, v);
+        if (consistent_mass)
+            orc_velocities_consistent(mat, n_nodes, x, n_loops, loop_off, normal, pinned, F, v);
+        else
+            orc_velocities(mat, n_nodes, x, n_loops, loop_off, normal, pinned, F, v);
         double Lp[9], rho;
         orc_lp_rho(n_nodes, x, n_loops, loop_off, burgers, v, volume, Lp, &rho);
         for (int m = 0; m < 9; ++m) S_Lp[m] += Lp[m] * dt;

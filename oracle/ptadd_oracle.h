@@ -77,6 +77,17 @@ void orc_velocities(const double mat[5], int64_t n_nodes, const double* xyz,
                     int64_t n_loops, const int64_t* loop_off, const double* normal,
                     const uint8_t* pinned, const double* F, double* v_out);
 
+/* Consistent (Galerkin) glide mobility of Eq. 2.1: with linear shape
+ * functions N_a the weak form gives, per loop, sum_b B M_ab w_b = (I - n n) F_a
+ * with the mass matrix M_ab = int N_a N_b dl (a ring: M_aa = (L_prev + L_next)/3,
+ * M_a,a+-1 = L/6 of the segment between them) and w_a = 0 at pinned nodes
+ * (Dirichlet rows); solved per loop and component by Gaussian elimination with
+ * partial pivoting.  A free node whose two segments have zero length is held
+ * at rest, as in the lumped form.  The lumped form is its row-sum diagonal. */
+void orc_velocities_consistent(const double mat[5], int64_t n_nodes, const double* xyz,
+                               int64_t n_loops, const int64_t* loop_off, const double* normal,
+                               const uint8_t* pinned, const double* F, double* v_out);
+
 /* State functions: Lp = (1/V) sum_s L_s b_s (x) (t_s x vbar_s) (row-major 3x3,
  * Sec. 2.2 / Eq. 2.9) and rho = (1/V) sum_s L_s (Sec. 2.4). */
 void orc_lp_rho(int64_t n_nodes, const double* xyz, int64_t n_loops,
@@ -96,14 +107,16 @@ void orc_polar_velocity(int64_t n_nodes, const double* xyz, int64_t n_loops,
  * running averages R^Lp and R^rho of Eq. 2.5 over the step-start states,
  * and, if V_avg is not NULL, R^V of the polar velocity (Eq. 2.11, core area
  * core_area).  xyz_out (may alias nothing) receives the final positions;
- * Lp_trace and rho_trace (or NULL) receive the per-step samples.  Returns 0,
+ * Lp_trace and rho_trace (or NULL) receive the per-step samples.
+ * consistent_mass: 0 the lumped mobility, 1 the consistent one.  Returns 0,
  * or -1 if a non-finite value appeared. */
 int orc_burst(const double mat[5], int64_t n_nodes, const double* xyz,
               int64_t n_loops, const int64_t* loop_off, const double* burgers,
               const double* normal, const uint8_t* pinned, double volume,
               const double sig_app[6], int interactions, int64_t n_steps, double dt,
               double* xyz_out, double Lp_avg[9], double* rho_avg,
-              double* Lp_trace, double* rho_trace, double core_area, double* V_avg);
+              double* Lp_trace, double* rho_trace, double core_area, double* V_avg,
+              int consistent_mass);
 
 /* ---- MLP (mlp_oracle.c): dims[0] -> ... -> dims[L], GELU on hidden layers,
  * linear output, parameters packed per layer as W (dims[l+1] x dims[l],

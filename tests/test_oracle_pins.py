@@ -530,3 +530,111 @@ def test_polar_velocity_of_a_half_pinned_polygon(sense):
     # a 1-step burst averages the step-start state: its R^V is this V
     one = O.burst(mat, net, 1, 1e-12, interactions=False, core_area=core)
     assert rel(one["V_avg"], V) < 1e-14
+
+
+# ------------------------------------------------- consistent mass mobility
+def _irregular_loop(n, rng, pinned_every=0):
+    """A planar loop of n nodes at uneven angles and radii, in the (111) glide plane."""
+    bh, nh = W.fcc_slip_systems()
+    m, nn = bh[0], nh[0]
+    e2 = np.cross(nn, m)
+    phi = np.sort(rng.uniform(0, 2 * math.pi, n))
+    rad = 300 * A * (1 + 0.3 * rng.uniform(-1, 1, n))
+    xyz = rad[:, None] * (np.cos(phi)[:, None] * m + np.sin(phi)[:, None] * e2)
+    pin = np.zeros(n, np.uint8)
+    if pinned_every:
+        pin[::pinned_every] = 1
+    return W.Network(xyz, np.array([0, n], np.int64), (BB * m)[None, :], nn[None, :], pin, 1e-18, np.zeros(6)), nn
+
+
+def _galerkin_load(net, g, B):
+    """F_a = B int N_a g dl for the piecewise-linear field g (nodal values),
+    integrated segment by segment with the 2-point Gauss rule (exact here,
+    the integrand being quadratic) -- independent of any mass matrix."""
+    x = net.xyz
+    n = x.shape[0]
+    F = np.zeros_like(g)
+    xi = np.array([0.5 - 0.5 / math.sqrt(3.0), 0.5 + 0.5 / math.sqrt(3.0)])
+    for i in range(n):
+        j = (i + 1) % n
+        L = np.linalg.norm(x[j] - x[i])
+        for q in xi:
+            gq = (1 - q) * g[i] + q * g[j]
+            F[i] += B * L * 0.5 * (1 - q) * gq
+            F[j] += B * L * 0.5 * q * gq
+    return F
+
+
+@pytest.mark.parametrize("pinned_every", [0, 5])
+def test_consistent_mobility_returns_a_piecewise_linear_velocity(pinned_every):
+    """Eq. 2.1's weak form with linear shape functions: when the nodal loads
+    are the Galerkin loads of a piecewise-linear in-plane velocity field g
+    (zero at pinned nodes), the consistent mobility returns g exactly and
+    the lumped one does not."""
+    rng = np.random.default_rng(41 + pinned_every)
+    net, nn = _irregular_loop(27, rng, pinned_every)
+    g = rng.normal(size=(27, 3))
+    g -= np.outer(g @ nn, nn)
+    g[net.pinned.astype(bool)] = 0.0
+    F = _galerkin_load(net, g, MAT[4])
+    v = O.velocities(MAT, net, F, consistent=True)
+    assert rel(v, g) < 1e-12
+    assert np.all(v[net.pinned.astype(bool)] == 0.0)
+    assert rel(O.velocities(MAT, net, F), g) > 1e-3
+
+
+def test_consistent_and_lumped_mobility_agree_under_a_uniform_load():
+    """A uniform load per length on a free loop: the Galerkin loads are
+    B g (L_prev + L_next)/2, and both mobilities return g at every node."""
+    rng = np.random.default_rng(44)
+    net, nn = _irregular_loop(31, rng)
+    g = np.cross(nn, [0.3, -0.2, 0.9])
+    g = np.tile(g, (31, 1))
+    F = _galerkin_load(net, g, MAT[4])
+    assert rel(O.velocities(MAT, net, F, consistent=True), g) < 1e-12
+    assert rel(O.velocities(MAT, net, F), g) < 1e-12
+
+
+def test_consistent_mobility_of_a_regular_polygon_in_uniform_shear():
+    """Regular N-gon under uniform resolved shear tau, no self stress: the
+    nodal forces are radial, tau |b| l cos(pi/N) r_a with l the side; the
+    consistent mass matrix maps a radial field of one speed w to
+    B w l (2 + cos(2 pi/N))/3 r_a, so every node moves radially at
+    tau |b| cos(pi/N) / (B (2 + cos(2 pi/N))/3) (the lumped speed
+    tau |b| cos(pi/N)/B over (2 + cos(2 pi/N))/3)."""
+    N, R, tau, Bd = 24, 500 * A, 30e6, 1e-4
+    mat = (MU, NU, BB, A, Bd)
+    bh, nh = W.fcc_slip_systems()
+    m, n = bh[5], nh[5]
+    e2 = np.cross(n, m)
+    net = _polygon(N, R, np.zeros(3), m, e2, BB * m)
+    net.sig_app = voigt(_shear_tensor(m, n, tau))
+    F = O.nodal_forces(mat, net, interactions=False)
+    v = O.velocities(mat, net, F, consistent=True)
+    rhat = net.xyz / R
+    speed = np.sum(v * rhat, axis=1)
+    w = tau * BB * math.cos(math.pi / N) / (Bd * (2 + math.cos(2 * math.pi / N)) / 3)
+    assert np.allclose(np.abs(speed), w, rtol=1e-12)
+    assert np.all(np.sign(speed) == np.sign(speed[0]))
+    assert np.max(np.abs(v - speed[:, None] * rhat)) <= 1e-12 * w  # radial
+    vl = O.velocities(mat, net, F)
+    assert np.allclose(np.abs(np.sum(vl * rhat, axis=1)), tau * BB * math.cos(math.pi / N) / Bd, rtol=1e-12)
+
+
+def test_consistent_mass_burst_steps_with_the_consistent_velocities():
+    """A loop in uniform shear, self stress off: one Euler step of the
+    burst with the consistent mobility moves every node by its Galerkin
+    velocity, and three steps keep the nodes in their glide plane."""
+    N, R, tau, Bd = 16, 400 * A, 20e6, 1e-4
+    mat = (MU, NU, BB, A, Bd)
+    bh, nh = W.fcc_slip_systems()
+    m, n = bh[1], nh[1]
+    net = _polygon(N, R, np.array([1.0, 2.0, -1.0]) * 1e-7, m, np.cross(n, m), BB * m)
+    net.sig_app = voigt(_shear_tensor(m, n, tau))
+    dt = 5e-13
+    out = O.burst(mat, net, 1, dt, interactions=False, consistent_mass=True)
+    F = O.nodal_forces(mat, net, interactions=False)
+    v = O.velocities(mat, net, F, consistent=True)
+    assert rel(out["xyz"], net.xyz + v * dt) < 1e-15
+    out3 = O.burst(mat, net, 3, dt, interactions=False, consistent_mass=True)
+    assert np.max(np.abs((out3["xyz"] - net.xyz) @ n)) <= 1e-12 * np.max(np.abs(out3["xyz"] - net.xyz))
