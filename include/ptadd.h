@@ -384,6 +384,19 @@ ptadd_status ptadd_dissipation_projection(const double T6[6], const double alpha
 ptadd_status ptadd_dissipation_projection_dev(int64_t n_points, const double* T6_dev, const double* alpha_dev,
                                               double* Lp_dev, double* V_dev, int* n_bad_dev, void* stream);
 
+/* Glide mobility of Eq. 2.1 (Sec. 2.1) for ptadd_advance on this context.
+ * consistent = 0 (the default): the lumped form, v_a = (I - n n) F_a / (B M_a)
+ * with M_a = (L_prev + L_next)/2.  consistent = 1: the consistent (Galerkin)
+ * form with the linear shape functions, per loop sum_b B M_ab v_b = (I - n n)
+ * F_a with M_aa = (L_prev + L_next)/3 and M_a,a+-1 = L/6 of the segment
+ * between them, v = 0 at pinned nodes (and at a free node whose two segments
+ * have zero length); n is the loop's glide normal.  The setting stays with
+ * the context across networks; the batch (ptadd_batch_*) and
+ * ptadd_forces_noalloc use the lumped form.  PTADD_ERR_ARG for another value;
+ * PTADD_ERR_STATE for consistent = 1 while junctions are on (they hold nodes
+ * at rest by the lumped form's rule). */
+ptadd_status ptadd_set_mobility(ptadd_ctx* ctx, int32_t consistent);
+
 /* Junctions and thermally activated breaking in the burst (Sec. 2.2).
  * Sessile segments are those whose two nodes are pinned.  In every step of
  * ptadd_advance, before the Euler update, each free node:
@@ -407,7 +420,7 @@ ptadd_status ptadd_dissipation_projection_dev(int64_t n_points, const double* T6
  * The state blob of ptadd_get_state carries the junction state while they
  * are on.  Single-realisation API (ptadd_batch_set_junctions below is the
  * batch's).  PTADD_ERR_ARG on negative or non-finite parameters;
- * PTADD_ERR_STATE without a network. */
+ * PTADD_ERR_STATE without a network or with the consistent mobility on. */
 typedef struct {
     double capture_radius;  /* m */
     double max_break_time;  /* a, s */

@@ -226,6 +226,160 @@ cudaError_t launch_node_velocity(const DevNetwork& net, int chunks, cudaStream_t
     return cudaGetLastError();
 }
 
+// ------------------------------------------------- consistent mobility
+// Eq. 2.1's weak form with linear shape functions N_a, per loop (internal
+// units, B = 1): sum_b M_ab v_b = P F_a with M_ab = int N_a N_b dl, i.e.
+// M_aa = (L_prev + L_next)/3 and M_a,a+1 = L/6 of the segment between them;
+// v = 0 at pinned nodes and at a free node whose two segments have zero
+// length (held, Dirichlet).  One thread per loop: each chain of free nodes
+// between held ones is a tridiagonal system (Thomas elimination); a loop with
+// no held node is cyclic (the Sherman-Morrison form of the elimination, with
+// the corner terms as a rank-one correction); a two-node loop is solved
+// directly.  The matrix is diagonally dominant (M_aa = 2 (M_a,a-1 +
+// M_a,a+1)), so no pivoting is needed.  scr: [5 n] per-node factors.
+__device__ __forceinline__ double seg_len(const double* __restrict__ pos, int64_t n, int64_t i, int64_t j)
+{
+    const double dx = pos[j] - pos[i], dy = pos[n + j] - pos[n + i], dz = pos[2 * n + j] - pos[2 * n + i];
+    return sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+__global__ void consistent_velocity_kernel(int64_t n_loops, const int64_t* __restrict__ loop_off,
+                                           const double* __restrict__ pos, int64_t n,
+                                           const double* __restrict__ force, const uint8_t* __restrict__ pinned,
+                                           const double* __restrict__ loop_n, double* __restrict__ vel,
+                                           double* __restrict__ scr)
+{
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n_loops) return;
+    const int64_t b = loop_off[k], m = loop_off[k + 1] - b;
+    const double nn[3] = {loop_n[3 * k], loop_n[3 * k + 1], loop_n[3 * k + 2]};
+    // ring helpers: node t of the loop (0 <= t < m) is global b + t
+    auto node = [&](int64_t t) { return b + (t % m + m) % m; };
+    auto Lseg = [&](int64_t t) { return seg_len(pos, n, node(t), node(t + 1)); };  // segment t -> t+1
+    auto held = [&](int64_t t) { return pinned[node(t)] != 0 || !(Lseg(t - 1) + Lseg(t) > 0.0); };
+    auto rhs = [&](int64_t t, double d[3]) {  // P F
+        const int64_t a = node(t);
+        const double F[3] = {force[a], force[n + a], force[2 * n + a]};
+        const double nF = nn[0] * F[0] + nn[1] * F[1] + nn[2] * F[2];
+        for (int c = 0; c < 3; ++c) d[c] = F[c] - nn[c] * nF;
+    };
+    auto put = [&](int64_t t, const double v[3]) {
+        const int64_t a = node(t);
+        vel[a] = v[0];
+        vel[n + a] = v[1];
+        vel[2 * n + a] = v[2];
+    };
+    double* cp = scr;          // c' of the elimination
+    double* dp = scr + n;      // d' (3 components)
+    double* zp = scr + 4 * n;  // d' of the rank-one correction
+    int64_t h = -1;
+    for (int64_t t = 0; t < m && h < 0; ++t)
+        if (held(t)) h = t;
+    if (h < 0 && m == 2) {
+        const double S = Lseg(0) + Lseg(1), p = S / 3.0, q = S / 6.0, det = p * p - q * q;
+        double d0[3], d1[3], v0[3], v1[3];
+        rhs(0, d0);
+        rhs(1, d1);
+        for (int c = 0; c < 3; ++c) {
+            v0[c] = (p * d0[c] - q * d1[c]) / det;
+            v1[c] = (p * d1[c] - q * d0[c]) / det;
+        }
+        put(0, v0);
+        put(1, v1);
+        return;
+    }
+    if (h < 0) {
+        // cyclic: rows a_t x_{t-1} + b_t x_t + c_t x_{t+1} = d_t; corners
+        // beta = a_0 (row 0, column m-1) and alpha = c_{m-1} (row m-1, column 0)
+        const double L0 = Lseg(0), Lm = Lseg(m - 1);
+        const double b0 = (Lm + L0) / 3.0, beta = Lm / 6.0, alpha = Lm / 6.0;
+        const double gam = -b0;
+        double Lprev = Lm;
+        for (int64_t t = 0; t < m; ++t) {
+            const double Lt = Lseg(t);
+            double bt = (Lprev + Lt) / 3.0;
+            if (t == 0) bt -= gam;
+            if (t == m - 1) bt -= alpha * beta / gam;
+            const double at = t > 0 ? Lprev / 6.0 : 0.0, ct = t < m - 1 ? Lt / 6.0 : 0.0;
+            const int64_t a = node(t), ap = node(t - 1);
+            const double den = t > 0 ? bt - at * cp[ap] : bt;
+            double d[3];
+            rhs(t, d);
+            const double u = t == 0 ? gam : (t == m - 1 ? alpha : 0.0);
+            cp[a] = ct / den;
+            for (int c = 0; c < 3; ++c) dp[c * n + a] = (d[c] - (t > 0 ? at * dp[c * n + ap] : 0.0)) / den;
+            zp[a] = (u - (t > 0 ? at * zp[ap] : 0.0)) / den;
+            Lprev = Lt;
+        }
+        for (int64_t t = m - 2; t >= 0; --t) {  // back substitution, in place
+            const int64_t a = node(t), an = node(t + 1);
+            for (int c = 0; c < 3; ++c) dp[c * n + a] -= cp[a] * dp[c * n + an];
+            zp[a] -= cp[a] * zp[an];
+        }
+        const int64_t a0 = node(0), am = node(m - 1);
+        const double den = 1.0 + zp[a0] + beta * zp[am] / gam;
+        double f[3];
+        for (int c = 0; c < 3; ++c) f[c] = (dp[c * n + a0] + beta * dp[c * n + am] / gam) / den;
+        for (int64_t t = 0; t < m; ++t) {
+            const int64_t a = node(t);
+            const double v[3] = {dp[a] - f[0] * zp[a], dp[n + a] - f[1] * zp[a], dp[2 * n + a] - f[2] * zp[a]};
+            put(t, v);
+        }
+        return;
+    }
+    // chains of free nodes between held ones, walking the ring from h
+    const double zero[3] = {0.0, 0.0, 0.0};
+    int64_t t = h;
+    for (int64_t done = 0; done < m;) {
+        if (held(t)) {
+            put(t, zero);
+            ++t;
+            ++done;
+            continue;
+        }
+        // a chain starts at t (its predecessor is held); forward elimination
+        int64_t r = 0;
+        double Lprev = Lseg(t - 1);
+        while (!held(t + r) && done + r < m) {
+            const double Lt = Lseg(t + r);
+            const double bt = (Lprev + Lt) / 3.0;
+            const double at = r > 0 ? Lprev / 6.0 : 0.0;
+            const bool last = held(t + r + 1) || done + r + 1 >= m;
+            const double ct = last ? 0.0 : Lt / 6.0;
+            const int64_t a = node(t + r), ap = node(t + r - 1);
+            const double den = r > 0 ? bt - at * cp[ap] : bt;
+            double d[3];
+            rhs(t + r, d);
+            cp[a] = ct / den;
+            for (int c = 0; c < 3; ++c) dp[c * n + a] = (d[c] - (r > 0 ? at * dp[c * n + ap] : 0.0)) / den;
+            Lprev = Lt;
+            ++r;
+        }
+        // back substitution
+        for (int64_t q = r - 1; q >= 0; --q) {
+            const int64_t a = node(t + q);
+            double v[3];
+            for (int c = 0; c < 3; ++c) {
+                v[c] = dp[c * n + a];
+                if (q < r - 1) v[c] -= cp[a] * dp[c * n + node(t + q + 1)];
+                dp[c * n + a] = v[c];
+            }
+            put(t + q, v);
+        }
+        t += r;
+        done += r;
+    }
+}
+
+cudaError_t launch_consistent_velocity(const DevNetwork& net, cudaStream_t st)
+{
+    if (net.n_loops == 0) return cudaSuccess;
+    consistent_velocity_kernel<<<(unsigned)((net.n_loops + 127) / 128), 128, 0, st>>>(
+        net.n_loops, net.loop_off, net.pos[net.cur], net.n_nodes, net.force, net.pinned, net.loop_n, net.vel,
+        net.cm_scratch);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ lp_euler
 constexpr int RED_TPB = 256;
 // per-segment sums of the step-start state: L b (x) (t x vbar) (9), L (1),

@@ -643,6 +643,10 @@ extern "C" ptadd_status ptadd_set_junctions(ptadd_ctx* ctx, const ptadd_junction
         set_error("ptadd_set_junctions: no network loaded");
         return PTADD_ERR_STATE;
     }
+    if (p && ctx->consistent_mass) {
+        set_error("ptadd_set_junctions: junctions need the lumped mobility (ptadd_set_mobility(ctx, 0))");
+        return PTADD_ERR_STATE;
+    }
     if (p && !(p->capture_radius >= 0.0 && isfinite(p->capture_radius) && p->max_break_time >= 0.0 &&
                isfinite(p->max_break_time) && p->stuck_disp >= 0.0 && isfinite(p->stuck_disp))) {
         set_error("ptadd_set_junctions: parameters must be non-negative and finite");

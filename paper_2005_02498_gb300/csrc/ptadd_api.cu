@@ -47,7 +47,7 @@ static void free_network(DevNetwork& n)
 {
     void* ptrs[] = {n.pos[0], n.pos[1], n.nxt,   n.prv,   n.loop_of, n.loop_b,  n.loop_n, n.pinned, n.tgt_burst,
                     n.tgt_all, n.src,    n.fpart, n.vel,   n.force,   n.partial, n.acc,    n.flag,   n.staging,
-                    n.src32,   n.near_count, n.k64};
+                    n.src32,   n.near_count, n.k64, n.loop_off, n.cm_scratch};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     n = DevNetwork{};
@@ -240,6 +240,8 @@ ptadd_status ptadd_set_network(ptadd_ctx* ctx, int64_t n_nodes, const double* xy
     ALLOC(net.src32, SRC32_STRIDE * n);
     ALLOC(net.near_count, 1);
     ALLOC(net.k64, 4);
+    ALLOC(net.loop_off, n_loops + 1);
+    ALLOC(net.cm_scratch, 5 * n);
 #undef ALLOC
     if (st != PTADD_OK) {
         free_network(net);
@@ -256,6 +258,7 @@ ptadd_status ptadd_set_network(ptadd_ctx* ctx, int64_t n_nodes, const double* xy
     PTADD_CUDA(cudaMemcpyAsync(net.loop_b, lb.data(), 3 * n_loops * sizeof(double), cudaMemcpyHostToDevice, s));
     PTADD_CUDA(cudaMemcpyAsync(net.loop_n, ln.data(), 3 * n_loops * sizeof(double), cudaMemcpyHostToDevice, s));
     PTADD_CUDA(cudaMemcpyAsync(net.pinned, pin.data(), n, cudaMemcpyHostToDevice, s));
+    PTADD_CUDA(cudaMemcpyAsync(net.loop_off, loop_off, (n_loops + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
     if (!tb.empty())
         PTADD_CUDA(cudaMemcpyAsync(net.tgt_burst, tb.data(), tb.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
     PTADD_CUDA(cudaMemcpyAsync(net.tgt_all, ta.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
@@ -361,6 +364,18 @@ static ptadd_status drain_events(ptadd_ctx* ctx)
     return PTADD_OK;
 }
 
+ptadd_status ptadd_set_mobility(ptadd_ctx* ctx, int32_t consistent)
+{
+    CHECK_CTX(ctx);
+    if (consistent != 0 && consistent != 1) return arg_error("ptadd_set_mobility: consistent must be 0 or 1");
+    if (consistent && ctx->junc) {
+        set_error("ptadd_set_mobility: the consistent mobility does not combine with junctions (switch them off first)");
+        return PTADD_ERR_STATE;
+    }
+    ctx->consistent_mass = consistent == 1;
+    return PTADD_OK;
+}
+
 ptadd_status ptadd_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, double Lp_avg[9], double* rho_avg)
 {
     CHECK_CTX(ctx);
@@ -378,6 +393,10 @@ ptadd_status ptadd_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, double Lp
     for (int64_t it = 0; it < n_steps; ++it) {
         ptadd_status st = eval_forces(ctx, net.tgt_burst, net.n_tgt_burst);
         if (st != PTADD_OK) return st;
+        if (ctx->consistent_mass) {
+            PTADD_CUDA(launch_consistent_velocity(net, s));
+            ctx->kernel_launches += 1;
+        }
         if (ctx->junc) {
             PTADD_CUDA(launch_junction_update(ctx, s));
             ctx->kernel_launches += 3;

@@ -82,6 +82,8 @@ struct DevNetwork {
                                    // (sum_s L vbar) dt (polar velocity)
     int* flag = nullptr;           // non-finite flag
     double* staging = nullptr;     // [3*n] AoS SI positions in / out
+    int64_t* loop_off = nullptr;   // [n_loops + 1] first node of each loop (consistent mobility)
+    double* cm_scratch = nullptr;  // [5*n] elimination factors of the consistent mobility
     double volume = 0;             // m^3
 };
 
@@ -99,6 +101,9 @@ cudaError_t launch_pair(const DevNetwork& net, const int32_t* tgt, int64_t n_tgt
                         int precision, const Consts& c, const double sig_hat[6], cudaStream_t st);
 // node stage: F = sum of parts, v = P F / M (0 if pinned); writes net.force / net.vel
 cudaError_t launch_node_velocity(const DevNetwork& net, int chunks, cudaStream_t st);
+// consistent mobility (Eq. 2.1 with its Galerkin mass matrix): M v = P F per
+// loop, v = 0 at pinned nodes; replaces net.vel from net.force
+cudaError_t launch_consistent_velocity(const DevNetwork& net, cudaStream_t st);
 // Lp/rho sample of the step-start state, Euler update into the other buffer,
 // and the fixed-order reduction into net.acc (weighted by dt_hat)
 cudaError_t launch_lp_euler(DevNetwork& net, double dt_hat, cudaStream_t st);
@@ -152,6 +157,7 @@ struct ptadd_ctx {
     int len_exp = 0;       // internal length unit l = 2^len_exp m
     double len_unit = 1.0; // l in metres
     ptadd_precision prec = PTADD_FP64;
+    bool consistent_mass = false;  // ptadd_set_mobility
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
     ptadd::DevNetwork net;

@@ -35,7 +35,7 @@ EXPORTS = ["ptadd_version", "ptadd_create", "ptadd_destroy", "ptadd_last_error",
            "ptadd_surrogate_fit", "ptadd_surrogate_predict", "ptadd_surrogate_predict_dev",
            "ptadd_closure_sweep", "ptadd_closure_realisation", "ptadd_dissipation_projection",
            "ptadd_dissipation_projection_dev",
-           "ptadd_block_average", "ptadd_block_stress_pair", "ptadd_set_junctions", "ptadd_get_junctions",
+           "ptadd_block_average", "ptadd_block_stress_pair", "ptadd_set_junctions", "ptadd_get_junctions", "ptadd_set_mobility",
            "ptadd_batch_set_junctions", "ptadd_batch_get_junctions", "ptadd_system_densities",
            "ptadd_surrogate_get_state", "ptadd_surrogate_set_state"]
 NOALLOC_MAX_SEGMENTS = 16384
@@ -203,6 +203,8 @@ def load(build_if_missing=True):
     lib.ptadd_set_junctions.restype = st
     lib.ptadd_get_junctions.argtypes = [_VP, ctypes.POINTER(JunctionInfo), _I32, _I32, _I32, _D]
     lib.ptadd_get_junctions.restype = st
+    lib.ptadd_set_mobility.argtypes = [_VP, ctypes.c_int32]
+    lib.ptadd_set_mobility.restype = st
     lib.ptadd_batch_set_junctions.argtypes = [_VP, ctypes.POINTER(JunctionParams)]
     lib.ptadd_batch_set_junctions.restype = st
     lib.ptadd_batch_get_junctions.argtypes = [_VP, ctypes.POINTER(JunctionInfo), _I32, _I32, _I32, _D]
@@ -501,6 +503,10 @@ class Context:
     def set_state(self, blob):
         buf = ctypes.create_string_buffer(blob, len(blob))
         _check(self._lib.ptadd_set_state(self._h, ctypes.cast(buf, _VP), len(blob)))
+
+    def set_mobility(self, consistent):
+        """ptadd_set_mobility: True for the consistent (Galerkin) mass matrix of Eq. 2.1."""
+        _check(self._lib.ptadd_set_mobility(self._h, int(bool(consistent))))
 
     # ---------------------------------------------------------- junctions
     def set_junctions(self, capture_radius=None, max_break_time=1e-3, stuck_disp=0.0, seed=0):
