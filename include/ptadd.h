@@ -384,16 +384,17 @@ ptadd_status ptadd_dissipation_projection(const double T6[6], const double alpha
 ptadd_status ptadd_dissipation_projection_dev(int64_t n_points, const double* T6_dev, const double* alpha_dev,
                                               double* Lp_dev, double* V_dev, int* n_bad_dev, void* stream);
 
-/* Glide mobility of Eq. 2.1 (Sec. 2.1) for ptadd_advance on this context.
+/* Glide mobility of Eq. 2.1 (Sec. 2.1) for ptadd_advance and
+ * ptadd_batch_advance on this context.
  * consistent = 0 (the default): the lumped form, v_a = (I - n n) F_a / (B M_a)
  * with M_a = (L_prev + L_next)/2.  consistent = 1: the consistent (Galerkin)
  * form with the linear shape functions, per loop sum_b B M_ab v_b = (I - n n)
  * F_a with M_aa = (L_prev + L_next)/3 and M_a,a+-1 = L/6 of the segment
  * between them, v = 0 at pinned nodes (and at a free node whose two segments
  * have zero length); n is the loop's glide normal.  The setting stays with
- * the context across networks; the batch (ptadd_batch_*) and
- * ptadd_forces_noalloc use the lumped form.  PTADD_ERR_ARG for another value;
- * PTADD_ERR_STATE for consistent = 1 while junctions are on (they hold nodes
+ * the context across networks and batches (ptadd_forces_noalloc computes
+ * forces only).  PTADD_ERR_ARG for another value; PTADD_ERR_STATE for
+ * consistent = 1 while junctions are on, single or batched (they hold nodes
  * at rest by the lumped form's rule). */
 ptadd_status ptadd_set_mobility(ptadd_ctx* ctx, int32_t consistent);
 

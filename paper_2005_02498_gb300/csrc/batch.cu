@@ -95,6 +95,10 @@ struct DevBatch {
     int graph_prec = -1;
     int graph_cur = -1;
     bool graph_junc = false;
+    bool graph_cons = false;
+    bool consistent = false;          // consistent mobility in this burst (the context's setting)
+    int64_t* d_loop_off = nullptr;    // [n_loops + 1] (consistent mobility)
+    double* cm_scratch = nullptr;     // [5 n] (consistent mobility)
     DevBatchJunctions* junc = nullptr;  // junctions (ptadd_batch_set_junctions), NULL: off
     double dt_s = 0.0;                  // the step of the current burst, s (the junction clock)
     double time_scale = 0.0;            // mu / B: internal time -> s
@@ -502,6 +506,11 @@ cudaError_t batch_step(DevBatch& B, int prec, const Consts& c, double dt_hat, cu
                                          B.d_node_off, B.d_fp_base, B.d_chunks, B.fpart, B.force, B.vel);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (B.consistent) {
+        e = launch_consistent_velocity_raw(B.n_loops, B.d_loop_off, B.pos[B.cur], B.n, B.force, B.pinned, B.loop_n,
+                                           B.vel, B.cm_scratch, s);
+        if (e != cudaSuccess) return e;
+    }
     if (B.junc) {
         e = launch_batch_junction_update(B.junc, B.pos[B.cur], B.src32, B.nxt, B.loop_of, B.real_of, B.d_node_off,
                                          B.pinned, B.vel, s);
@@ -527,6 +536,8 @@ void free_batch(DevBatch& B)
 {
     if (B.graph) cudaGraphExecDestroy(B.graph);
     batch_junctions_free(B.junc);
+    if (B.d_loop_off) cudaFree(B.d_loop_off);
+    if (B.cm_scratch) cudaFree(B.cm_scratch);
     void* ptrs[] = {B.pos[0],   B.pos[1],    B.nxt,       B.prv,        B.loop_of,  B.real_of, B.tgt,
                     B.loop_b,   B.loop_n,    B.pinned,    B.src,        B.src32,    B.fpart,   B.vel,
                     B.force,    B.partial,   B.acc,       B.d_node_off, B.d_fp_base, B.d_chunks, B.d_origin,
@@ -608,6 +619,8 @@ void tune_store(const std::string& file, const std::string& key, const BatchConf
 }
 
 }  // namespace
+
+bool batch_has_junctions(const ptadd_ctx* ctx) { return ctx && ctx->batch && ctx->batch->junc; }
 
 void batch_free(ptadd_ctx* ctx)
 {
@@ -788,6 +801,8 @@ ptadd_status ptadd_batch_set(ptadd_ctx* ctx, int32_t R, const int64_t* node_off,
     BALLOC(B.near_count, 1);
     BALLOC(B.staging, 3 * n);
     BALLOC(B.k64, 4);
+    BALLOC(B.d_loop_off, n_loops + 1);
+    BALLOC(B.cm_scratch, 5 * n);
 #undef BALLOC
     if (st != PTADD_OK) {
         free_batch(B);
@@ -808,6 +823,7 @@ ptadd_status ptadd_batch_set(ptadd_ctx* ctx, int32_t R, const int64_t* node_off,
     H2D(B.loop_n, ln.data(), 3 * n_loops);
     H2D(B.pinned, pin.data(), n);
     H2D(B.d_node_off, node_off, R + 1);
+    H2D(B.d_loop_off, loop_off, n_loops + 1);
     H2D(B.d_origin, origin.data(), 3 * R);
     H2D(B.d_sh, sh.data(), 6 * R);
     H2D(B.d_blk_real, blk_real.data(), B.nblk);
@@ -866,10 +882,12 @@ ptadd_status ptadd_batch_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, dou
     B.dt_s = dt;
     B.time_scale = ctx->mat.mu / ctx->mat.B;
     const bool junc = B.junc != nullptr;
-    const int per_step = junc ? 9 : 5;
+    B.consistent = ctx->consistent_mass;
+    const int per_step = (junc ? 9 : 5) + (B.consistent ? 1 : 0);
     int64_t left = n_steps;
     if (left >= 2) {
-        if (!B.graph || B.graph_dt != dt_hat || B.graph_prec != prec || B.graph_cur != B.cur || B.graph_junc != junc) {
+        if (!B.graph || B.graph_dt != dt_hat || B.graph_prec != prec || B.graph_cur != B.cur || B.graph_junc != junc ||
+            B.graph_cons != B.consistent) {
             if (B.graph) cudaGraphExecDestroy(B.graph);
             B.graph = nullptr;
             const int cur0 = B.cur;
@@ -896,6 +914,7 @@ ptadd_status ptadd_batch_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, dou
             B.graph_prec = prec;
             B.graph_cur = B.cur;
             B.graph_junc = junc;
+            B.graph_cons = B.consistent;
         }
         while (left >= 2) {
             PTADD_CUDA(cudaGraphLaunch(B.graph, s));
@@ -946,6 +965,10 @@ ptadd_status ptadd_batch_set_junctions(ptadd_ctx* ctx, const ptadd_junction_para
     if (p && !(p->capture_radius >= 0.0 && isfinite(p->capture_radius) && p->max_break_time >= 0.0 &&
                isfinite(p->max_break_time) && p->stuck_disp >= 0.0 && isfinite(p->stuck_disp)))
         return barg("ptadd_batch_set_junctions: parameters must be non-negative and finite");
+    if (p && ctx->consistent_mass) {
+        set_error("ptadd_batch_set_junctions: junctions need the lumped mobility (ptadd_set_mobility(ctx, 0))");
+        return PTADD_ERR_STATE;
+    }
     PTADD_CUDA(cudaSetDevice(ctx->device));
     DevBatch& B = *ctx->batch;
     PTADD_CUDA(cudaStreamSynchronize(ctx->own_stream));

@@ -371,13 +371,20 @@ __global__ void consistent_velocity_kernel(int64_t n_loops, const int64_t* __res
     }
 }
 
+cudaError_t launch_consistent_velocity_raw(int64_t n_loops, const int64_t* loop_off, const double* pos, int64_t n,
+                                           const double* force, const uint8_t* pinned, const double* loop_n,
+                                           double* vel, double* scr, cudaStream_t st)
+{
+    if (n_loops == 0) return cudaSuccess;
+    consistent_velocity_kernel<<<(unsigned)((n_loops + 127) / 128), 128, 0, st>>>(n_loops, loop_off, pos, n, force,
+                                                                                  pinned, loop_n, vel, scr);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_consistent_velocity(const DevNetwork& net, cudaStream_t st)
 {
-    if (net.n_loops == 0) return cudaSuccess;
-    consistent_velocity_kernel<<<(unsigned)((net.n_loops + 127) / 128), 128, 0, st>>>(
-        net.n_loops, net.loop_off, net.pos[net.cur], net.n_nodes, net.force, net.pinned, net.loop_n, net.vel,
-        net.cm_scratch);
-    return cudaGetLastError();
+    return launch_consistent_velocity_raw(net.n_loops, net.loop_off, net.pos[net.cur], net.n_nodes, net.force,
+                                          net.pinned, net.loop_n, net.vel, net.cm_scratch, st);
 }
 
 // ------------------------------------------------------------ lp_euler

@@ -368,7 +368,7 @@ ptadd_status ptadd_set_mobility(ptadd_ctx* ctx, int32_t consistent)
 {
     CHECK_CTX(ctx);
     if (consistent != 0 && consistent != 1) return arg_error("ptadd_set_mobility: consistent must be 0 or 1");
-    if (consistent && ctx->junc) {
+    if (consistent && (ctx->junc || batch_has_junctions(ctx))) {
         set_error("ptadd_set_mobility: the consistent mobility does not combine with junctions (switch them off first)");
         return PTADD_ERR_STATE;
     }

@@ -104,6 +104,11 @@ cudaError_t launch_node_velocity(const DevNetwork& net, int chunks, cudaStream_t
 // consistent mobility (Eq. 2.1 with its Galerkin mass matrix): M v = P F per
 // loop, v = 0 at pinned nodes; replaces net.vel from net.force
 cudaError_t launch_consistent_velocity(const DevNetwork& net, cudaStream_t st);
+// the same on raw arrays (loops [loop_off[k], loop_off[k+1]) of n nodes, SoA
+// positions, forces and velocities; scr: 5 n doubles), for the batch
+cudaError_t launch_consistent_velocity_raw(int64_t n_loops, const int64_t* loop_off, const double* pos, int64_t n,
+                                           const double* force, const uint8_t* pinned, const double* loop_n,
+                                           double* vel, double* scr, cudaStream_t st);
 // Lp/rho sample of the step-start state, Euler update into the other buffer,
 // and the fixed-order reduction into net.acc (weighted by dt_hat)
 cudaError_t launch_lp_euler(DevNetwork& net, double dt_hat, cudaStream_t st);
@@ -128,6 +133,7 @@ ptadd_status junction_state_set(ptadd_ctx* ctx, const char* src);
 
 struct DevBatch;
 void batch_free(ptadd_ctx* ctx);
+bool batch_has_junctions(const ptadd_ctx* ctx);
 // junctions of a batched ensemble (junctions.cu)
 struct DevBatchJunctions;
 void batch_junctions_free(DevBatchJunctions*& j);

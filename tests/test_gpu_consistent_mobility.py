@@ -4,8 +4,9 @@
 Networks: the 512-segment loop workload (free rings: the cyclic solve), the
 same with every seventh node pinned (chains between pinned nodes), and the
 paper's junction microstructure (fully pinned sessile loops beside free
-mobile ones).  Bursts of 40 steps at dt = 5e-13 s, where the trajectories
-are well conditioned; FP64 to the FP64 bars, mixed to the mixed ones.
+mobile ones), alone and as one batch of three.  Bursts of 40 steps at dt =
+5e-13 s, where the trajectories are well conditioned; FP64 to the FP64
+bars, mixed to the mixed ones.
 """
 
 import numpy as np
@@ -85,3 +86,28 @@ def test_set_mobility_arguments_and_junctions():
         Lp, rho = c.advance(5, DT)
         ref = O.burst(MAT, net, 5, DT)
         assert relmax(Lp, ref["Lp_avg"]) <= 1e-8
+
+
+@pytest.mark.parametrize("precision", [ptadd.PTADD_FP64, ptadd.PTADD_MIXED])
+def test_consistent_mobility_in_the_batch_matches_oracle(precision):
+    nets = list(_networks().values())
+    refs = [O.burst(MAT, nt, STEPS, DT, consistent_mass=True) for nt in nets]
+    batch = W.batch_from_networks(nets)
+    with ptadd.Context(MAT, precision, 0) as c:
+        c.set_mobility(True)
+        c.batch_set(batch)
+        Lp, rho = c.batch_advance(STEPS, DT)
+        x = c.batch_get_nodes()
+        with pytest.raises(ptadd.PtaddError) as e:
+            c.batch_set_junctions(2e-8, 2.5e-11, 0.0, 5)
+        assert e.value.status == 5
+    for r, (nt, ref) in enumerate(zip(nets, refs)):
+        a, b = batch.node_off[r], batch.node_off[r + 1]
+        if precision == ptadd.PTADD_FP64:
+            assert relmax(x[a:b], ref["xyz"]) <= 1e-9, r
+            assert relmax(x[a:b] - nt.xyz, ref["xyz"] - nt.xyz) <= 1e-7, r
+            assert relmax(Lp[r], ref["Lp_avg"]) <= 1e-8, r
+            assert abs(rho[r] / ref["rho_avg"] - 1) <= 1e-12, r
+        else:
+            assert relmax(x[a:b] - nt.xyz, ref["xyz"] - nt.xyz) <= 1e-4, r
+            assert relfro(Lp[r], ref["Lp_avg"]) <= 1e-2, r
