@@ -7,9 +7,9 @@ different sizes and applied stresses (16, 20 and 24 loops of 32 nodes, each
 with mobile and sessile loops; the 16-loop one with Lomer-Cottrell-type
 sessiles, Case 1 of Sec. 3.2, the others with Case 2), capture radius 20 nm,
 maximum break time 50 DD steps, FP64 pair kernel, 100 steps (the batch runs
-them as 50 replays of its two-step graph).  Realisation r draws its break fractions from the
-stream of seed ^ (r * 0x9E3779B97F4A7C15), so the oracle runs it with that
-seed.  Two stuck rules: never, and always while a junction is held (every
+them as 50 replays of its two-step graph).  Realisation r draws its break
+fractions from the stream of seed ^ (r * 0x9E3779B97F4A7C15), so the oracle
+runs it with that seed.  Two stuck rules: never, and always while a junction is held (every
 realisation then jumps its own clock to each of its breaks).  Each case is
 checked to be well conditioned first: the oracle's decisions do not change
 when the start positions move by 1e-10 relative.

@@ -159,3 +159,29 @@ def test_argument_errors_leave_context_usable():
             c.advance(1, -1.0)
         Lp, _ = c.advance(1, 1e-12)
         assert np.all(np.isfinite(Lp))
+
+
+@pytest.mark.parametrize("prec", [ptadd.PTADD_FP64, ptadd.PTADD_MIXED])
+def test_zero_length_segment_matches_oracle(prec):
+    """A degenerate case of the method: two coincident consecutive nodes make
+    a zero-length segment, whose field is zero (its line integral is empty);
+    the node next to it keeps the lumped mass of its other segment.  Forces
+    against the oracle, then a 10-step burst (the two nodes separate)."""
+    net = W.small_loop_network()
+    net.xyz[6] = net.xyz[5]
+    Fo = O.nodal_forces(MAT, net)
+    ref = O.burst(MAT, net, 10, 5e-13)
+    with ctx_for(net, prec) as c:
+        c.set_applied_stress(net.sig_app)
+        F = c.get_forces()
+        Lp, rho = c.advance(10, 5e-13)
+        x = c.get_nodes()
+    assert np.all(np.isfinite(F)) and np.all(np.isfinite(x))
+    if prec == ptadd.PTADD_FP64:
+        assert relmax(F, Fo) <= 1e-11
+        assert relmax(x - net.xyz, ref["xyz"] - net.xyz) <= 1e-8
+        assert relmax(Lp, ref["Lp_avg"]) <= 1e-9
+    else:
+        assert relmax(F, Fo) <= 1e-4
+        assert relmax(x - net.xyz, ref["xyz"] - net.xyz) <= 1e-4
+    assert abs(rho / ref["rho_avg"] - 1) <= 1e-6
