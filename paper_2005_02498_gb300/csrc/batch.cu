@@ -484,8 +484,8 @@ cudaError_t launch_batch_pair(const DevBatch& B, int prec, const Consts& c, cuda
     const float near2 = (float)((NEAR_FACTOR * NEAR_FACTOR + 1.0) * c.a2);
     const bool mixed = prec == (int)PTADD_MIXED;
     if (B.cfg.tpb == 64)
-        return mixed ? launch_batch_pair_t<64, 6, true>(B, c, near2, s) : launch_batch_pair_t<64, 8, false>(B, c, near2, s);
-    return mixed ? launch_batch_pair_t<128, 3, true>(B, c, near2, s) : launch_batch_pair_t<128, 4, false>(B, c, near2, s);
+        return mixed ? launch_batch_pair_t<64, 6, true>(B, c, near2, s) : launch_batch_pair_t<64, 6, false>(B, c, near2, s);
+    return mixed ? launch_batch_pair_t<128, 3, true>(B, c, near2, s) : launch_batch_pair_t<128, 3, false>(B, c, near2, s);
 }
 
 // One DD step of the whole batch on stream s (pos[cur] -> pos[1-cur]).
