@@ -52,15 +52,33 @@ __device__ __forceinline__ float rsqrt_approx(float x)
     asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// The seed's conversions on the integer pipe (the hardware FP64 <-> FP32
+// conversions run on the 1/64-rate FP64 pipe here): FP64 -> FP32 by
+// truncating the mantissa (the seed's own error is far larger), FP32 -> FP64
+// exactly, by moving the IEEE-754 fields.  The domain is that of the FP32
+// approximations with flush-to-zero, FP32's normal range, which holds the
+// seeds' arguments (squared distances plus a^2 and their products).
+__device__ __forceinline__ float d2f_seed(double x)
+{
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const int e = min(max((int)((hi >> 20) & 0x7FFu) - 896, 0), 255);
+    return __uint_as_float((hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+__device__ __forceinline__ double f2d_seed(float y)
+{
+    const unsigned u = __float_as_uint(y);
+    const unsigned hi = (u & 0x80000000u) | ((((u >> 23) & 0xFFu) + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
 __device__ __forceinline__ double rcp_nr(double x)
 {
-    const double y = (double)rcp_approx(__double2float_rn(x));
+    const double y = f2d_seed(rcp_approx(d2f_seed(x)));
     const double e = fma(-x, y, 1.0);
     return fma(y, fma(e, e, e), y);
 }
 __device__ __forceinline__ double rsqrt_nr(double x)
 {
-    const double y = (double)rsqrt_approx(__double2float_rn(x));
+    const double y = f2d_seed(rsqrt_approx(d2f_seed(x)));
     const double e = fma(-x * y, y, 1.0);
     return fma(y * e, fma(e, 0.375, 0.5), y);
 }
