@@ -598,14 +598,21 @@ ptadd_status ptadd_mlp_train(ptadd_ctx* ctx, int64_t n, const float* xn, const f
     const int64_t rows = batch;
     st = ensure_work(m, rows);
     if (st != PTADD_OK) return st;
-    float *dx = nullptr, *dy = nullptr;
+    float *dx = nullptr, *dy = nullptr, *dloss = nullptr;
     int32_t* didx = nullptr;
+    // per-minibatch loss partials of an epoch, kept on the device and read once
+    // per epoch (reading them per minibatch would stall the stream every time)
+    const int nb = (int)((rows + 255) / 256);
+    const int64_t nbatches = n / batch;
     if ((st = m_alloc(&dx, (size_t)n * NIN)) != PTADD_OK) return st;
-    if ((st = m_alloc(&dy, (size_t)n * NOUT)) != PTADD_OK || (st = m_alloc(&didx, (size_t)n)) != PTADD_OK) {
+    if ((st = m_alloc(&dy, (size_t)n * NOUT)) != PTADD_OK || (st = m_alloc(&didx, (size_t)n)) != PTADD_OK ||
+        (st = m_alloc(&dloss, (size_t)std::max<int64_t>(1, nbatches) * nb)) != PTADD_OK) {
         cudaFree(dx);
         cudaFree(dy);
+        cudaFree(didx);
         return st;
     }
+    std::vector<float> hloss((size_t)std::max<int64_t>(1, nbatches) * nb);
     std::vector<int32_t> perm(n);
     std::iota(perm.begin(), perm.end(), 0);
     uint64_t rs = seed;
@@ -626,21 +633,38 @@ ptadd_status ptadd_mlp_train(ptadd_ctx* ctx, int64_t n, const float* xn, const f
             if (e == cudaSuccess) e = backward(m, batch, rows, s, &launches);
             if (e == cudaSuccess) e = adam_all(m, lr, 0.9f, 0.999f, 1e-8f, s);
             launches += 2 + 8 + 4;
-            if (e == cudaSuccess && loss_per_epoch) {
-                float l = 0.0f;
-                st = read_loss(m, rows, s, &l);
-                ep_loss += l;
-            }
+            if (e == cudaSuccess && loss_per_epoch)
+                e = cudaMemcpyAsync(dloss + (size_t)nbatch * nb, m.loss_part, nb * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, s);
             ++nbatch;
         }
+        if (e == cudaSuccess && loss_per_epoch && nbatch)
+            e = cudaMemcpyAsync(hloss.data(), dloss, (size_t)nbatch * nb * sizeof(float), cudaMemcpyDeviceToHost, s);
         // a synchronisation per epoch keeps the host copy of perm safe to rewrite
         cudaError_t e2 = cudaStreamSynchronize(s);
         if (e == cudaSuccess) e = e2;
-        if (loss_per_epoch) loss_per_epoch[ep] = nbatch ? (float)(ep_loss / nbatch) : 0.0f;
+        if (e == cudaSuccess && loss_per_epoch) {
+            // each minibatch's loss as its partials summed in order, then the epoch mean
+            for (int b = 0; b < nbatch; ++b) {
+                double t = 0.0;
+                for (int q = 0; q < nb; ++q) t += hloss[(size_t)b * nb + q];
+                ep_loss += (float)t;
+            }
+            loss_per_epoch[ep] = nbatch ? (float)(ep_loss / nbatch) : 0.0f;
+        }
+        if (e == cudaSuccess) {  // a tensor-core wait that gave up ends the training at the epoch's end
+            int err = 0;
+            e = cudaMemcpy(&err, m.err, sizeof(int), cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess && err) {
+                set_error("a tensor-core wait gave up");
+                st = PTADD_ERR_TIMEOUT;
+            }
+        }
     }
     cudaFree(dx);
     cudaFree(dy);
     cudaFree(didx);
+    cudaFree(dloss);
     if (e != cudaSuccess) {
         set_error("surrogate training: %s", cudaGetErrorString(e));
         return PTADD_ERR_CUDA;
