@@ -200,7 +200,7 @@ def test_fused_inference_unaligned_input_takes_the_copy_path_and_agrees():
     staged with one bulk copy per tile: the kernel then stages them with 8-byte
     asynchronous copies.  Both paths feed the same arithmetic, so the outputs
     and trust-region flags agree bit for bit (2 000 rows: 16 tiles, the last
-    ragged)."""
+    ragged), and a call without a trust-region array gives the same outputs."""
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(31)
     n_fit, n = 2048, 2000
@@ -224,7 +224,16 @@ def test_fused_inference_unaligned_input_takes_the_copy_path_and_agrees():
             torch.cuda.synchronize()
             outs.append((lp6.cpu().numpy().copy(), reg.cpu().numpy().copy()))
         ref, ref_in = c.surrogate_predict(test)
+        # without a trust-region array: the same outputs
+        aligned.copy_(torch.from_numpy(test.reshape(-1)))
+        lp6 = torch.empty(n * 6, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        c.surrogate_predict_dev(n, aligned.data_ptr(), lp6.data_ptr(), None)
+        torch.cuda.synchronize()
+        no_region = lp6.cpu().numpy().copy()
+    assert np.array_equal(no_region, outs[0][0])
     assert np.all(np.isfinite(outs[0][0]))
     assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
     assert np.array_equal(outs[0][0].reshape(n, 6), ref) and np.array_equal(outs[0][1].astype(bool), ref_in)
     assert 0 < outs[0][1].sum() < n
+
