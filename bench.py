@@ -180,18 +180,24 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(precision):
-    """DRAM bytes per pair launch from a committed ncu capture, if the kernel
-    source is unchanged since it was taken."""
+def recorded_capture(precision):
+    """The committed ncu figures of the pair kernel (DRAM bytes per launch,
+    executed FLOPs per evaluation), if the kernel source is unchanged since
+    they were taken; else an empty dict."""
     path = os.path.join(ROOT, "profiles", "pair_kernel_traffic.json")
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
-        return None
+        return {}
     e = rec.get(precision)
     if not e or e.get("kernel_src_sha") != kernel_source_sha():
-        return None
-    return e.get("dram_bytes_per_launch")
+        return {}
+    return e
+
+
+def recorded_traffic(precision):
+    """DRAM bytes per pair launch from a committed ncu capture, or None."""
+    return recorded_capture(precision).get("dram_bytes_per_launch")
 
 
 def cpu_sample(net, seconds, mat):
@@ -509,7 +515,13 @@ def run_ours(args):
     lanes = 2 if args.precision == "fp64" else 128  # FMA lanes per SM per clock
     peak = sms * lanes * 2 * max_mhz * 1e6
     if fp64_cmp:
-        fp64_cmp["pair_kernel_frac_of_fp64_peak"] = fp64_cmp["pair_kernel_tflops"] * 1e12 / (sms * 2 * 2 * max_mhz * 1e6)
+        peak64 = sms * 2 * 2 * max_mhz * 1e6
+        fp64_cmp["pair_kernel_frac_of_fp64_peak"] = fp64_cmp["pair_kernel_tflops"] * 1e12 / peak64
+        x64 = recorded_capture("fp64").get("executed_fp64_flops_per_pair")
+        if x64 is not None:
+            t64 = fp64_cmp["pair_kernel_tflops"] * x64 / FLOPS_PER_PAIR
+            fp64_cmp["executed"] = {"flops_per_pair": x64, "achieved": t64, "frac": t64 * 1e12 / peak64,
+                                    "unit": "TFLOP/s"}
     roof = {"kernel": "pair_fp64_kernel" if args.precision == "fp64" else "pair_mixed_kernel",
             "bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": recorded_traffic(args.precision),
@@ -520,6 +532,17 @@ def run_ours(args):
                            % ("FP64" if args.precision == "fp64" else "FP32", sms, lanes, max_mhz),
             "measured_fma_chain_tflops": {"fp64": meas_fp64 / 1e12, "fp32": meas_fp32 / 1e12,
                                           "fp32_packed_pairs": meas_fp32x2 / 1e12}}
+    # the same launch in executed operations (ncu instruction counters of the
+    # recorded capture): the mixed kernel's coefficient form needs fewer than
+    # the formulation that defines the unit
+    cap = recorded_capture(args.precision)
+    xkey = "executed_fp64_flops_per_pair" if args.precision == "fp64" else "executed_fp32_flops_per_pair"
+    if cap.get(xkey) is not None and avg_ms > 0:
+        executed = cap[xkey] * evals_per_launch / (avg_ms * 1e-3)
+        roof["executed"] = {"flops_per_pair": cap[xkey], "achieved": executed / 1e12, "frac": executed / peak,
+                            "unit": "TFLOP/s", "counted_on": cap.get("executed_counted_on")}
+    else:
+        roof["executed"] = None
 
     out = {"metric": "segment-pair evals/s", "value": value, "unit": "pair-evals/s", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
