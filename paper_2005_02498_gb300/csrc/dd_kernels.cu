@@ -80,7 +80,7 @@ cudaError_t launch_seg_prep(const DevNetwork& net, cudaStream_t st)
 constexpr int PAIR_TPB = 128;
 constexpr int PAIR_TILE = 128;
 constexpr int MIX_TPB = 128;
-constexpr int MIX_TILE = 128;
+constexpr int MIX_TILE = 192;  // sources per staged tile: 3 blocks of 66.5 KB fit one SM's shared memory
 constexpr int MIX_MINB = 3;  // resident blocks per SM the register budget is sized for
 
 __global__ void __launch_bounds__(PAIR_TPB) pair_fp64_kernel(TileArgs base, int64_t n_tgt, int64_t chunk_len,

@@ -95,10 +95,11 @@ __device__ __forceinline__ void pair_tile_fp64(const TileArgs& a, const Consts& 
         xq[qp][1] = __dadd_rn(ya, __dmul_rn(xi, Dy));
         xq[qp][2] = __dadd_rn(za, __dmul_rn(xi, Dz));
     }
-    double acc[4][3];  // (sigma b') / c2 at the Gauss points
+    double acc[4][3];  // (sigma b') / c2 at the Gauss points, without the term along b'
+    double accb[4];    // coefficient sums of the term along b'
 #pragma unroll
-    for (int qp = 0; qp < 4; ++qp) acc[qp][0] = acc[qp][1] = acc[qp][2] = 0.0;
-    const double nr = -c.c1 / c.c2;
+    for (int qp = 0; qp < 4; ++qp) acc[qp][0] = acc[qp][1] = acc[qp][2] = accb[qp] = 0.0;
+    const double nr = -c.c1 / c.c2, nra2 = nr * c.a2, kn = 1.0 - 2.0 * c.c1 / c.c2;
 
     for (int64_t j0 = a.js; j0 < a.je; j0 += TILE) {
         const int cnt = (int)min((int64_t)TILE, a.je - j0);
@@ -116,14 +117,24 @@ __device__ __forceinline__ void pair_tile_fp64(const TileArgs& a, const Consts& 
             const double q[3] = {r[12], r[13], r[14]};
             PairK k;
             pair_constants(t, q, bt, nr, k);
+            // per Gauss point the geometry, then a vote: where every pair of
+            // the warp is one-sided the straddling forms are not evaluated
+            // (the FP64 pipe is the bound, so the branches cost nothing there)
 #pragma unroll
-            for (int qp = 0; qp < 4; ++qp)
-                seg_sigma_b(xq[qp][0] - x1[0], xq[qp][1] - x1[1], xq[qp][2] - x1[2], t, L, b, q, bt, k, c.a2, nr,
-                            acc[qp]);
+            for (int qp = 0; qp < 4; ++qp) {
+                SegGeo G;
+                seg_geo(xq[qp][0] - x1[0], xq[qp][1] - x1[1], xq[qp][2] - x1[2], t, L, c.a2, G);
+                if (__all_sync(0xffffffffu, seg_one_side(G, L)))
+                    seg_sigma_b_geo<1>(G, t, L, b, q, bt, k, c.a2, nr, nra2, kn, acc[qp], accb[qp]);
+                else
+                    seg_sigma_b_geo<0>(G, t, L, b, q, bt, k, c.a2, nr, nra2, kn, acc[qp], accb[qp]);
+            }
         }
     }
 #pragma unroll
-    for (int qp = 0; qp < 4; ++qp) acc[qp][0] *= c.c2, acc[qp][1] *= c.c2, acc[qp][2] *= c.c2;
+    for (int qp = 0; qp < 4; ++qp)
+#pragma unroll
+        for (int e = 0; e < 3; ++e) acc[qp][e] = c.c2 * fma(accb[qp], bt[e], acc[qp][e]);
     if (active) tile_store(a, seg, Dx, Dy, Dz, bt, acc);
 }
 
@@ -133,8 +144,8 @@ __device__ __forceinline__ void pair_tile_fp64(const TileArgs& a, const Consts& 
 // FP32 resolution anywhere in the box); if the point lies within 10 a of the
 // source segment the pair is evaluated in FP64 from the FP64 records,
 // otherwise in FP32.  Per Gauss point the FP32 contributions are summed in
-// three levels: plainly over groups of SUM_GROUP sources, with Kahan
-// compensation over the groups of the work item's source range, and in FP64
+// three levels: plainly over the sources of each staged tile, with Kahan
+// compensation over the tiles of the work item's source range, and in FP64
 // over work items (where the FP64 near-field values also go); the FP64 sums
 // feed the PK force and the nodal assembly.
 //
@@ -162,8 +173,9 @@ __device__ __forceinline__ void kahan_add2(float2& s, float2& c, float2 v)
     c = sub2(sub2(t, s), y);
     s = t;
 }
-// sources summed plainly before a compensated add
-constexpr int SUM_GROUP = 32;
+// sources summed plainly before a compensated add: no fewer than a staged
+// tile holds, so each tile's sources form one plain group
+constexpr int SUM_GROUP = 256;
 // sources of one group handled per loop iteration (two independent chains)
 constexpr int MIX_UNROLL = 2;
 // keep a register value opaque, so the compiler holds it instead of
@@ -210,7 +222,7 @@ __device__ __forceinline__ void seg_geo2(const float2 R0[3], const Src2& S, floa
 //   (sigma b') / c2 = cRxb (Rp x b) + cq q + cRp Rp + ct t + cb b',
 // the formula of seg_sigma_b (FP64: c2 taken out, K_k = 3 J_k, (b x b').Rp
 // as b'.(Rp x b)) regrouped so that each coefficient costs few operations:
-//   B0 = a^2 K2 + J0 (= A0 - J0),  C1 = r A1 + J1,
+//   B0 = a^2 K2 + J0 (= A0 - J0),  C1 = r A1 + J1 = (r a^2) K3 + (1 + 2r) J1,
 //   cRxb = (r A0) t.b',  cq = C1 t.b' - J0 (Rp.b'),
 //   ct = (r A0) Rw + C1 q.b' + (q.Rp)(K4 t.b' - K3 (Rp.b')),
 //   cRp = (q.Rp)(K2 (Rp.b') - K3 t.b') - J0 q.b',  cb = (q.Rp) B0,
@@ -220,15 +232,28 @@ __device__ __forceinline__ void seg_geo2(const float2 R0[3], const Src2& S, floa
 // factors are finite, rho >= a > 0), so such a lane contributes exactly 0 and
 // the caller adds the terms unconditionally.  SAME = 1: every lane of the
 // warp has both ends of the source on one side of the foot of the
-// perpendicular (u1 u2 >= 0), so the straddling forms are not evaluated.
+// perpendicular (u1 u2 >= 0), so the straddling forms are not evaluated,
+// and the one-side integrals come from the single reciprocal
+// rr = 1 / ((p + m)(1 + pm)(1/rho1 + 1/rho2)) through Q = Li rr:
+//   J0 = Li / (p + m) = Q (1 + pm) isum,  J1 = Li / isum = Q (p + m)(1 + pm),
+//   K2 = J0 W = Q (isum Aw + (1 + pm) isum ssum),
+// with W = Aw / (1 + pm) + ssum and Aw = ssum - d^2 / (rho1^2 rho2^2)
+// = (u1^2 + u2^2 + d^2) / (rho1^2 rho2^2) (at least ssum / 2, so the
+// difference loses at most one bit).  Every coefficient is linear in
+// J0, J1, K2, so there they are formed without the factor Q, which the
+// caller applies to their sum (C.Q): the reciprocal's latency then overlaps
+// the whole coefficient arithmetic.  Straddling warps form the coefficients
+// in full (C.Q = 1).  kn = 1 + 2r.
 struct Coef2 {
     float2 cRxb, cq, cRp, ct, cb;
     float2 X[3];  // Rp x b
+    float2 Q;     // common factor of the five coefficients
 };
 
 template <int SAME>
 __device__ __forceinline__ void seg_coef2(const Geo2& G, const Src2& S, const float2 bt[3], const Pair2& P,
-                                          float2 a2, float2 nr, bool nearx, bool neary, Coef2& C)
+                                          float2 a2, float2 nr, float2 nra2, float2 kn, bool nearx, bool neary,
+                                          Coef2& C)
 {
     const float2 ny = G.ny, d2 = G.d2, u2 = G.u2, r1s = G.r1s, r2s = G.r2s;
     const float2 Rpx = G.Rp[0], Rpy = G.Rp[1], Rpz = G.Rp[2];
@@ -241,35 +266,40 @@ __device__ __forceinline__ void seg_coef2(const Geo2& G, const Src2& S, const fl
     const float2 S2 = fma2(p, p, fma2(m, m, pm));
     const float2 isum = add2(i1, i2);
     const float2 pps = add2(p, m), one_pm = add2(f2(1.0f), pm);
-    bool samex = true, samey = true;
-    if (!SAME) {
-        samex = (ny.x >= 0.0f) || (u2.x <= 0.0f);
-        samey = (ny.y >= 0.0f) || (u2.y <= 0.0f);
-    }
-    const float2 den = SAME ? mul2(pps, one_pm) : sel2(samex, samey, mul2(pps, one_pm), d2);
-    const float2 dis = mul2(den, isum);
-    const float2 rr = sel2(nearx, neary, f2(0.0f), make_float2(rcp_approx(dis.x), rcp_approx(dis.y)));
-    const float2 rden = mul2(rr, isum);
     const float2 Li = mul2(fma2(ny, S.L2, S.LL), i12);  // L (u1 + u2) / (rho1^2 rho2^2)
-    const float2 J1 = mul2(Li, mul2(rr, den));
-    const float2 K3 = mul2(J1, fma2(i1, i2, ssum));
-    const float2 g = mul2(Li, rden);
-    // one-side form of (3 - p^2 - pm - m^2)/d^2: (u1^2 + u2^2 + d^2)/(rho1^2 rho2^2 (1 + pm)) + 1/rho1^2 + 1/rho2^2
-    const float2 Wsame = fma2(mul2(mul2(fma2(ny, ny, r2s), i12), rden), pps, ssum);
-    float2 J0, Wt;
+    const float2 E3 = fma2(i1, i2, ssum);
+    float2 J0, J1, K2;
     if (SAME) {
-        J0 = mul2(g, one_pm);
-        Wt = Wsame;
+        const float2 T = mul2(one_pm, isum);
+        const float2 den = mul2(pps, one_pm);
+        const float2 dis = mul2(pps, T);
+        const float2 Aw = fma2(neg2(d2), i12, ssum);
+        const float2 Z = fma2(isum, Aw, mul2(T, ssum));
+        const float2 rr = sel2(nearx, neary, f2(0.0f), make_float2(rcp_approx(dis.x), rcp_approx(dis.y)));
+        C.Q = mul2(Li, rr);
+        J0 = T;
+        J1 = den;
+        K2 = Z;
     } else {
+        C.Q = f2(1.0f);
+        const bool samex = (ny.x >= 0.0f) || (u2.x <= 0.0f);
+        const bool samey = (ny.y >= 0.0f) || (u2.y <= 0.0f);
+        const float2 den = sel2(samex, samey, mul2(pps, one_pm), d2);
+        const float2 dis = mul2(den, isum);
+        const float2 rr = sel2(nearx, neary, f2(0.0f), make_float2(rcp_approx(dis.x), rcp_approx(dis.y)));
+        const float2 rden = mul2(rr, isum);
+        J1 = mul2(Li, mul2(rr, den));
+        const float2 g = mul2(Li, rden);
+        // one-side form of (3 - p^2 - pm - m^2)/d^2: (u1^2 + u2^2 + d^2)/(rho1^2 rho2^2 (1 + pm)) + 1/rho1^2 + 1/rho2^2
+        const float2 Wsame = fma2(mul2(mul2(fma2(ny, ny, r2s), i12), rden), pps, ssum);
         J0 = sel2(samex, samey, mul2(g, one_pm), mul2(sub2(p, m), rden));
-        Wt = sel2(samex, samey, Wsame, mul2(sub2(f2(3.0f), S2), rden));
+        K2 = mul2(J0, sel2(samex, samey, Wsame, mul2(sub2(f2(3.0f), S2), rden)));
     }
-    const float2 K2 = mul2(J0, Wt);
+    const float2 K3 = mul2(J1, E3);
     const float2 K4 = mul2(J0, S2);
     const float2 B0 = fma2(a2, K2, J0);
     const float2 A0 = add2(B0, J0);
-    const float2 A1 = fma2(a2, K3, add2(J1, J1));
-    const float2 C1 = fma2(nr, A1, J1);
+    const float2 C1 = fma2(nra2, K3, mul2(kn, J1));
     const float2 nrA0 = mul2(nr, A0);
     C.X[0] = fma2(Rpy, S.b[2], mul2(Rpz, S.nb[1]));
     C.X[1] = fma2(Rpz, S.b[0], mul2(Rpx, S.nb[2]));
@@ -425,10 +455,10 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
 #pragma unroll
     for (int k = 0; k < 12; ++k) sm.ksum[k * TPB + threadIdx.x] = f2(0.0f);
     // loop-invariant constants held in registers (not re-derived from FP64 inputs in the loop)
-    float kc[2] = {(float)c.a2, (float)(-c.c1 / c.c2)};
-    opaque(kc[0]);
-    opaque(kc[1]);
-    const float2 a2 = f2(kc[0]), nr = f2(kc[1]);
+    float kc[4] = {(float)c.a2, (float)(-c.c1 / c.c2), (float)(-c.c1 / c.c2 * c.a2), (float)(1.0 - 2.0 * c.c1 / c.c2)};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) opaque(kc[k]);
+    const float2 a2 = f2(kc[0]), nr = f2(kc[1]), nra2 = f2(kc[2]), kn = f2(kc[3]);
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     uint2* wq = sm.queue[threadIdx.x >> 5];
@@ -518,19 +548,19 @@ __device__ __forceinline__ void pair_tile_mixed(const TileArgs& a, const Consts&
                 // that their two chains interleave
                 Coef2 C[2];
                 if (uni) {
-                    seg_coef2<1>(G[0], S, bt2, P, a2, nr, nrq[0][0], nrq[0][1], C[0]);
-                    seg_coef2<1>(G[1], S, bt2, P, a2, nr, nrq[1][0], nrq[1][1], C[1]);
+                    seg_coef2<1>(G[0], S, bt2, P, a2, nr, nra2, kn, nrq[0][0], nrq[0][1], C[0]);
+                    seg_coef2<1>(G[1], S, bt2, P, a2, nr, nra2, kn, nrq[1][0], nrq[1][1], C[1]);
                 } else {
-                    seg_coef2<0>(G[0], S, bt2, P, a2, nr, nrq[0][0], nrq[0][1], C[0]);
-                    seg_coef2<0>(G[1], S, bt2, P, a2, nr, nrq[1][0], nrq[1][1], C[1]);
+                    seg_coef2<0>(G[0], S, bt2, P, a2, nr, nra2, kn, nrq[0][0], nrq[0][1], C[0]);
+                    seg_coef2<0>(G[1], S, bt2, P, a2, nr, nra2, kn, nrq[1][0], nrq[1][1], C[1]);
                 }
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {
-                    SB[p] = add2(SB[p], C[p].cb);  // (times b' when the group closes)
+                    SB[p] = fma2(C[p].Q, C[p].cb, SB[p]);  // (times b' when the group closes)
 #pragma unroll
                     for (int e = 0; e < 3; ++e)
-                        SG[p][e] = fma2(C[p].cRxb, C[p].X[e], fma2(C[p].cq, S.q[e], fma2(C[p].cRp, G[p].Rp[e],
-                                        fma2(C[p].ct, S.t[e], SG[p][e]))));
+                        SG[p][e] = fma2(C[p].Q, fma2(C[p].cRxb, C[p].X[e], fma2(C[p].cq, S.q[e],
+                                        fma2(C[p].cRp, G[p].Rp[e], mul2(C[p].ct, S.t[e])))), SG[p][e]);
                 }
                 if (__any_sync(0xffffffffu, nrq[0][0] || nrq[0][1] || nrq[1][0] || nrq[1][1])) {
                     const unsigned js = (unsigned)(j0 + jj);
