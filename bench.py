@@ -149,27 +149,36 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.fh.close()
-        rows = []
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        with open(self.path) as f:
+            summary = clock_summary(f)
         os.unlink(self.path)
-        if not rows:
-            return None
+        return summary
 
-        def num(x):
-            try:
-                return float(x)
-            except ValueError:
-                return float("nan")
 
-        sm = [num(r[1]) for r in rows]
-        mx = [num(r[2]) for r in rows]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
-        return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": float(np.nanmax(mx)), "reasons": reasons,
-                "samples": len(rows)}
+def clock_summary(lines):
+    """Median and maximum SM clock and the throttle reasons seen, from the
+    lines of `nvidia-smi --query-gpu=<ClockSampler.FIELDS>
+    --format=csv,noheader,nounits`; None without a sample."""
+    rows = []
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) >= 9:
+            rows.append(parts)
+    if not rows:
+        return None
+
+    def num(x):
+        try:
+            return float(x)
+        except ValueError:
+            return float("nan")
+
+    sm = [num(r[1]) for r in rows]
+    mx = [num(r[2]) for r in rows]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+    return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": float(np.nanmax(mx)), "reasons": reasons,
+            "samples": len(rows)}
 
 
 # ---------------------------------------------------------------- helpers
