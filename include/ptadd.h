@@ -52,7 +52,7 @@ extern "C" {
 #endif
 
 #define PTADD_VERSION_MAJOR 0
-#define PTADD_VERSION_MINOR 1
+#define PTADD_VERSION_MINOR 2
 
 typedef struct ptadd_ctx ptadd_ctx; /* opaque; owns its device memory and stream */
 

@@ -108,7 +108,10 @@ namespace {
 
 constexpr int BRED = 256;   // nodes per reduction block
 constexpr int TILE_FP64 = 128;
-constexpr int TILE_MIX = 128;
+// sources per staged tile of the mixed kernel: 192 at 128 threads (3 blocks
+// of 66.5 KB fit one SM's shared memory), 128 at 64 threads
+template <int TPB>
+constexpr int tile_mix() { return TPB >= 128 ? 192 : 128; }
 
 // ------------------------------------------------------------ kernels
 __global__ void batch_prep_kernel(int64_t n, const double* __restrict__ pos, const int32_t* __restrict__ nxt,
@@ -197,6 +200,7 @@ __device__ __forceinline__ TileArgs tile_from_item(const BatchPairArgs& b, const
 template <int TPB, int MINB, bool MIXED>
 __global__ void __launch_bounds__(TPB, MINB) batch_pair_kernel(BatchPairArgs b, Consts c, float near2)
 {
+    constexpr int TILE_MIX = tile_mix<TPB>();
     constexpr int SM_BYTES = MIXED ? (int)sizeof(MixSmem<TILE_MIX, TPB>) : TILE_FP64 * SRC_STRIDE * 8;
     __shared__ __align__(16) unsigned char smem[SM_BYTES];
     __shared__ int item;

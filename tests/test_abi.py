@@ -35,7 +35,7 @@ def test_library_builds_and_exports_every_declared_symbol():
 def test_version_and_error_string_without_gpu():
     from paper_2005_02498_gb300 import ptadd
     lib = ptadd.load()
-    assert lib.ptadd_version() == 1
+    assert lib.ptadd_version() == 2
     assert isinstance(lib.ptadd_last_error(), bytes)
 
 
