@@ -1,6 +1,7 @@
 """The oracle's junctions and thermally activated breaking (Sec. 2.2) and the
 paper's microstructure recipe (Sec. 3.2.1), against what fixes them from
-outside: the published SplitMix64 test vector, closed-form capture times of
+outside: the published SplitMix64 test vector (the mixing function and the
+stream of break fractions), closed-form capture times of
 a loop that expands at a known speed, the clock of a stuck network, the
 plain burst when no junction can form, and the Schmid factors of [001]
 tension."""
@@ -23,6 +24,9 @@ def test_splitmix64_published_vector():
             16408922859458223821]
     got = [O.splitmix64_mix((1234567 + k * GOLDEN) & (2 ** 64 - 1)) for k in range(1, 6)]
     assert got == want
+    # node 0's break fractions are that stream's outputs, top 53 bits on [0, 1):
+    # the k-th draw (k = 0, 1, ...) is the generator's (k+1)-th output
+    assert [O.junction_fraction(1234567, 0, k) for k in range(5)] == [(w >> 11) * 2.0 ** -53 for w in want]
 
 
 def test_break_fractions_are_uniform_on_the_unit_interval():
@@ -105,6 +109,10 @@ def test_stuck_network_jumps_to_the_break_and_the_node_stays_free():
     seg = np.roll(net.xyz[:N], -1, 0) - net.xyz[:N]
     length = np.linalg.norm(seg, axis=1).sum() + 2 * 2 * 50e-9
     assert math.isclose(r["rho_avg"], length / net.volume, rel_tol=1e-13)  # rho kept through the jump
+    # the jump puts the start of step 1 exactly at the break time, and a
+    # junction is released by the step that starts at (or after) its break
+    r2 = O.burst_junctions(MAT, net, 2, dt, rc, a, 1e-15, seed, interactions=False)
+    assert list(r2["state"]["counts"]) == [1, 1, 1] and r2["state"]["seg"][0] == -1
 
 
 def test_no_junction_reduces_to_the_plain_burst():

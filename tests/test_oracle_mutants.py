@@ -1,0 +1,175 @@
+"""The oracle's pins against planted mistakes (mutation testing, CPU only).
+
+Each mutant is a copy of the oracle's C sources with one plausible mistake
+planted by a textual replacement that matches exactly once: a dropped term,
+a wrong sign, a wrong index, a transposed operand, a swapped shape function
+or weight.  The copy is compiled with the oracle's own flags into a
+temporary library, and the pin tests of that part of the oracle are run
+against it in a subprocess (the oracle package is pointed at the copy before
+its first call).  Every mutant must make at least one pin fail; the
+unmutated copy, built and run the same way, must pass them all.
+
+Mutants that cannot change any result are not listed: for instance the time
+average weighted by a constant dt, or a boundary comparison that the inputs
+never meet.  The committed oracle sources are only read; nothing here
+changes them.
+"""
+
+import concurrent.futures
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+SOURCES = ["ptadd_oracle.c", "mlp_oracle.c", "junction_oracle.c"]
+HEADER = "ptadd_oracle.h"
+
+PINS = "tests/test_oracle_pins.py"
+JPINS = "tests/test_junction_oracle.py"
+MPINS = "tests/test_mlp_oracle.py"
+
+# (name, source file, text, replacement, pin file)
+MUTANTS = [
+    # the segment stress (nonsingular isotropic field, Sec. 2.1)
+    ("a2_term_dropped_in_A0", "ptadd_oracle.c",
+     "const double A0 = 2.0 * J[0] + 3.0 * a2 * J[2];", "const double A0 = 2.0 * J[0];", PINS),
+    ("sign_of_q_term_in_g", "ptadd_oracle.c",
+     "G[i] = -(A0 * Rxb[i] + A1 * q[i]);", "G[i] = -(A0 * Rxb[i] - A1 * q[i]);", PINS),
+    ("poisson_factor_sign", "ptadd_oracle.c",
+     "mu / (4.0 * ORC_PI * (1.0 - nu))", "mu / (4.0 * ORC_PI * (1.0 + nu))", PINS),
+    ("sign_of_the_J3_term", "ptadd_oracle.c",
+     "- (Rp[al] * t[be] + t[al] * Rp[be]) * J[3]", "+ (Rp[al] * t[be] + t[al] * Rp[be]) * J[3]", PINS),
+    ("diagonal_J2_dropped", "ptadd_oracle.c",
+     "dab * qR * (J[0] + 3.0 * a2 * J[2])", "dab * qR * J[0]", PINS),
+    ("J1_wrong_index", "ptadd_oracle.c",
+     "J[1] = dr / (r1 * r2);", "J[1] = dr / (r1 * r1);", PINS),
+    ("straddling_J0_sign", "ptadd_oracle.c",
+     "J[0] = u2 / (d2 * r2) - u1 / (d2 * r1);", "J[0] = u2 / (d2 * r2) + u1 / (d2 * r1);", PINS),
+    ("one_side_J2_tail_term", "ptadd_oracle.c",
+     "return (w + 2.0 * r) / (3.0 * r * r * r * (r + w) * (r + w));",
+     "return (w + r) / (3.0 * r * r * r * (r + w) * (r + w));", PINS),
+    ("gauss_weights_swapped", "ptadd_oracle.c",
+     "GL4_W[4] = {0.3478548451374538, 0.6521451548625461,",
+     "GL4_W[4] = {0.6521451548625461, 0.3478548451374538,", PINS),
+    # the Peach-Koehler force and the nodal assembly (Sec. 2.1)
+    ("pk_force_operands_transposed", "ptadd_oracle.c",
+     "cross3(sb, t, f);", "cross3(t, sb, f);", PINS),
+    ("shape_function_swapped", "ptadd_oracle.c",
+     "Fs[c] += L * w[q] * (1.0 - xi[q]) * f[c];", "Fs[c] += L * w[q] * xi[q] * f[c];", PINS),
+    ("stress_times_b_index", "ptadd_oracle.c",
+     "out[0] = s[0] * v[0] + s[5] * v[1] + s[4] * v[2];",
+     "out[0] = s[0] * v[0] + s[4] * v[1] + s[5] * v[2];", PINS),
+    ("nodal_assembly_neighbour", "ptadd_oracle.c",
+     "FsFe[6 * prv[a] + 3 + c]", "FsFe[6 * nxt[a] + 3 + c]", PINS),
+    # the glide mobility (Eq. 2.1), lumped and consistent
+    ("glide_projection_dropped", "ptadd_oracle.c",
+     "v[c] = (Fa[c] - n[c] * nF) / (B * M);", "v[c] = Fa[c] / (B * M);", PINS),
+    ("lumped_mass_not_halved", "ptadd_oracle.c",
+     "const double M = 0.5 * (sqrt(dot3(dp, dp)) + sqrt(dot3(dn, dn)));",
+     "const double M = (sqrt(dot3(dp, dp)) + sqrt(dot3(dn, dn)));", PINS),
+    ("consistent_mass_off_diagonal", "ptadd_oracle.c",
+     "A[i * m + j] += B * L / 6.0;", "A[i * m + j] += B * L / 3.0;", PINS),
+    # the averages (Eq. 2.5), the polar velocity (Eq. 2.11) and the Euler step
+    ("lp_outer_product_transposed", "ptadd_oracle.c",
+     "acc[al * 3 + be] += bv[al] * c[be];", "acc[al * 3 + be] += bv[be] * c[al];", PINS),
+    ("lp_cross_product_sign", "ptadd_oracle.c",
+     "cross3(dx, vb, c);", "cross3(vb, dx, c);", PINS),
+    ("rho_squared_length", "ptadd_oracle.c",
+     "len += sqrt(dot3(dx, dx));", "len += dot3(dx, dx);", PINS),
+    ("polar_velocity_length_dropped", "ptadd_oracle.c",
+     "acc[m] += L * 0.5 * (v[3 * i + m] + v[3 * j + m]);",
+     "acc[m] += 0.5 * (v[3 * i + m] + v[3 * j + m]);", PINS),
+    ("euler_step_sign", "ptadd_oracle.c",
+     "++m) x[m] += v[m] * dt;", "++m) x[m] -= v[m] * dt;", PINS),
+    # junctions (Sec. 2.2): the counter-based generator, the capture distance,
+    # the release and the clock jump
+    ("splitmix_shift", "junction_oracle.c",
+     "z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;", "z = (z ^ (z >> 28)) * 0x94D049BB133111EBull;", JPINS),
+    ("break_fraction_counter", "junction_oracle.c",
+     "(uint64_t)(k + 1) * 0x9E3779B97F4A7C15ull", "(uint64_t)k * 0x9E3779B97F4A7C15ull", JPINS),
+    ("far_end_not_clamped", "junction_oracle.c",
+     "if (u > 1.0) u = 1.0;", "if (u > 2.0) u = 2.0;", JPINS),
+    ("release_strictly_after_the_break", "junction_oracle.c",
+     "jbreak[p] <= t) {", "jbreak[p] < t) {", JPINS),
+    ("jump_from_the_step_start", "junction_oracle.c",
+     "const double jump = tmin - t1;", "const double jump = tmin - t;", JPINS),
+    # the surrogate's network (Sec. 3.3): activation, loss gradient, Adam
+    ("gelu_derivative_exponent", "mlp_oracle.c",
+     "z * exp(-0.5 * z * z) / sqrt(2.0 * pi)", "z * exp(-z * z) / sqrt(2.0 * pi)", MPINS),
+    ("loss_gradient_factor", "mlp_oracle.c",
+     "d[off[L] + i] = 2.0 * e * scale;", "d[off[L] + i] = e * scale;", MPINS),
+    ("bias_gradient_doubled", "mlp_oracle.c",
+     "gb[i] += dz[i];", "gb[i] += 2.0 * dz[i];", MPINS),
+    ("adam_bias_corrections_swapped", "mlp_oracle.c",
+     "p[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);",
+     "p[i] -= lr * (m[i] / c2) / (sqrt(v[i] / c1) + eps);", MPINS),
+]
+
+# Runs one pin file against the library named by argv[1]: the oracle package
+# loads its library lazily, so pointing it at the copy before the first call
+# is enough.
+RUNNER = (
+    "import sys\n"
+    "import oracle\n"
+    "lib = sys.argv[1]\n"
+    "oracle._LIB = lib\n"
+    "oracle.build = lambda force=False: lib\n"
+    "import pytest\n"
+    "sys.exit(pytest.main(sys.argv[2:]))\n"
+)
+
+
+def _build_copy(workdir, mutant):
+    """Copy the oracle sources into workdir, plant the mutant (None: none),
+    and compile them as the oracle's build does; returns the library path."""
+    os.makedirs(workdir, exist_ok=True)
+    for f in SOURCES + [HEADER]:
+        shutil.copy(os.path.join(ORACLE, f), os.path.join(workdir, f))
+    if mutant is not None:
+        _, fname, old, new, _ = mutant
+        path = os.path.join(workdir, fname)
+        text = open(path).read()
+        assert text.count(old) == 1, "%s: the text to mutate occurs %d times" % (mutant[0], text.count(old))
+        open(path, "w").write(text.replace(old, new))
+    lib = os.path.join(workdir, "liboracle.so")
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off", "-std=c11", "-o", lib,
+           *[os.path.join(workdir, f) for f in SOURCES], "-lm"]
+    subprocess.run(cmd, check=True, capture_output=True)
+    return lib
+
+
+def _run_pins(lib, pin_file):
+    """Exit status of the pin file against lib (0: every pin passed)."""
+    env = dict(os.environ, OMP_NUM_THREADS="2", PYTHONPATH=ROOT + os.pathsep + os.environ.get("PYTHONPATH", ""))
+    args = [sys.executable, "-c", RUNNER, lib, pin_file, "-x", "-q", "-m", "not gpu", "-p", "no:cacheprovider"]
+    r = subprocess.run(args, cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    return r.returncode, r.stdout[-2000:]
+
+
+def test_unmutated_copy_passes_every_pin(tmp_path):
+    lib = _build_copy(str(tmp_path / "orig"), None)
+    for pins in (PINS, JPINS, MPINS):
+        rc, out = _run_pins(lib, pins)
+        assert rc == 0, "the harness fails the unmutated oracle on %s:\n%s" % (pins, out)
+
+
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    names = [m[0] for m in MUTANTS]
+    assert len(set(names)) == len(names)
+
+    def one(m):
+        lib = _build_copy(str(tmp_path / m[0]), m)
+        return m[0], _run_pins(lib, m[4])
+
+    workers = max(1, min(8, (os.cpu_count() or 2) // 2))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
+        results = list(ex.map(one, MUTANTS))
+    survivors = [name for name, (rc, _) in results if rc == 0]
+    assert not survivors, "planted mistakes that no pin catches: %s" % survivors
+    # a pin failed (exit status 1), not the harness (collection errors, crashes)
+    other = [(name, rc) for name, (rc, _) in results if rc not in (1,)]
+    assert not other, "mutants that ended otherwise than by a failing pin: %s" % other
