@@ -49,6 +49,25 @@ def test_pta_records_follow_the_rules():
             assert abs(recs[k + 1]["t"] - (r["t"] + h)) <= 1e-15 * max(1.0, r["t"] + h)
 
 
+def test_pta_network_that_cannot_move_converges_in_two_chunks():
+    """Every node pinned: each chunk's averages are Lp = 0 and the constant
+    rho = length / volume, so each running average converges as soon as it
+    can be compared (two chunks), nothing jumps or is extended, and the slow
+    step is the largest allowed."""
+    p = P()
+    net = W.small_loop_network()
+    net.pinned = np.ones(net.n_nodes, dtype=np.uint8)
+    length = sum(np.linalg.norm(np.roll(net.xyz[a:b], -1, 0) - net.xyz[a:b], axis=1).sum()
+                 for a, b in zip(net.loop_off[:-1], net.loop_off[1:]))
+    rho = length / net.volume
+    recs = OP.run(MAT, net, p, 2)
+    for r in recs:
+        assert r["chunks"] == [2, 2] and r["jumps"] == 0 and r["extended"] == 0
+        assert np.all(r["Lp"] == 0.0) and np.all(r["Lpdot"] == 0.0) and r["rhodot"] == 0.0
+        assert abs(r["rho"] / rho - 1) < 1e-12
+    assert recs[1]["t"] == p.h_max
+
+
 def test_pta_jump_rule_restarts_until_the_cap():
     p = P(lpdot_max=0.0, max_jumps=2, max_chunks=2)
     recs = OP.run(MAT, W.small_loop_network(), p, 1)
@@ -69,6 +88,44 @@ def test_pta_first_step_is_two_plain_bursts_when_one_chunk_is_allowed():
     n2.sig_app = np.array(p.pattern) * p.rate * p.delta
     r2 = O.burst(MAT, n2, p.chunk, p.dt)
     assert np.array_equal(rec["Lp_prev"], r1["Lp_avg"]) and np.array_equal(rec["Lp"], r2["Lp_avg"])
+
+
+def _chain(net, p, loads):
+    """Plain oracle bursts of p.chunk steps, one per load value (times the
+    pattern), each from the end state of the one before."""
+    out, xyz = [], net.xyz.copy()
+    for load in loads:
+        m = net.copy()
+        m.xyz, m.sig_app = xyz, np.array(p.pattern) * load
+        out.append(O.burst(MAT, m, p.chunk, p.dt))
+        xyz = out[-1]["xyz"]
+    return out
+
+
+def test_pta_second_step_starts_where_the_first_ended():
+    """The microstructure is carried: the second slow step's bursts at
+    l(t1 - Delta) and l(t1) continue from the end of the first step's l(0)
+    burst."""
+    p = P(max_chunks=1, extend_chunks=0)
+    net = W.small_loop_network()
+    recs = OP.run(MAT, net, p, 2)
+    t1 = recs[1]["t"]
+    # l(t) = rate (t + Delta), at t = t1 - Delta and at t = t1 (rounded as written)
+    r = _chain(net, p, [0.0, p.rate * p.delta, p.rate * ((t1 - p.delta) + p.delta), p.rate * (t1 + p.delta)])
+    assert np.array_equal(recs[0]["Lp"], r[1]["Lp_avg"])
+    assert np.array_equal(recs[1]["Lp_prev"], r[2]["Lp_avg"]) and np.array_equal(recs[1]["Lp"], r[3]["Lp_avg"])
+
+
+def test_pta_jump_restarts_the_pair_from_the_end_of_the_pair():
+    """A jump restarts both averages from the state the l(t) burst ended in:
+    with the threshold at 0 and one jump allowed, the step is the pair of
+    bursts that follows the first pair."""
+    p = P(max_chunks=1, extend_chunks=0, lpdot_max=0.0, max_jumps=1)
+    net = W.small_loop_network()
+    rec = OP.run(MAT, net, p, 1)[0]
+    r = _chain(net, p, [0.0, p.rate * p.delta, 0.0, p.rate * p.delta])
+    assert rec["jumps"] == 1
+    assert np.array_equal(rec["Lp_prev"], r[2]["Lp_avg"]) and np.array_equal(rec["Lp"], r[3]["Lp_avg"])
 
 
 class _StandInContext:
