@@ -215,10 +215,11 @@ def test_stress_step_control_halves_down_to_delta_star():
 
 class _StandInBatch:
     """The batch calls of a context, answered by the oracle's burst on the
-    host, so that the product's block driver can be checked on the CPU."""
+    host (or another burst function of the same signature), so that the
+    product's block driver can be checked on the CPU."""
 
-    def __init__(self, net):
-        self.net = net
+    def __init__(self, net, burst_fn=O.burst):
+        self.net, self.burst_fn = net, burst_fn
 
     def batch_set(self, batch):
         self.xyz = [batch.xyz[batch.node_off[r]:batch.node_off[r + 1]].copy() for r in range(batch.R)]
@@ -231,7 +232,7 @@ class _StandInBatch:
         for r in range(len(self.xyz)):
             m = self.net.copy()
             m.xyz, m.sig_app = self.xyz[r], self.sig[r]
-            b = O.burst(MAT, m, n, dt)
+            b = self.burst_fn(MAT, m, n, dt)
             self.xyz[r], lp[r], rho[r] = b["xyz"], b["Lp_avg"], b["rho_avg"]
         return lp, rho
 
@@ -258,6 +259,21 @@ def test_block_driver_follows_the_oracle_increment():
         for key in ("T_prev", "T_t", "mag", "R_prev", "R_t", "Lpdot", "rhodot", "Lp"):
             assert np.allclose(got[key], want[key], rtol=1e-12, atol=0), key
         prev = T_k
+
+
+def test_block_driver_runs_in_lock_step_like_the_oracle():
+    """Blocks whose answers settle at different rates: the product's driver,
+    like the oracle's increment, keeps every block running until the slowest
+    one has converged."""
+    net = W.small_loop_network()
+    net.xyz[0, 0] = 0.0
+    p = P(tol_lp=1e-3, max_chunks=100)
+    T = np.array([[q, 0, 0, 0, 0, 0] for q in (0.3, 0.6, 0.8)])
+    st = {"Lp": np.zeros((3, 3, 3)), "Lpdot": np.zeros((3, 3, 3))}
+    want = OB.increment(None, net, [net.xyz.copy() for _ in range(3)], st, T, None, 0.0, p, _drifting_burst)
+    got = B.BlockPTA(_StandInBatch(net, _drifting_burst), net, 3, p).increment(T, None, 0.0)
+    assert got["chunks"] == want["chunks"] and want["chunks"][0] > 2
+    assert np.allclose(got["R_prev"], want["R_prev"], rtol=1e-15, atol=0)
 
 
 def test_synthetic_coupling_run_on_stand_in_bursts():
