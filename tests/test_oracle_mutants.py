@@ -97,6 +97,25 @@ MUTANTS = [
      "acc[m] += 0.5 * (v[3 * i + m] + v[3 * j + m]);", PINS),
     ("euler_step_sign", "ptadd_oracle.c",
      "++m) x[m] += v[m] * dt;", "++m) x[m] -= v[m] * dt;", PINS),
+    # the network tables, the total stress and the pinned nodes
+    ("loop_left_open", "ptadd_oracle.c",
+     "nxt[i] = (i + 1 < e) ? i + 1 : b;", "nxt[i] = (i + 1 < e) ? i + 1 : e - 1;", PINS),
+    ("applied_stress_dropped", "ptadd_oracle.c",
+     "for (int c = 0; c < 6; ++c) sig[c] = sig_app[c];", "for (int c = 0; c < 6; ++c) sig[c] = 0.0 * sig_app[c];", PINS),
+    ("half_the_interactions", "ptadd_oracle.c",
+     "for (int64_t i = 0; i < n_nodes; ++i) {\n        orc_seg_stress",
+     "for (int64_t i = 0; i < n_nodes; i += 2) {\n        orc_seg_stress", PINS),
+    ("pinned_nodes_move", "ptadd_oracle.c",
+     "if ((pinned && pinned[a]) || !(M > 0.0)) {", "if (!(M > 0.0)) {", PINS),
+    ("segments_skipped_at_one_pinned_end", "ptadd_oracle.c",
+     "if (skip_pinned && pinned && pinned[i] && pinned[nxt[i]]) continue;",
+     "if (skip_pinned && pinned && pinned[i]) continue;", PINS),
+    # the brute-force reference the analytic field is checked against
+    ("quadrature_reference_laplacian_sign", "ptadd_oracle.c",
+     "(d3[(i * 3 + al) * 3 + be] - ((al == be) ? dl[i] : 0.0L))",
+     "(d3[(i * 3 + al) * 3 + be] + ((al == be) ? dl[i] : 0.0L))", PINS),
+    ("quadrature_reference_weight", "ptadd_oracle.c",
+     "const long double wt = 0.5L * h * w[g];", "const long double wt = h * w[g];", PINS),
     # junctions (Sec. 2.2): the counter-based generator, the capture distance,
     # the release and the clock jump
     ("splitmix_shift", "junction_oracle.c",
