@@ -100,6 +100,9 @@ int ptadd_version(void);
 /* Create a context on CUDA device `device` (it is made current).  mat must
  * have mu > 0, -1 < nu < 0.5, b > 0, a > 0, B > 0. */
 ptadd_status ptadd_create(ptadd_ctx** out, const ptadd_material* mat, ptadd_precision prec, int device);
+/* Synchronise the context's stream, then free everything the context owns
+ * (device buffers, graphs, events, its own stream; a caller's stream set by
+ * ptadd_set_stream is left alone).  NULL is a no-op. */
 void ptadd_destroy(ptadd_ctx* ctx);
 
 /* Message of the last failed call on this host thread (never NULL). */
@@ -134,6 +137,10 @@ ptadd_status ptadd_set_network(ptadd_ctx* ctx, int64_t n_nodes, const double* xy
 /* Applied stress sigma_app (Pa, Voigt order), uniform over the box. */
 ptadd_status ptadd_set_applied_stress(ptadd_ctx* ctx, const double sig[6]);
 
+/* Sizes of the loaded network into *info (caller-owned): nodes, loops,
+ * target segments (those with an unpinned node), segment pairs per DD step
+ * (targets x sources), precision and device.  PTADD_ERR_STATE without a
+ * network; PTADD_ERR_ARG for NULL arguments. */
 ptadd_status ptadd_get_info(const ptadd_ctx* ctx, ptadd_info* info);
 
 /* ------------------------------------------------------------------- burst */
@@ -145,7 +152,6 @@ ptadd_status ptadd_get_info(const ptadd_ctx* ctx, ptadd_info* info);
 ptadd_status ptadd_advance(ptadd_ctx* ctx, int64_t n_steps, double dt,
                            double Lp_avg[9], double* rho_avg);
 
-/* Current node positions (m) into host xyz[n_nodes*3]. */
 /* Polar dislocation velocity of the last burst (Sec. 2.4, Eq. 2.11; Eq. 2.5
  * for its running average): the volume-averaged dislocation velocity
  *   V = (1/|B|) sum_s vbar_s l_s A_s,
@@ -158,6 +164,10 @@ ptadd_status ptadd_advance(ptadd_ctx* ctx, int64_t n_steps, double dt,
  * PTADD_ERR_STATE before the first ptadd_advance after ptadd_set_network;
  * PTADD_ERR_ARG for a non-positive core_area. */
 ptadd_status ptadd_get_polar_velocity(ptadd_ctx* ctx, double core_area, double V_avg[3]);
+
+/* Current node positions (m) into host xyz[n_nodes*3] (caller-owned, node
+ * order of ptadd_set_network); synchronises the stream.  PTADD_ERR_STATE
+ * without a network; PTADD_ERR_ARG for a NULL array. */
 ptadd_status ptadd_get_nodes(ptadd_ctx* ctx, double* xyz);
 
 /* Replace the positions of the loaded network (host xyz[n_nodes*3], m; same
@@ -177,6 +187,11 @@ ptadd_status ptadd_get_forces_dev(ptadd_ctx* ctx, double* F_dev);
  * PTA carry-over of Sec. 2.5) into buf.  Call with buf = NULL to get the size
  * in *bytes; otherwise *bytes must hold the buffer size. */
 ptadd_status ptadd_get_state(ptadd_ctx* ctx, void* buf, size_t* bytes);
+/* Restore positions (and, while junctions are on, the junction state) from a
+ * blob of ptadd_get_state taken on the same network.  PTADD_ERR_ARG if the
+ * size or the header does not match (another network, or junctions on in
+ * one and off in the other); PTADD_ERR_STATE without a network.  The blob
+ * stays the caller's. */
 ptadd_status ptadd_set_state(ptadd_ctx* ctx, const void* buf, size_t bytes);
 
 /* ------------------------------------------------------------------ batched */
@@ -200,6 +215,14 @@ typedef struct {
     int32_t tuned;          /* 1 if the configuration came from the tuner/cache */
 } ptadd_batch_info;
 
+/* Load a batch (host arrays, copied; layout as above): node_off[R+1] with
+ * node_off[0] = 0 and >= 2 nodes per realisation, loop_off[n_loops+1],
+ * xyz[n*3] (m), burgers and normal [n_loops*3], pinned[n] (NULL: none),
+ * sig6[R*6] (Pa), volume[R] (m^3).  Replaces any earlier batch and resets
+ * its running averages.  PTADD_ERR_ARG on NULL arrays, R < 1, offset
+ * tables that do not run from 0 to n_nodes, a loop or realisation of fewer
+ * than 2 nodes, a loop that straddles realisations, a volume that is not
+ * positive and finite, or more than 2^31 - 1 nodes. */
 ptadd_status ptadd_batch_set(ptadd_ctx* ctx, int32_t R, const int64_t* node_off, int64_t n_loops,
                              const int64_t* loop_off, const double* xyz, const double* burgers,
                              const double* normal, const uint8_t* pinned, const double* sig6,
@@ -212,8 +235,13 @@ ptadd_status ptadd_batch_advance(ptadd_ctx* ctx, int64_t n_steps, double dt, dou
 /* R^V of the last batch burst per realisation (as ptadd_get_polar_velocity,
  * with each realisation's own volume): V_avg[R*3] (m/s). */
 ptadd_status ptadd_batch_get_polar_velocity(ptadd_ctx* ctx, double core_area, double* V_avg);
+/* Positions of every realisation (concatenated, m) into / from host
+ * xyz[n_nodes*3] (caller-owned); set_nodes keeps the topology, stresses and
+ * junctions.  PTADD_ERR_STATE without a batch; PTADD_ERR_ARG for NULL. */
 ptadd_status ptadd_batch_get_nodes(ptadd_ctx* ctx, double* xyz);
 ptadd_status ptadd_batch_set_nodes(ptadd_ctx* ctx, const double* xyz);
+/* Sizes and the pair-stage configuration of the loaded batch into *info.
+ * PTADD_ERR_STATE without a batch; PTADD_ERR_ARG for NULL. */
 ptadd_status ptadd_batch_get_info(ptadd_ctx* ctx, ptadd_batch_info* info);
 /* Time the pair stage of the loaded batch for every candidate (tile of 64 or
  * 128 targets x chunks of 1024/2048/4096 sources), keep the fastest, and
@@ -276,6 +304,10 @@ ptadd_status ptadd_gemm_timeout_selftest(int device);
 int64_t ptadd_mlp_param_count(void);
 /* Glorot-uniform weights from a splitmix64 stream of `seed`, zero biases. */
 ptadd_status ptadd_mlp_init(ptadd_ctx* ctx, uint64_t seed);
+/* Copy all parameters in (set: also resets Adam's moments) or out, packed
+ * as above; params[count] is host memory of the caller, count must equal
+ * ptadd_mlp_param_count() (else PTADD_ERR_ARG).  get before init or set:
+ * PTADD_ERR_STATE. */
 ptadd_status ptadd_mlp_set_params(ptadd_ctx* ctx, const float* params, int64_t count);
 ptadd_status ptadd_mlp_get_params(ptadd_ctx* ctx, float* params, int64_t count);
 /* Loss and gradient (packed like the parameters) of one forward/backward pass
@@ -500,6 +532,8 @@ ptadd_status ptadd_block_stress_pair(int32_t n_blocks, const double* T6_k, const
 /* Save / restore a fitted surrogate (weights, input/output maps, trust
  * region) as one blob; buf = NULL asks for the size. */
 ptadd_status ptadd_surrogate_get_state(ptadd_ctx* ctx, void* buf, size_t* bytes);
+/* Restore a blob of ptadd_surrogate_get_state (any context, same library
+ * version); PTADD_ERR_ARG if its size or header does not match. */
 ptadd_status ptadd_surrogate_set_state(ptadd_ctx* ctx, const void* buf, size_t bytes);
 
 /* ------------------------------------------------------------- measurement */
