@@ -175,8 +175,12 @@ ptadd_status ptadd_get_nodes(ptadd_ctx* ctx, double* xyz);
  * gives a direct DMA) and converted there.  Resets nothing else. */
 ptadd_status ptadd_set_nodes(ptadd_ctx* ctx, const double* xyz);
 
-/* Nodal forces (N) at the current positions into host F[n_nodes*3]; every
- * segment is evaluated (pinned ones included). */
+/* Nodal forces (N) at the current positions into host F[n_nodes*3]: the
+ * Peach-Koehler force (Sec. 2.1) of the nonsingular stress of every segment
+ * plus the applied stress, integrated against the linear shape functions
+ * with the 4-point Gauss rule, in the context's precision; every segment is
+ * evaluated (pinned ones included).  PTADD_ERR_STATE without a network;
+ * PTADD_ERR_ARG for a NULL array. */
 ptadd_status ptadd_get_forces(ptadd_ctx* ctx, double* F);
 
 /* Same as ptadd_get_forces into a device buffer F_dev[n_nodes*3] (N),
@@ -335,10 +339,14 @@ ptadd_status ptadd_surrogate_fit(ptadd_ctx* ctx, int64_t n, const double* feat, 
                                  int batch, float lr, uint64_t seed, float* loss_per_epoch);
 /* Host arrays; in_region (or NULL) receives 1 inside the trust region.
  * Prediction runs one fused kernel (input map, trust region, the four layers,
- * output map).  Its GELU evaluates erf through tanh(x (A + B x^2)), a fit
- * with |error| <= 2.8e-4, below the BF16 rounding of the activations; so its
- * answers can differ from ptadd_mlp_forward (exact erf) in the last BF16
- * bits. */
+ * output map) on the tensor cores with FP16 operands (the BF16 weights
+ * convert to FP16 exactly in its normal range; inputs and activations are
+ * rounded to FP16) and FP32 accumulation.  Its GELU evaluates erf through
+ * tanh(x (A + B x^2)), a fit with |error| <= 2.8e-4, in f16x2 arithmetic, at
+ * the size of the FP16 rounding of the stored activations; so its answers
+ * can differ from ptadd_mlp_forward (BF16 activations, exact erf) at the
+ * level of those roundings (4.9e-4 relative against the FP64 reference in
+ * the tests). */
 ptadd_status ptadd_surrogate_predict(ptadd_ctx* ctx, int64_t n, const double* feat, double* lp6, uint8_t* in_region);
 /* Device arrays, enqueued on the context's stream without synchronising. */
 ptadd_status ptadd_surrogate_predict_dev(ptadd_ctx* ctx, int64_t n, const double* feat_dev, double* lp6_dev,
@@ -470,8 +478,8 @@ typedef struct {
     int64_t broken;
     int64_t jumps;
 } ptadd_junction_info;
-/* Junction state; the per-node arrays (caller-owned, n_nodes each, any may
- * be NULL): seg = held sessile segment or -1, last = sessile loop last
+/* Junction state (Sec. 2.2, Eq. 2.2); the per-node arrays (caller-owned,
+ * n_nodes each, any may be NULL): seg = held sessile segment or -1, last = sessile loop last
  * broken from or -1, count = junctions formed, break_time (s).
  * PTADD_ERR_STATE when junctions are off. */
 ptadd_status ptadd_get_junctions(ptadd_ctx* ctx, ptadd_junction_info* info, int32_t* seg, int32_t* last,
@@ -492,7 +500,8 @@ ptadd_status ptadd_get_junctions(ptadd_ctx* ctx, ptadd_junction_info* info, int3
  * PTADD_ERR_STATE without a batch; PTADD_ERR_ARG on negative or non-finite
  * parameters. */
 ptadd_status ptadd_batch_set_junctions(ptadd_ctx* ctx, const ptadd_junction_params* p);
-/* info[R] (one per realisation, caller-owned); the per-node arrays (n nodes
+/* The batch's junction state (Sec. 2.2, per realisation): info[R] (one per
+ * realisation, caller-owned); the per-node arrays (n nodes
  * of the batch each, any may be NULL) in realisation-local numbers: seg =
  * start node of the held sessile segment within its realisation or -1, last
  * = loop (numbered from 0 within the realisation) last broken from or -1,
