@@ -431,15 +431,15 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
                 if (!ok) break;
                 tc_fence_after();
                 for (int s = 0; s < 2; ++s)
-                    tc_mma_bf16(accA, smem_desc(uX + s * 256, 128, 512), smem_desc(uW1 + s * 256, 128, 512), id_h,
-                                s ? 1u : 0u);
+                    tc_mma_f16(accA, smem_desc(uX + s * 256, 128, 512), smem_desc(uW1 + s * 256, 128, 512), id_h,
+                               s ? 1u : 0u);
                 // trust region: W = z_hi L_hi + z_hi L_lo + z_lo L_hi (kind::f16 with FP16 operands)
                 for (int s = 0; s < 2; ++s) {
                     const uint64_t zh = smem_desc(uX + s * 256, 128, 512), zl = smem_desc(uXlo + s * 256, 128, 512);
                     const uint64_t lh = smem_desc(uLH + s * 256, 128, 512), ll = smem_desc(uLL + s * 256, 128, 512);
-                    tc_mma_bf16(tmem + MAHA_COL, zh, lh, id_m, s ? 1u : 0u);
-                    tc_mma_bf16(tmem + MAHA_COL, zh, ll, id_m, 1u);
-                    tc_mma_bf16(tmem + MAHA_COL, zl, lh, id_m, 1u);
+                    tc_mma_f16(tmem + MAHA_COL, zh, lh, id_m, s ? 1u : 0u);
+                    tc_mma_f16(tmem + MAHA_COL, zh, ll, id_m, 1u);
+                    tc_mma_f16(tmem + MAHA_COL, zl, lh, id_m, 1u);
                 }
                 tc_commit(uacc0);
                 mma_out = true;
@@ -461,8 +461,8 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
                             ok = wait_or_abort(ufull0 + 8 * st, (uint32_t)((q / NST) & 1), &abort_flag);
                             if (!ok) break;
                             tc_fence_after();
-                            tc_mma_bf16(acc, smem_desc(uOnes, 128, 256), smem_desc(uWC + st * WC_BYTES, 128, 256), id_h,
-                                        0u);
+                            tc_mma_f16(acc, smem_desc(uOnes, 128, 256), smem_desc(uWC + st * WC_BYTES, 128, 256), id_h,
+                                       0u);
                             tc_commit(uempty0 + 8 * st);
                             ++q;
                         }
@@ -472,8 +472,8 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
                         tc_fence_after();
                         const uint32_t ub = uWC + st * WC_BYTES;
                         for (int s = 0; s < KCH / 16; ++s)
-                            tc_mma_bf16(acc, smem_desc(uH + (jj * (KCH / 16) + s) * 256, 128, 4096),
-                                        smem_desc(ub + s * 256, 128, 16 * KCH), id_h, 1u);
+                            tc_mma_f16(acc, smem_desc(uH + (jj * (KCH / 16) + s) * 256, 128, 4096),
+                                       smem_desc(ub + s * 256, 128, 16 * KCH), id_h, 1u);
                         tc_commit(uempty0 + 8 * st);  // the stage is free once these MMAs are done
                     }
                     if (!ok) break;
@@ -487,8 +487,8 @@ __global__ void __launch_bounds__(IT_ALL, 1) mlp_infer_kernel(InferArgs g)
                     if (!ok) break;
                     tc_fence_after();
                     for (int s = 4 * kc; s < 4 * kc + 4; ++s)
-                        tc_mma_bf16(accB, smem_desc(uH + s * 256, 128, 4096), smem_desc(uW4 + s * 256, 128, 4096),
-                                    id_o, s ? 1u : 0u);
+                        tc_mma_f16(accB, smem_desc(uH + s * 256, 128, 4096), smem_desc(uW4 + s * 256, 128, 4096),
+                                   id_o, s ? 1u : 0u);
                 }
                 if (!ok) break;
                 tc_commit(uacc0 + 24);

@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(GEMM_THREADS) tc_gemm_kernel(GemmArgs g)
             const uint32_t a0 = ubase + (uint32_t)(k & 1) * GEMM_STAGE, b0 = a0 + GEMM_A_BYTES;
             const int kc = min(GEMM_KC, g.K - k * GEMM_KC);
             for (int s = 0; s < kc / 16; ++s)
-                tc_mma_bf16(tmem, smem_desc(a0 + s * 256, 128, 1024), smem_desc(b0 + s * 256, 128, 1024), idesc,
-                            (k > 0 || s > 0) ? 1u : 0u);
+                tc_mma_f16(tmem, smem_desc(a0 + s * 256, 128, 1024), smem_desc(b0 + s * 256, 128, 1024), idesc,
+                           (k > 0 || s > 0) ? 1u : 0u);
             tc_commit(mb);
         }
         // every thread waits for the MMAs before the chunk's stage is refilled

@@ -68,8 +68,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
     return true;
 }
 
-__device__ __forceinline__ void tc_mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                            uint32_t accumulate)
+// One tcgen05.mma of kind::f16 issued by the calling thread: D (TMEM, FP32)
+// (+)= A B^T with A and B both BF16 or both FP16, the type set by the
+// instruction descriptor (idesc_bf16_f32 / idesc_f16_f32); accumulate = 0
+// overwrites D.
+__device__ __forceinline__ void tc_mma_f16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate)
 {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
