@@ -250,8 +250,9 @@ ptadd_status ptadd_batch_get_info(ptadd_ctx* ctx, ptadd_batch_info* info);
 /* Time the pair stage of the loaded batch for every candidate (tile of 64 or
  * 128 targets x chunks of 1024/2048/4096 sources), keep the fastest, and
  * append it to a JSON-lines cache (cache_path, else $PTADD_TUNE_CACHE, else
- * $HOME/.cache/ptadd_tune.jsonl) keyed by GPU, library version, precision and
- * the batch's size class.  A cached entry is reused unless force != 0.
+ * $HOME/.cache/ptadd_tune.jsonl) keyed by GPU, library version, a hash of
+ * the sources the library was built from, precision and the batch's size
+ * class.  A cached entry is reused unless force != 0.
  * ptadd_batch_set applies a cached entry when one exists. */
 ptadd_status ptadd_batch_autotune(ptadd_ctx* ctx, const char* cache_path, int force);
 /* Set the pair-stage configuration by hand: tile_targets (threads per

@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
+import hashlib
 import os
 import shutil
 import subprocess
@@ -39,6 +40,17 @@ def _deps():
             + glob.glob(os.path.join(ROOT, "include", "*.h")) + [os.path.abspath(__file__)])
 
 
+def source_hash():
+    """First 16 hex digits of a SHA-256 over the CUDA sources and the public
+    header the library is compiled from; the batch autotuner keys its cache
+    by it, so a tuning is never reused by a library built from other code."""
+    h = hashlib.sha256()
+    for f in sorted(_sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def up_to_date():
     if not os.path.exists(LIB):
         return False
@@ -52,10 +64,11 @@ def build(force=False, verbose=False, extra_flags=()):
         return LIB
     os.makedirs(os.path.join(LIBDIR, "obj"), exist_ok=True)
     exe = nvcc()
+    tag = ["-DPTADD_BUILD_HASH=0x%sull" % source_hash()]
 
     def compile_one(src):
         obj = os.path.join(LIBDIR, "obj", os.path.basename(src) + ".o")
-        cmd = [exe, *ARCH, *NVCC_FLAGS, *extra_flags, "-c", src, "-o", obj]
+        cmd = [exe, *ARCH, *NVCC_FLAGS, *tag, *extra_flags, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd))
         r = subprocess.run(cmd, capture_output=True, text=True)

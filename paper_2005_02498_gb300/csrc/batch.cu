@@ -21,8 +21,9 @@
 //
 // Autotuner: the tile width (threads per block) and the source-chunk length
 // are chosen by timing the pair phase of the loaded batch for each candidate;
-// results are kept in a JSON-lines cache keyed by GPU, library version,
-// precision and the batch's size class.
+// results are kept in a JSON-lines cache keyed by GPU, library version, a
+// hash of the sources the library was built from, precision and the batch's
+// size class.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
@@ -563,15 +564,18 @@ Consts batch_consts(const ptadd_ctx* ctx)
 }
 
 // ----------------------------------------------------------- tune cache
+#ifndef PTADD_BUILD_HASH
+#define PTADD_BUILD_HASH 0ull  // a build that passes no source hash (build.py passes one)
+#endif
 std::string tune_key(const ptadd_ctx* ctx, const DevBatch& B, int prec)
 {
     cudaDeviceProp p;
     cudaGetDeviceProperties(&p, ctx->device);
     const double mean_n = (double)B.n / std::max(1, B.R);
     char buf[512];
-    snprintf(buf, sizeof(buf), "%.200s|sm%d|v%d|%s|n2^%d|R2^%d", p.name, p.multiProcessorCount, ptadd_version(),
-             prec == (int)PTADD_MIXED ? "mixed" : "fp64", (int)lround(log2(std::max(1.0, mean_n))),
-             (int)lround(log2((double)std::max(1, B.R))));
+    snprintf(buf, sizeof(buf), "%.200s|sm%d|v%d|h%016llx|%s|n2^%d|R2^%d", p.name, p.multiProcessorCount,
+             ptadd_version(), (unsigned long long)PTADD_BUILD_HASH, prec == (int)PTADD_MIXED ? "mixed" : "fp64",
+             (int)lround(log2(std::max(1.0, mean_n))), (int)lround(log2((double)std::max(1, B.R))));
     for (char* q = buf; *q; ++q)
         if (*q == '"' || *q == '\n') *q = '_';
     return buf;

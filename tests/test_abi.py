@@ -84,3 +84,25 @@ def test_product_package_never_imports_the_oracle():
 def test_oracle_builds_and_reports_threads():
     import oracle
     assert oracle.num_threads() >= 1
+
+
+def test_source_hash_follows_the_sources(tmp_path, monkeypatch):
+    """The autotuner's cache key part that names the build: the same for the
+    same sources, different when a CUDA source or the public header changes."""
+    import shutil
+    from paper_2005_02498_gb300 import build as B
+    shutil.copytree(B.CSRC, tmp_path / "pkg" / "csrc")
+    shutil.copytree(os.path.join(B.ROOT, "include"), tmp_path / "include")
+    monkeypatch.setattr(B, "CSRC", str(tmp_path / "pkg" / "csrc"))
+    monkeypatch.setattr(B, "ROOT", str(tmp_path))
+    h0 = B.source_hash()
+    assert h0 == B.source_hash() and len(h0) == 16 and int(h0, 16) >= 0
+    for rel in ("pkg/csrc/pair_tile.cuh", "pkg/csrc/batch.cu", "include/ptadd.h"):
+        f = tmp_path / rel
+        text = f.read_text()
+        f.write_text(text + "\n// changed\n")
+        assert B.source_hash() != h0, rel
+        f.write_text(text)
+        assert B.source_hash() == h0
+    (tmp_path / "pkg" / "csrc" / "notes.txt").write_text("not a source")
+    assert B.source_hash() == h0
