@@ -77,6 +77,8 @@ MUTANTS = [
      "out[0] = s[0] * v[0] + s[4] * v[1] + s[5] * v[2];", PINS),
     ("nodal_assembly_neighbour", "ptadd_oracle.c",
      "FsFe[6 * prv[a] + 3 + c]", "FsFe[6 * nxt[a] + 3 + c]", PINS),
+    ("subset_assembly_wrong_end", "ptadd_oracle.c",
+     "F_out[3 * k + c] = Fs[c] + Ge[c];", "F_out[3 * k + c] = Fs[c] + Gs[c];", PINS),
     # the glide mobility (Eq. 2.1), lumped and consistent
     ("glide_projection_dropped", "ptadd_oracle.c",
      "v[c] = (Fa[c] - n[c] * nF) / (B * M);", "v[c] = Fa[c] / (B * M);", PINS),
