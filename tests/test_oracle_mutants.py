@@ -130,6 +130,18 @@ MUTANTS = [
      "jbreak[p] <= t) {", "jbreak[p] < t) {", JPINS),
     ("jump_from_the_step_start", "junction_oracle.c",
      "const double jump = tmin - t1;", "const double jump = tmin - t;", JPINS),
+    ("held_node_keeps_moving", "junction_oracle.c",
+     "v[3 * p] = v[3 * p + 1] = v[3 * p + 2] = 0.0;\n                held += 1;", "held += 1;", JPINS),
+    ("recaptured_by_the_loop_it_left", "junction_oracle.c",
+     "if (loop_of[q] == loop_of[p] || loop_of[q] == jlast[p]) continue;",
+     "if (loop_of[q] == loop_of[p]) continue;", JPINS),
+    ("capture_radius_doubled", "junction_oracle.c",
+     "x + 3 * nxt[q]) < rc2) {", "x + 3 * nxt[q]) < 4.0 * rc2) {", JPINS),
+    ("density_dropped_over_the_jump", "junction_oracle.c",
+     "S_rho += rho * jump;", "S_rho += 0.0 * jump;", JPINS),
+    ("pinned_rows_keep_their_coupling", "ptadd_oracle.c",
+     "for (int64_t q = 0; q < m; ++q) A[i * m + q] = 0.0;\n                A[i * m + i] = 1.0;",
+     "A[i * m + i] = 1.0;", PINS),
     # the surrogate's network (Sec. 3.3): activation, loss gradient, Adam
     ("gelu_derivative_exponent", "mlp_oracle.c",
      "z * exp(-0.5 * z * z) / sqrt(2.0 * pi)", "z * exp(-z * z) / sqrt(2.0 * pi)", MPINS),
